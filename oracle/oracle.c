@@ -1,0 +1,524 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU oracle of the micro-macro parareal hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * execute this file; only the tests, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py do.  It shares no code with the
+ * CUDA library (paper_1912_09240_gb300/csrc): every formula here is written
+ * out again from the paper (Legoll, Lelievre, Myerscough, Samaey,
+ * "Parareal computation of stochastic differential equations with time-scale
+ * separation: a numerical study", arXiv:1912.09240) in its own order and
+ * notation, in double precision, with no blocking, fusion or reordering.
+ *
+ * Readings of passages that are silent or garbled are listed in the design doc
+ * ("Readings of the paper") and repeated at the function they affect.
+ *
+ * Compile with -ffp-contract=off so that no multiply-add is fused: every
+ * operation below is one IEEE-754 double operation, identical on x86-64 and
+ * aarch64.
+ *
+ * Pins (tests/test_oracle_*.py): Philox words against Triton's independent
+ * Philox4x32-10, normal statistics, EM moment recursion of the linear
+ * family, brute-force restriction and CDF-at-edge exactness, strong
+ * projection of the matching, Gaussian quantile arithmetic and the iterator
+ * property of J_q, the parareal exactness theorem.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Random numbers.  The paper draws the EM increments dU_m, dV_m ~ N(0, dt)  */
+/* independently (Section 2.1.3, Eqs. EMx/EMy) and reuses the same numbers  */
+/* in every parareal iteration within a subinterval (Section 6).  Both are   */
+/* met by a counter-based generator keyed by (seed) and counted by           */
+/* (step, particle, slice, problem): Philox4x32-10 as published by Salmon,   */
+/* Moraes, Dror and Shaw (SC'11).                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Philox4x32 round multipliers and Weyl key increments (SC'11, Table 2). */
+static const uint32_t OR_PHILOX_MUL_A = 0xD2511F53u;
+static const uint32_t OR_PHILOX_MUL_B = 0xCD9E8D57u;
+static const uint32_t OR_PHILOX_WEYL_A = 0x9E3779B9u;
+static const uint32_t OR_PHILOX_WEYL_B = 0xBB67AE85u;
+
+/* One Philox4x32-10 block: 10 rounds of the S-box, key bumped in between. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += OR_PHILOX_WEYL_A;
+            k1 += OR_PHILOX_WEYL_B;
+        }
+        uint64_t prod_a = (uint64_t)OR_PHILOX_MUL_A * (uint64_t)c0;
+        uint64_t prod_b = (uint64_t)OR_PHILOX_MUL_B * (uint64_t)c2;
+        uint32_t hi_a = (uint32_t)(prod_a >> 32), lo_a = (uint32_t)prod_a;
+        uint32_t hi_b = (uint32_t)(prod_b >> 32), lo_b = (uint32_t)prod_b;
+        uint32_t n0 = hi_b ^ c1 ^ k0;
+        uint32_t n1 = lo_b;
+        uint32_t n2 = hi_a ^ c3 ^ k1;
+        uint32_t n3 = lo_a;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Batch form for tests: n counters in ctr[n][4], one key. */
+void or_philox_batch(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out)
+{
+    uint32_t key[2] = { (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32) };
+    for (int64_t i = 0; i < n; ++i) or_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
+/* Uniform on (0,1) from one 32-bit word: the odd 24-bit integer
+ * 2*(w >> 9) + 1 times 2^-24.  Exactly representable in binary32 and
+ * binary64, never 0 or 1. */
+double or_uniform(uint32_t w)
+{
+    return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+/* Box-Muller: two uniforms to two independent standard normals. */
+static void or_box_muller(uint32_t w0, uint32_t w1, double* z0, double* z1)
+{
+    double u0 = or_uniform(w0);
+    double u1 = or_uniform(w1);
+    double r = sqrt(-2.0 * log(u0));
+    double theta = 2.0 * M_PI * u1;
+    *z0 = r * cos(theta);
+    *z1 = r * sin(theta);
+}
+
+/* The Q = 1 + d standard normals of fine step m of particle p in slice n of
+ * problem `problem`.  Counter layout (a reading: the paper fixes only that
+ * numbers are reused across iterations):
+ *   Q <= 2 : one block serves two steps, ctr = (m >> 1, p, n, problem << 8);
+ *            step m takes words 2*(m & 1) and 2*(m & 1) + 1.
+ *   Q  > 2 : ctr = (m, p, n, (problem << 8) | g), g = 0, 1, ..., words taken
+ *            in pairs in order; the last pair's spare normal is dropped.
+ * z[0] drives the slow variable, z[1 + j] the fast component j. */
+void or_step_normals(uint64_t seed, uint32_t problem, uint32_t p, uint32_t n,
+                     uint32_t m, int Q, double* z)
+{
+    uint32_t key[2] = { (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32) };
+    uint32_t ctr[4], w[4];
+    if (Q <= 2) {
+        ctr[0] = m >> 1; ctr[1] = p; ctr[2] = n; ctr[3] = problem << 8;
+        or_philox4x32_10(ctr, key, w);
+        int off = 2 * (int)(m & 1u);
+        double a, b;
+        or_box_muller(w[off], w[off + 1], &a, &b);
+        z[0] = a;
+        if (Q == 2) z[1] = b;
+        return;
+    }
+    int got = 0;
+    for (uint32_t g = 0; got < Q; ++g) {
+        ctr[0] = m; ctr[1] = p; ctr[2] = n; ctr[3] = (problem << 8) | g;
+        or_philox4x32_10(ctr, key, w);
+        for (int pair = 0; pair < 2 && got < Q; ++pair) {
+            double a, b;
+            or_box_muller(w[2 * pair], w[2 * pair + 1], &a, &b);
+            z[got++] = a;
+            if (got < Q) z[got++] = b;
+        }
+    }
+}
+
+/* Normals of steps m0 .. m0+n_steps-1 for particles p0 .. p0+n_part-1 of
+ * slice n: out[particle][step][Q] (for statistical tests). */
+void or_normals_block(uint64_t seed, uint32_t problem, uint32_t p0, int64_t n_part,
+                      uint32_t n, uint32_t m0, int n_steps, int Q, double* out)
+{
+    for (int64_t i = 0; i < n_part; ++i)
+        for (int m = 0; m < n_steps; ++m)
+            or_step_normals(seed, problem, p0 + (uint32_t)i, n, m0 + (uint32_t)m, Q,
+                            out + (i * n_steps + m) * Q);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Slow-fast SDE (Section 2.1.1, Eqs. SDEx/SDEy) and its Euler-Maruyama      */
+/* discretisation (Section 2.1.3, Eqs. EMx/EMy).  Three drift families:      */
+/*   kind 0 (linear OU):  d_x F = x - lambda*y,          D = 1/beta          */
+/*   kind 1 (double well): d_x F = x^3 - x + lambda*y,   D = 1/beta          */
+/*   kind 2 (double well, d-dim fast OU): d_x F = x^3 - x + lambda*mean(y)   */
+/* and in every family the fast potential G = |y - x|^2 / 2 (per component), */
+/* E = 1.                                                                    */
+/* ------------------------------------------------------------------------ */
+
+enum { OR_MODEL_OU = 0, OR_MODEL_DOUBLE_WELL = 1, OR_MODEL_DW_MULTI = 2 };
+
+static double or_dFdx(int kind, int d, double lambda, double x, const double* y)
+{
+    if (kind == OR_MODEL_OU) return x - lambda * y[0];
+    if (kind == OR_MODEL_DOUBLE_WELL) return x * x * x - x + lambda * y[0];
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) s += y[j];
+    return x * x * x - x + lambda * (s / (double)d);
+}
+
+/* Advance slices slice_begin .. slice_begin + n_slices - 1 in place.
+ * x: [n_slices][N], y: [n_slices][d][N] (structure of arrays).  Each slice
+ * takes S Euler-Maruyama steps of size dt; slice n uses the random numbers
+ * of (seed, problem, particle, n, step). */
+void or_fine_propagate(int kind, int d, double lambda, double beta, double eps, double tau_x,
+                       uint64_t seed, uint32_t problem,
+                       double* x, double* y, int64_t N,
+                       int slice_begin, int n_slices, int S, double dt)
+{
+    const int Q = 1 + d;
+    const double D = 1.0 / beta;     /* slow diffusion D(x, y) */
+    const double E = 1.0;            /* fast diffusion E(x, y) */
+    const double sqrt_dt = sqrt(dt);
+    for (int s = 0; s < n_slices; ++s) {
+        const uint32_t n = (uint32_t)(slice_begin + s);
+        double* xs = x + (int64_t)s * N;
+        double* ys = y + (int64_t)s * d * N;
+#pragma omp parallel for schedule(static)
+        for (int64_t p = 0; p < N; ++p) {
+            double X = xs[p];
+            double Y[64], Ynew[64], z[65];
+            for (int j = 0; j < d; ++j) Y[j] = ys[(int64_t)j * N + p];
+            for (int m = 0; m < S; ++m) {
+                or_step_normals(seed, problem, (uint32_t)p, n, (uint32_t)m, Q, z);
+                double dU = sqrt_dt * z[0];
+                double Xnew = X - (1.0 / tau_x) * or_dFdx(kind, d, lambda, X, Y) * dt
+                                + sqrt(2.0 * D / tau_x) * dU;
+                for (int j = 0; j < d; ++j) {
+                    double dV = sqrt_dt * z[1 + j];
+                    double dGdy = Y[j] - X;
+                    Ynew[j] = Y[j] - (1.0 / eps) * dGdy * dt + sqrt(2.0 * E / eps) * dV;
+                }
+                X = Xnew;
+                for (int j = 0; j < d; ++j) Y[j] = Ynew[j];
+            }
+            xs[p] = X;
+            for (int j = 0; j < d; ++j) ys[(int64_t)j * N + p] = Y[j];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Uniform grid x_lo = e_0 < e_1 < ... < e_I = x_hi (Section 2.2.2).         */
+/* ------------------------------------------------------------------------ */
+
+double or_edge(int i, int I, double lo, double hi)
+{
+    double h = (hi - lo) / (double)I;
+    return lo + (double)i * h;
+}
+
+/* Bin of x: the i with e_i <= x < e_{i+1}, decided by exact comparison with
+ * the edges, and clamped into [0, I-1] (a reading: the paper's strict
+ * inequalities in Eq. binning leave edge points and escaped particles
+ * unassigned; clamping keeps unit mass like the zero-flux coarse model). */
+int or_bin(double x, int I, double lo, double hi)
+{
+    if (!(x >= lo)) return 0;          /* also catches NaN */
+    if (x >= hi) return I - 1;
+    double h = (hi - lo) / (double)I;
+    int i = (int)floor((x - lo) / h);
+    if (i < 0) i = 0;
+    if (i > I - 1) i = I - 1;
+    while (i > 0 && x < or_edge(i, I, lo, hi)) --i;
+    while (i < I - 1 && x >= or_edge(i + 1, I, lo, hi)) ++i;
+    return i;
+}
+
+/* Restriction R = R2 o R1 (Section 3.2.2, Eq. binning) with uniform weights
+ * W = 1/N: counts per bin, and the piecewise-linear CDF at the edges
+ * (Eq. discr_cdf), C_0 = 0, C_i = (number of particles in bins < i) / N. */
+void or_restrict(const double* x, int64_t N, int n_slices, int I, double lo, double hi,
+                 uint32_t* counts, double* cdf)
+{
+    for (int s = 0; s < n_slices; ++s) {
+        const double* xs = x + (int64_t)s * N;
+        uint32_t* cs = counts + (int64_t)s * I;
+        double* Cs = cdf + (int64_t)s * (I + 1);
+        for (int i = 0; i < I; ++i) cs[i] = 0;
+        for (int64_t p = 0; p < N; ++p) cs[or_bin(xs[p], I, lo, hi)] += 1;
+        uint64_t below = 0;
+        Cs[0] = 0.0;
+        for (int i = 0; i < I; ++i) {
+            below += cs[i];
+            Cs[i + 1] = (double)below / (double)N;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Matching that preserves the fast marginal (Section 5.1, Eq.              */
+/* transformation): X = c^{-1}(cbar(Xbar)), Y = Ybar, with both CDFs the     */
+/* piecewise-linear ones of the histograms.  Readings (the printed formulas  */
+/* swap rho and rhobar): the prior's bin mass enters cbar, the posterior's   */
+/* bin mass enters the inversion; the inverse bin is the lowest non-empty    */
+/* bin whose upper CDF value reaches u; where prior and target CDF agree at  */
+/* both edges of the particle's bin the map is the identity there (this is  */
+/* the strong projection property, Eq. projection, held exactly); particles  */
+/* outside [x_lo, x_hi] move by the displacement of the nearest edge.        */
+/* ------------------------------------------------------------------------ */
+
+static double or_match_one(double xbar, int I, double lo, double hi,
+                           const double* Cp, const double* Ct)
+{
+    const double h = (hi - lo) / (double)I;
+    int i = or_bin(xbar, I, lo, hi);
+    if (Cp[i] == Ct[i] && Cp[i + 1] == Ct[i + 1]) return xbar;
+    double ei = or_edge(i, I, lo, hi);
+    double frac = (xbar - ei) / h;
+    int below = 0, above = 0;
+    if (frac < 0.0) { frac = 0.0; below = 1; }
+    if (frac > 1.0) { frac = 1.0; above = 1; }
+    double rho_prior = Cp[i + 1] - Cp[i];
+    double u = Cp[i] + frac * rho_prior;
+    int j = -1, last_nonempty = -1;
+    for (int k = 0; k < I; ++k) {
+        double rho_k = Ct[k + 1] - Ct[k];
+        if (rho_k > 0.0) {
+            last_nonempty = k;
+            if (Ct[k + 1] >= u) { j = k; break; }
+        }
+    }
+    if (j < 0) j = last_nonempty;
+    if (j < 0) return xbar;            /* empty target: nothing to match */
+    double rho_j = Ct[j + 1] - Ct[j];
+    double t = (u - Ct[j]) / rho_j;
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    double xnew = or_edge(j, I, lo, hi) + t * h;
+    if (below) return xbar + (xnew - lo);
+    if (above) return xbar + (xnew - hi);
+    return xnew;
+}
+
+void or_match(const double* x_prior, double* x_out, int64_t N, int n_slices,
+              int I, double lo, double hi, const double* cdf_prior, const double* cdf_target)
+{
+    for (int s = 0; s < n_slices; ++s) {
+        const double* Cp = cdf_prior + (int64_t)s * (I + 1);
+        const double* Ct = cdf_target + (int64_t)s * (I + 1);
+#pragma omp parallel for schedule(static)
+        for (int64_t p = 0; p < N; ++p)
+            x_out[(int64_t)s * N + p] = or_match_one(x_prior[(int64_t)s * N + p], I, lo, hi, Cp, Ct);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Quantile iterator J_q (Section 4.4, Eqs. quantile_reconstruction,        */
+/* discr_cdf).  All three states are given as CDFs at the I+1 edges.         */
+/*   a = rho_c^{n+1} (qhat), b = rho_f^* (qbar), c = rho_c^* (q).            */
+/* mode 0 ("two-sided", default reading): at a level p that a CDF takes on a */
+/* flat stretch, both ends of the stretch are kept as knots, so that         */
+/* J(a, b, a) = b holds exactly.  mode 1 ("midpoint", the paper's literal    */
+/* rule): the midpoint of the stretch.  Both modes use q(0) = max{x: c = 0}  */
+/* and q(1) = min{x: c = 1}.  qtilde = qbar + (qhat - q) in that order.  The  */
+/* monotonicity repair averages violating neighbours until none is left      */
+/* (pool-adjacent-violators with equal weights).                             */
+/* ------------------------------------------------------------------------ */
+
+/* A level strictly between two edge values of a CDF has its quantile
+ * strictly inside that bin: e0 + t*h, kept off the edges e0, e1 when the
+ * rounding of the interpolation would land on one.  (Without this a tiny
+ * level could round onto an edge and lift the CDF read back there.) */
+static double or_inside(double e0, double e1, double t, double h)
+{
+    double q = e0 + t * h;
+    if (q <= e0) q = nextafter(e0, e1);
+    if (q >= e1) q = nextafter(e1, e0);
+    return q;
+}
+
+/* q^-(p) = min{x : F(x) >= p} */
+static double or_q_minus(const double* F, int I, double lo, double hi, double p)
+{
+    const double h = (hi - lo) / (double)I;
+    int a = 0;
+    while (a < I && F[a] < p) ++a;
+    if (F[a] == p || a == 0) return or_edge(a, I, lo, hi);
+    double t = (p - F[a - 1]) / (F[a] - F[a - 1]);
+    return or_inside(or_edge(a - 1, I, lo, hi), or_edge(a, I, lo, hi), t, h);
+}
+
+/* q^+(p) = max{x : F(x) <= p} */
+static double or_q_plus(const double* F, int I, double lo, double hi, double p)
+{
+    const double h = (hi - lo) / (double)I;
+    int b = I;
+    while (b > 0 && F[b] > p) --b;
+    if (F[b] == p || b == I) return or_edge(b, I, lo, hi);
+    double t = (p - F[b]) / (F[b + 1] - F[b]);
+    return or_inside(or_edge(b, I, lo, hi), or_edge(b + 1, I, lo, hi), t, h);
+}
+
+static int or_cmp_double(const void* a, const void* b)
+{
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* Returns the number of knots used (for tests); out[I+1] is the new CDF. */
+int or_quantile_update(int I, double lo, double hi, int mode,
+                       const double* A, const double* B, const double* C, double* out)
+{
+    const int M = 3 * (I + 1);
+    double* levels = (double*)malloc(sizeof(double) * M);
+    for (int i = 0; i <= I; ++i) {
+        levels[i] = A[i];
+        levels[I + 1 + i] = B[i];
+        levels[2 * (I + 1) + i] = C[i];
+    }
+    for (int k = 0; k < M; ++k) {
+        if (levels[k] < 0.0) levels[k] = 0.0;
+        if (levels[k] > 1.0) levels[k] = 1.0;
+    }
+    qsort(levels, M, sizeof(double), or_cmp_double);
+    int L = 0;
+    for (int k = 0; k < M; ++k)
+        if (L == 0 || levels[k] != levels[L - 1]) levels[L++] = levels[k];
+
+    double* kq = (double*)malloc(sizeof(double) * 2 * L);
+    double* kp = (double*)malloc(sizeof(double) * 2 * L);
+    int nk = 0;
+    for (int l = 0; l < L; ++l) {
+        double p = levels[l];
+        int first = (l == 0), last = (l == L - 1);
+        double am = or_q_minus(A, I, lo, hi, p), ap = or_q_plus(A, I, lo, hi, p);
+        double bm = or_q_minus(B, I, lo, hi, p), bp = or_q_plus(B, I, lo, hi, p);
+        double cm = or_q_minus(C, I, lo, hi, p), cp = or_q_plus(C, I, lo, hi, p);
+        if (mode == 0) {
+            if (!first) { kq[nk] = bm + (am - cm); kp[nk] = p; ++nk; }
+            if (!last)  { kq[nk] = bp + (ap - cp); kp[nk] = p; ++nk; }
+            if (first && last) { kq[nk] = bp + (ap - cp); kp[nk] = p; ++nk; }
+        } else {
+            double qa, qb, qc;
+            if (first) { qa = ap; qb = bp; qc = cp; }
+            else if (last) { qa = am; qb = bm; qc = cm; }
+            else { qa = 0.5 * (am + ap); qb = 0.5 * (bm + bp); qc = 0.5 * (cm + cp); }
+            kq[nk] = qb + (qa - qc); kp[nk] = p; ++nk;
+        }
+    }
+
+    /* pool adjacent violators on kq (equal weights) */
+    double* bsum = (double*)malloc(sizeof(double) * nk);
+    int* bcnt = (int*)malloc(sizeof(int) * nk);
+    int nb = 0;
+    for (int k = 0; k < nk; ++k) {
+        bsum[nb] = kq[k]; bcnt[nb] = 1; ++nb;
+        while (nb >= 2 && bsum[nb - 2] / bcnt[nb - 2] > bsum[nb - 1] / bcnt[nb - 1]) {
+            bsum[nb - 2] += bsum[nb - 1];
+            bcnt[nb - 2] += bcnt[nb - 1];
+            --nb;
+        }
+    }
+    int k = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (bcnt[b] == 1) { ++k; continue; }       /* untouched knot keeps its bits */
+        double mean = bsum[b] / bcnt[b];
+        for (int c = 0; c < bcnt[b]; ++c) kq[k++] = mean;
+    }
+
+    /* PL CDF through (kq, kp), right-continuous, evaluated at the edges */
+    out[0] = 0.0;
+    out[I] = 1.0;
+    for (int i = 1; i < I; ++i) {
+        double x = or_edge(i, I, lo, hi);
+        int jmax = -1;
+        for (int j = 0; j < nk; ++j)
+            if (kq[j] <= x) jmax = j;
+        double v;
+        if (jmax < 0) v = 0.0;
+        else if (jmax == nk - 1) v = kp[nk - 1];
+        else {
+            double t = (x - kq[jmax]) / (kq[jmax + 1] - kq[jmax]);
+            v = kp[jmax] + t * (kp[jmax + 1] - kp[jmax]);
+        }
+        if (v < 0.0) v = 0.0;
+        if (v > 1.0) v = 1.0;
+        out[i] = v;
+    }
+    free(levels); free(kq); free(kp); free(bsum); free(bcnt);
+    return nk;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The other iterators of Section 4 on bin masses (rho_i = C_{i+1} - C_i),  */
+/* results returned as CDFs.                                                 */
+/* ------------------------------------------------------------------------ */
+
+static void or_cdf_from_mass(int I, const double* m, double* out)
+{
+    double total = 0.0;
+    for (int i = 0; i < I; ++i) total += m[i];
+    double run = 0.0;
+    out[0] = 0.0;
+    for (int i = 0; i < I; ++i) {
+        run += m[i];
+        out[i + 1] = run / total;
+    }
+    out[I] = 1.0;
+}
+
+/* kind 1: additive (Section 4.1), negatives to zero then rescale.
+ * kind 2: multiplicative (Section 4.2), unsupported bins to zero then rescale.
+ * kind 3: rotation on the L2 sphere (Section 4.3). */
+void or_iterator_mass(int kind, int I, const double* A, const double* B, const double* C, double* out)
+{
+    double* a = (double*)malloc(sizeof(double) * I);
+    double* b = (double*)malloc(sizeof(double) * I);
+    double* c = (double*)malloc(sizeof(double) * I);
+    double* r = (double*)malloc(sizeof(double) * I);
+    for (int i = 0; i < I; ++i) {
+        a[i] = A[i + 1] - A[i];
+        b[i] = B[i + 1] - B[i];
+        c[i] = C[i + 1] - C[i];
+    }
+    if (kind == 1) {
+        for (int i = 0; i < I; ++i) {
+            r[i] = a[i] + b[i] - c[i];
+            if (r[i] < 0.0) r[i] = 0.0;
+        }
+    } else if (kind == 2) {
+        for (int i = 0; i < I; ++i) r[i] = (c[i] > 0.0) ? a[i] * (b[i] / c[i]) : 0.0;
+    } else {
+        double u = 0.0, v = 0.0, w = 0.0;
+        for (int i = 0; i < I; ++i) {
+            u += sqrt(b[i] * c[i]);
+            v += sqrt(b[i] * a[i]);
+            w += sqrt(c[i] * a[i]);
+        }
+        double ca = (u + 2.0 * u * w - v) / (1.0 + w);
+        double cc = (u + v) / (1.0 + w);
+        for (int i = 0; i < I; ++i) {
+            double s = ca * sqrt(a[i]) + sqrt(b[i]) - cc * sqrt(c[i]);
+            r[i] = s * s;
+        }
+    }
+    or_cdf_from_mass(I, r, out);
+    free(a); free(b); free(c); free(r);
+}
+
+/* ------------------------------------------------------------------------ */
+/* W1 distance between two histograms on the same grid, each read as its    */
+/* piecewise-linear CDF: integral of |C1 - C2| over [x_lo, x_hi], exact for */
+/* the linear difference on every bin.                                       */
+/* ------------------------------------------------------------------------ */
+
+double or_w1(int I, double lo, double hi, const double* C1, const double* C2)
+{
+    const double h = (hi - lo) / (double)I;
+    double acc = 0.0;
+    for (int i = 0; i < I; ++i) {
+        double d0 = C1[i] - C2[i], d1 = C1[i + 1] - C2[i + 1];
+        double a0 = fabs(d0), a1 = fabs(d1);
+        if ((d0 >= 0.0 && d1 >= 0.0) || (d0 <= 0.0 && d1 <= 0.0)) acc += 0.5 * h * (a0 + a1);
+        else acc += h * (d0 * d0 + d1 * d1) / (2.0 * (a0 + a1));
+    }
+    return acc;
+}

@@ -1,0 +1,355 @@
+"""Plain FP64 CPU oracle of the micro-macro parareal hot path.
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module.  It shares no code with the CUDA library and never imports it.
+
+The per-particle and per-bin work is plain C in ``oracle.c`` (loaded through
+ctypes); the coarse Fokker-Planck propagator is assembled here entry by entry
+from the finite-volume fluxes of Section 2.2.2 and exponentiated with
+``scipy.linalg.expm`` (a library primitive).  The parareal driver follows
+Sections 3.2.3-3.2.4 step by step.
+
+Parity pins live in ``tests/test_oracle_*.py``; every function below is pinned
+(no "parity unpinned" function remains in this module).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+
+MODEL_OU, MODEL_DOUBLE_WELL, MODEL_DW_MULTI = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into _build/liboracle.so (gcc, FP64, no contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call([
+            "gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+            "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        d, i64, i32, u32, u64 = (ctypes.c_double, ctypes.c_int64, ctypes.c_int,
+                                 ctypes.c_uint32, ctypes.c_uint64)
+        vp = ctypes.c_void_p
+        _lib.or_philox_batch.argtypes = [vp, i64, u64, vp]
+        _lib.or_uniform.argtypes = [u32]
+        _lib.or_uniform.restype = d
+        _lib.or_step_normals.argtypes = [u64, u32, u32, u32, u32, i32, vp]
+        _lib.or_normals_block.argtypes = [u64, u32, u32, i64, u32, u32, i32, i32, vp]
+        _lib.or_fine_propagate.argtypes = [i32, i32, d, d, d, d, u64, u32, vp, vp, i64,
+                                           i32, i32, i32, d]
+        _lib.or_edge.argtypes = [i32, i32, d, d]
+        _lib.or_edge.restype = d
+        _lib.or_bin.argtypes = [d, i32, d, d]
+        _lib.or_bin.restype = i32
+        _lib.or_restrict.argtypes = [vp, i64, i32, i32, d, d, vp, vp]
+        _lib.or_match.argtypes = [vp, vp, i64, i32, i32, d, d, vp, vp]
+        _lib.or_quantile_update.argtypes = [i32, d, d, i32, vp, vp, vp, vp]
+        _lib.or_quantile_update.restype = i32
+        _lib.or_iterator_mass.argtypes = [i32, i32, vp, vp, vp, vp]
+        _lib.or_w1.argtypes = [i32, d, d, vp, vp]
+        _lib.or_w1.restype = d
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# --------------------------------------------------------------------------
+# Model and grid descriptions
+# --------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class Model:
+    """Slow-fast SDE of Section 2.1.1 with tau_x = 1 unless given.
+
+    kind 0: d_x F = x - lambda*y           (linear OU family)
+    kind 1: d_x F = x^3 - x + lambda*y     (double well)
+    kind 2: d_x F = x^3 - x + lambda*mean(y), y in R^d
+    fast:   d_y G = y - x per component, E = 1; slow diffusion D = 1/beta.
+    """
+    kind: int
+    fast_dim: int = 1
+    lam: float = 1.0
+    beta: float = 1.0
+    eps: float = 0.1
+    tau_x: float = 1.0
+
+
+@dataclass(frozen=True)
+class Grid:
+    bins: int
+    lo: float
+    hi: float
+
+    @property
+    def h(self) -> float:
+        return (self.hi - self.lo) / self.bins
+
+    def edges(self) -> np.ndarray:
+        return np.array([lib().or_edge(i, self.bins, self.lo, self.hi)
+                         for i in range(self.bins + 1)])
+
+
+# --------------------------------------------------------------------------
+# RNG
+# --------------------------------------------------------------------------
+
+def philox(ctr: np.ndarray, seed: int) -> np.ndarray:
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr)
+    lib().or_philox_batch(_p(ctr), ctr.shape[0], seed, _p(out))
+    return out
+
+
+def uniform(w: int) -> float:
+    return lib().or_uniform(w)
+
+
+def step_normals(seed: int, problem: int, p: int, n: int, m: int, Q: int) -> np.ndarray:
+    z = np.empty(Q, dtype=np.float64)
+    lib().or_step_normals(seed, problem, p, n, m, Q, _p(z))
+    return z
+
+
+def normals_block(seed: int, problem: int, p0: int, n_part: int, n: int, m0: int,
+                  n_steps: int, Q: int) -> np.ndarray:
+    out = np.empty((n_part, n_steps, Q), dtype=np.float64)
+    lib().or_normals_block(seed, problem, p0, n_part, n, m0, n_steps, Q, _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Fine propagator (Section 2.1.3, Eqs. EMx/EMy)
+# --------------------------------------------------------------------------
+
+def fine_propagate(model: Model, seed: int, x: np.ndarray, y: np.ndarray, slice_begin: int,
+                   steps: int, dt: float, problem: int = 0):
+    """Advance x[n_slices][N], y[n_slices][d][N] (copies) by `steps` EM steps per slice."""
+    x = np.array(x, dtype=np.float64, order="C", copy=True)
+    y = np.array(y, dtype=np.float64, order="C", copy=True)
+    n_slices, N = x.shape
+    assert y.shape == (n_slices, model.fast_dim, N)
+    lib().or_fine_propagate(model.kind, model.fast_dim, model.lam, model.beta, model.eps,
+                            model.tau_x, seed, problem, _p(x), _p(y), N, slice_begin,
+                            n_slices, steps, dt)
+    return x, y
+
+
+# --------------------------------------------------------------------------
+# Restriction, matching, iterators, W1
+# --------------------------------------------------------------------------
+
+def bin_index(x: float, grid: Grid) -> int:
+    return lib().or_bin(float(x), grid.bins, grid.lo, grid.hi)
+
+
+def restrict(x: np.ndarray, grid: Grid):
+    """x[n_slices][N] -> (counts[n_slices][I] uint32, cdf[n_slices][I+1])."""
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    n_slices, N = x.shape
+    counts = np.empty((n_slices, grid.bins), dtype=np.uint32)
+    cdf = np.empty((n_slices, grid.bins + 1), dtype=np.float64)
+    lib().or_restrict(_p(x), N, n_slices, grid.bins, grid.lo, grid.hi, _p(counts), _p(cdf))
+    return counts, cdf
+
+
+def match(x_prior: np.ndarray, grid: Grid, cdf_prior: np.ndarray, cdf_target: np.ndarray):
+    x_prior = np.ascontiguousarray(np.atleast_2d(x_prior), dtype=np.float64)
+    n_slices, N = x_prior.shape
+    cp = np.ascontiguousarray(np.atleast_2d(cdf_prior), dtype=np.float64)
+    ct = np.ascontiguousarray(np.atleast_2d(cdf_target), dtype=np.float64)
+    assert cp.shape == ct.shape == (n_slices, grid.bins + 1)
+    out = np.empty_like(x_prior)
+    lib().or_match(_p(x_prior), _p(out), N, n_slices, grid.bins, grid.lo, grid.hi, _p(cp), _p(ct))
+    return out
+
+
+QMODE_TWO_SIDED, QMODE_MIDPOINT = 0, 1
+ITER_QUANTILE, ITER_ADD, ITER_MULT, ITER_ROT = 0, 1, 2, 3
+
+
+def iterate(grid: Grid, a: np.ndarray, b: np.ndarray, c: np.ndarray,
+            iterator: int = ITER_QUANTILE, qmode: int = QMODE_TWO_SIDED) -> np.ndarray:
+    """J(a = rho_c^{n+1}, b = rho_f^*, c = rho_c^*) on CDFs; returns the new CDF."""
+    a, b, c = (np.ascontiguousarray(v, dtype=np.float64) for v in (a, b, c))
+    out = np.empty(grid.bins + 1, dtype=np.float64)
+    if iterator == ITER_QUANTILE:
+        lib().or_quantile_update(grid.bins, grid.lo, grid.hi, qmode, _p(a), _p(b), _p(c), _p(out))
+    else:
+        lib().or_iterator_mass(iterator, grid.bins, _p(a), _p(b), _p(c), _p(out))
+    return out
+
+
+def w1(grid: Grid, c1: np.ndarray, c2: np.ndarray) -> float:
+    c1 = np.ascontiguousarray(c1, dtype=np.float64)
+    c2 = np.ascontiguousarray(c2, dtype=np.float64)
+    return lib().or_w1(grid.bins, grid.lo, grid.hi, _p(c1), _p(c2))
+
+
+# --------------------------------------------------------------------------
+# Coarse propagator (Section 2.2.2): finite volumes on the detailed-balance
+# form of Eq. FPz_rewritten, exact in time through the matrix exponential.
+# --------------------------------------------------------------------------
+
+def effective_potential(model: Model, x):
+    """Fbar(x) with Fbar(0) = 0, by averaging d_x F over phi(y; x) = N(x, 1)
+    (Eq. Fbar; the fast OU has E[y | x] = x in every component)."""
+    x = np.asarray(x, dtype=np.float64)
+    if model.kind == MODEL_OU:
+        return 0.5 * (1.0 - model.lam) * x * x
+    return 0.25 * x ** 4 - 0.5 * (1.0 - model.lam) * x * x
+
+
+def log_rho_inf(model: Model, x):
+    """log rho_inf(x) = log(1/Dbar) - int_0^x Fbar'(s)/Dbar ds, Dbar = 1/beta (Eq. Dbar)."""
+    Dbar = 1.0 / model.beta
+    return np.log(1.0 / Dbar) - effective_potential(model, x) / Dbar
+
+
+def coarse_generator(model: Model, grid: Grid) -> np.ndarray:
+    """A with d m/dt = A m for the cell masses m_c (zero flux at both ends).
+
+    Flux at interior edge e between cells e-1 and e:
+      phi_e = Dbar rho_inf(x_e) / h_e * ( m_e / (h_{e+1/2} rho_inf(xi_e))
+                                       - m_{e-1} / (h_{e-1/2} rho_inf(xi_{e-1})) )
+    with h_e the distance between the two centres; dm_c/dt = (phi_{c+1} - phi_c)/tau_x.
+    """
+    I = grid.bins
+    x = grid.edges()
+    xi = 0.5 * (x[:-1] + x[1:])
+    width = x[1:] - x[:-1]
+    Dbar = 1.0 / model.beta
+    A = np.zeros((I, I), dtype=np.float64)
+    for e in range(1, I):
+        h_e = xi[e] - xi[e - 1]
+        coef = Dbar / h_e
+        r_right = np.exp(log_rho_inf(model, x[e]) - log_rho_inf(model, xi[e])) / width[e]
+        r_left = np.exp(log_rho_inf(model, x[e]) - log_rho_inf(model, xi[e - 1])) / width[e - 1]
+        # phi_e = coef * (r_right * m_e - r_left * m_{e-1})
+        # cell e-1 gains +phi_e (its right edge), cell e loses phi_e (its left edge)
+        A[e - 1, e] += coef * r_right / model.tau_x
+        A[e - 1, e - 1] -= coef * r_left / model.tau_x
+        A[e, e] -= coef * r_right / model.tau_x
+        A[e, e - 1] += coef * r_left / model.tau_x
+    return A
+
+
+def coarse_propagator(model: Model, grid: Grid, slice_dt: float) -> np.ndarray:
+    import scipy.linalg
+    return scipy.linalg.expm(coarse_generator(model, grid) * slice_dt)
+
+
+def coarse_apply(P: np.ndarray, cdf: np.ndarray) -> np.ndarray:
+    """C(rho) on a CDF: masses, P @ masses, cumulative sum normalised to 1."""
+    cdf = np.atleast_2d(np.asarray(cdf, dtype=np.float64))
+    out = np.empty_like(cdf)
+    for r in range(cdf.shape[0]):
+        m = cdf[r, 1:] - cdf[r, :-1]
+        mp = P @ m
+        s = np.cumsum(mp)
+        out[r, 0] = 0.0
+        out[r, 1:] = s / s[-1]
+        out[r, -1] = 1.0
+    return out
+
+
+# --------------------------------------------------------------------------
+# Micro-macro parareal driver (Sections 3.2.3-3.2.4), viewpoint (i)
+# --------------------------------------------------------------------------
+
+@dataclass
+class PararealResult:
+    x: list           # x[k] = array [K+1][N], X_k^n (slow)
+    y: list           # y[k] = array [K+1][d][N]
+    rho: list         # rho[k] = CDFs [K+1][I+1], rho_k^n
+    serial_x: np.ndarray | None = None
+    serial_rho: np.ndarray | None = None
+
+
+def serial_fine(model: Model, seed: int, x0, y0, K: int, steps: int, dt: float, problem: int = 0):
+    """X^{n+1} = F_n(X^n), n = 0..K-1 -> x[K+1][N], y[K+1][d][N]."""
+    N = x0.shape[-1]
+    d = model.fast_dim
+    xs = np.empty((K + 1, N))
+    ys = np.empty((K + 1, d, N))
+    xs[0] = x0
+    ys[0] = y0
+    for n in range(K):
+        xn, yn = fine_propagate(model, seed, xs[n][None], ys[n][None], n, steps, dt, problem)
+        xs[n + 1] = xn[0]
+        ys[n + 1] = yn[0]
+    return xs, ys
+
+
+def parareal(model: Model, grid: Grid, seed: int, x0, y0, K: int, steps: int, dt: float,
+             iters: int, qmode: int = QMODE_TWO_SIDED, iterator: int = ITER_QUANTILE,
+             problem: int = 0) -> PararealResult:
+    x0 = np.asarray(x0, dtype=np.float64)
+    y0 = np.asarray(y0, dtype=np.float64).reshape(model.fast_dim, -1)
+    N = x0.shape[0]
+    P = coarse_propagator(model, grid, steps * dt)
+    _, cdf0 = restrict(x0[None], grid)
+    cdf0 = cdf0[0]
+
+    # iteration 0: coarse sweep, then matching against the initial ensemble
+    rho = np.empty((K + 1, grid.bins + 1))
+    rho[0] = cdf0
+    for n in range(K):
+        rho[n + 1] = coarse_apply(P, rho[n])[0]
+    X = np.empty((K + 1, N))
+    Y = np.empty((K + 1, model.fast_dim, N))
+    X[0] = x0
+    Y[0] = y0
+    for n in range(1, K + 1):
+        X[n] = match(x0[None], grid, cdf0[None], rho[n][None])[0]
+        Y[n] = y0
+    res = PararealResult(x=[X.copy()], y=[Y.copy()], rho=[rho.copy()])
+
+    for _k in range(iters):
+        # parallel phase
+        Xbar, Ybar = fine_propagate(model, seed, X[:K], Y[:K], 0, steps, dt, problem)
+        _, f_star = restrict(Xbar, grid)
+        _, start = restrict(X[:K], grid)
+        c_star = coarse_apply(P, start)
+        # serial phase
+        new_rho = np.empty_like(rho)
+        new_rho[0] = cdf0
+        for n in range(K):
+            a = coarse_apply(P, new_rho[n])[0]
+            new_rho[n + 1] = iterate(grid, a, f_star[n], c_star[n], iterator, qmode)
+        # matching with the fine results as priors
+        Xn = np.empty_like(X)
+        Yn = np.empty_like(Y)
+        Xn[0] = x0
+        Yn[0] = y0
+        Xn[1:] = match(Xbar, grid, f_star, new_rho[1:])
+        Yn[1:] = Ybar
+        X, Y, rho = Xn, Yn, new_rho
+        res.x.append(X.copy())
+        res.y.append(Y.copy())
+        res.rho.append(rho.copy())
+    return res

@@ -1,0 +1,111 @@
+"""Pins of the oracle's random numbers (Philox4x32-10 + Box-Muller).
+
+Philox words are checked against an independent implementation: Triton's
+``tl.philox`` run by Triton's CPU interpreter in a subprocess.  Normals are
+checked statistically (moments, Kolmogorov-Smirnov, independence).
+"""
+import json
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+_TRITON_SCRIPT = textwrap.dedent(r'''
+    import os, sys, json
+    os.environ["TRITON_INTERPRET"] = "1"
+    import torch, triton, triton.language as tl
+
+    @triton.jit
+    def kern(c0p, c1p, c2p, c3p, out, seed, n: tl.constexpr):
+        i = tl.arange(0, n)
+        c0 = tl.load(c0p + i); c1 = tl.load(c1p + i)
+        c2 = tl.load(c2p + i); c3 = tl.load(c3p + i)
+        a, b, c, d = tl.philox(seed, c0, c1, c2, c3, 10)
+        tl.store(out + 4 * i + 0, a); tl.store(out + 4 * i + 1, b)
+        tl.store(out + 4 * i + 2, c); tl.store(out + 4 * i + 3, d)
+
+    cfg = json.loads(sys.stdin.read())
+    ctr = torch.tensor(cfg["ctr"], dtype=torch.int64).to(torch.uint32)
+    n = ctr.shape[0]
+    cols = [ctr[:, j].contiguous() for j in range(4)]
+    out = torch.zeros(4 * n, dtype=torch.uint32)
+    kern[(1,)](cols[0], cols[1], cols[2], cols[3], out, cfg["seed"], n)
+    print(json.dumps(out.to(torch.int64).tolist()))
+''')
+
+
+def _triton_philox(ctr: np.ndarray, seed: int) -> np.ndarray:
+    pytest.importorskip("triton")
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    res = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=json.dumps(
+        {"ctr": ctr.astype(np.int64).tolist(), "seed": int(seed)}), capture_output=True,
+        text=True, env=env, timeout=600)
+    if res.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + res.stderr[-300:])
+    return np.array(json.loads(res.stdout), dtype=np.int64).astype(np.uint32).reshape(-1, 4)
+
+
+@pytest.mark.parametrize("seed", [0, 0x0123456789ABCDEF, 0xFFFFFFFFFFFFFFFF])
+def test_philox_matches_triton(orc, seed):
+    rng = np.random.default_rng(7)
+    ctr = rng.integers(0, 2**32, size=(64, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    ctr[2] = [3, 0, 0, 0]
+    ctr[3] = [0, 0, 0, 1]
+    ours = orc.philox(ctr, seed)
+    ref = _triton_philox(ctr, seed)
+    np.testing.assert_array_equal(ours, ref)
+
+
+def test_uniform_exact_and_open(orc):
+    for w in [0, 1, 511, 512, 0x7FFFFFFF, 0x80000000, 0xFFFFFE00, 0xFFFFFFFF]:
+        u = orc.uniform(w)
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u          # exactly representable in binary32
+        k = u * 2.0**24                           # an odd integer below 2^24
+        assert k == int(k) and int(k) % 2 == 1
+    assert orc.uniform(0) == 2.0**-24
+    assert orc.uniform(0xFFFFFFFF) == 1.0 - 2.0**-24
+    # monotone in the top 23 bits
+    ws = np.sort(np.random.default_rng(1).integers(0, 2**32, 2000, dtype=np.uint64))
+    us = [orc.uniform(int(w)) for w in ws]
+    assert all(a <= b for a, b in zip(us, us[1:]))
+
+
+def test_normals_statistics(orc):
+    from scipy import stats
+    z = orc.normals_block(seed=0, problem=0, p0=0, n_part=20000, n=3, m0=0, n_steps=25, Q=2)
+    flat = z.reshape(-1)
+    n = flat.size
+    assert abs(flat.mean()) < 5.0 / np.sqrt(n)
+    assert abs(flat.var() - 1.0) < 5.0 * np.sqrt(2.0 / n)
+    assert stats.kstest(flat, "norm").pvalue > 1e-3
+    # the two normals of a step are uncorrelated, and so are consecutive steps
+    assert abs(np.corrcoef(z[:, :, 0].ravel(), z[:, :, 1].ravel())[0, 1]) < 5.0 / np.sqrt(n / 2)
+    assert abs(np.corrcoef(z[:, :-1, 0].ravel(), z[:, 1:, 0].ravel())[0, 1]) < 5.0 / np.sqrt(n / 2)
+    # fourth moment of a normal is 3
+    assert abs((flat ** 4).mean() - 3.0) < 5.0 * np.sqrt(96.0 / n)
+
+
+def test_normals_many_fast_components(orc):
+    from scipy import stats
+    z = orc.normals_block(seed=5, problem=3, p0=100, n_part=4000, n=1, m0=7, n_steps=10, Q=17)
+    flat = z.reshape(-1)
+    assert stats.kstest(flat, "norm").pvalue > 1e-3
+    c = np.corrcoef(z.reshape(-1, 17).T)
+    off = c[~np.eye(17, dtype=bool)]
+    assert np.max(np.abs(off)) < 5.0 / np.sqrt(40000)
+
+
+def test_counters_separate_streams(orc):
+    """Different slice, particle, problem or seed give different numbers; the
+    same key and counter give the same numbers (reuse across iterations)."""
+    base = orc.step_normals(0, 0, 5, 2, 10, 2)
+    assert np.array_equal(base, orc.step_normals(0, 0, 5, 2, 10, 2))
+    for args in [(1, 0, 5, 2, 10), (0, 1, 5, 2, 10), (0, 0, 6, 2, 10), (0, 0, 5, 3, 10),
+                 (0, 0, 5, 2, 11), (0, 0, 5, 2, 12)]:
+        assert not np.array_equal(base, orc.step_normals(*args, 2))
