@@ -1,0 +1,332 @@
+"""Throughput of the micro-macro parareal hot path on GB300.
+
+One step = one parareal iteration of the double-well workload (2^20
+particles, 50 slices x 1000 Euler-Maruyama steps, FP32 state, 512 bins):
+fine propagation of every slice with the matching fused into its prologue
+and the restriction into its epilogue, the coarse propagator on all start
+states, and the serial quantile-iterator update.  `value` is particle-steps
+per second over the whole job (all ranks); ranks are independent replicas.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the FP64 CPU oracle (the only reference this method
+has) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "fine-propagator particle-steps/s (FP32 vs FP64 GPU) and parareal iter time at W1≤1e-3"
+UNIT = "particle-steps/s"
+WORKLOAD = workloads.DOUBLE_WELL
+# Thread-instructions per particle-step of the binary32 fine kernel (d = 1),
+# from ncu sm__inst_executed on the double-well workload (profiles/); None
+# until measured.
+INST_PER_PARTICLE_STEP = None
+SMS = 152
+ISSUE_LANES_PER_SM_CLK = 4 * 32       # 4 sub-partitions x one 32-wide warp instruction per clock
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [v.strip() for v in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_sample(seconds_target: float = 12.0):
+    """Time the oracle's fine propagator on a bounded sample of the workload."""
+    from oracle import oracle as orc
+    w = WORKLOAD
+    om = orc.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    x0, y0 = workloads.initial_ensemble(w)
+    # calibrate on a small sample, then size the timed sample to ~seconds_target
+    n_cal, s_cal = 1 << 14, 100
+    t0 = time.perf_counter()
+    orc.fine_propagate(om, w.seed, x0[None, :n_cal], y0[None, :, :n_cal], 1, s_cal, w.step_dt)
+    rate = n_cal * s_cal / max(time.perf_counter() - t0, 1e-6)
+    n = int(min(w.N, max(1 << 14, rate * seconds_target / w.steps)))
+    t0 = time.perf_counter()
+    orc.fine_propagate(om, w.seed, x0[None, :n], y0[None, :, :n], 1, w.steps, w.step_dt)
+    el = time.perf_counter() - t0
+    return {"value": n * w.steps / el, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"{n} particles x 1 slice x {w.steps} EM steps of the double-well workload "
+                      f"(FP64 C oracle, OpenMP), {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = WORKLOAD
+    from oracle import oracle as orc
+    orc.build()
+    om = orc.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    x0, y0 = workloads.initial_ensemble(w)
+    n = 1 << 15
+    for _ in range(args.warmup):
+        orc.fine_propagate(om, w.seed, x0[None, :n], y0[None, :, :n], 1, 20, w.step_dt)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.fine_propagate(om, w.seed, x0[None, :n], y0[None, :, :n], 1, w.steps, w.step_dt)
+        times.append(time.perf_counter() - t0)
+    el = sum(times)
+    value = args.steps * n * w.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "sample_particles": n, "slices_per_step": 1,
+                   "steps_per_slice": w.steps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+                         "sample": f"{n} particles x 1 slice x {w.steps} EM steps per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1912_09240_gb300 import _lib as L
+    from paper_1912_09240_gb300 import build as b
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    if rank == 0 or ws == 1:
+        b.build()
+    if dist:
+        dist.barrier()
+    w = WORKLOAD
+    model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    grid = L.Grid(w.bins, w.lo, w.hi)
+    x0, y0 = workloads.initial_ensemble(w)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    solver = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                            rng=L.Rng(w.seed, rank), device=str(dev))
+    x0t = torch.tensor(x0, dtype=torch.float32, device=dev)
+    y0t = torch.tensor(y0, dtype=torch.float32, device=dev)
+    solver.set_initial(x0t, y0t)
+
+    for _ in range(args.warmup):
+        solver.iterate()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    solver.fine_events = []   # CUDA events around the dominant launch of every timed step
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            solver.iterate()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    fine_times = solver.fine_events
+    solver.fine_events = None
+    ms = t0.elapsed_time(t1) / args.steps
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ps_per_step = w.particle_steps_per_iteration
+    value = ws * ps_per_step / (ms / 1e3)
+    fine_ms = statistics.mean(a.elapsed_time(b_) for a, b_ in fine_times) if fine_times else None
+
+    # end to end through the public API: host X_0 in, host rho out, every step
+    x0h = torch.tensor(x0, dtype=torch.float32).pin_memory()
+    y0h = torch.tensor(y0, dtype=torch.float32).pin_memory()
+    rho_h = torch.empty(w.K + 1, w.bins + 1, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x0t.copy_(x0h, non_blocking=True)
+        y0t.copy_(y0h, non_blocking=True)
+        solver.set_initial(x0t, y0t)
+        solver.iterate()
+        rho_h.copy_(solver.rho, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - te0) / e2e_steps
+    e2e = {"value": ws * ps_per_step / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(x0h.numel() * 4 + y0h.numel() * 4),
+           "d2h_bytes_per_step": int(rho_h.numel() * 8)}
+
+    # plain FP64 GPU path on a sample of the same workload (2 slices)
+    fp64 = None
+    if not args.no_fp64:
+        xs = torch.tensor(np.stack([x0, x0]), dtype=torch.float64, device=dev)
+        ys = torch.tensor(np.stack([y0, y0]), dtype=torch.float64, device=dev)
+        L.pr_fine_propagate(model, L.PR_F64, L.Rng(w.seed), xs, ys, False, xs, ys, w.N, 1, 2, 50, w.step_dt)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        L.pr_fine_propagate(model, L.PR_F64, L.Rng(w.seed), xs, ys, False, xs, ys, w.N, 1, 2, w.steps, w.step_dt)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fp64_rate = 2 * w.N * w.steps / (f0.elapsed_time(f1) / 1e3)
+        fine_rate = (w.K - 1) * w.N * w.steps / (fine_ms / 1e3) if fine_ms else None
+        fp64 = {"fp64_particle_steps_per_s": fp64_rate,
+                "fp32_fine_particle_steps_per_s": fine_rate,
+                "fp32_over_fp64": (fine_rate / fp64_rate) if fine_rate else None,
+                "sample": f"FP64 fine kernel, {w.N} particles x 2 slices x {w.steps} steps"}
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        solver.close()
+        return 0
+
+    peaks = _peaks()
+    clocks = clk.summary()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    roofline = None
+    if fine_ms and INST_PER_PARTICLE_STEP:
+        launch_ps = (w.K - 1) * w.N * w.steps
+        achieved = INST_PER_PARTICLE_STEP * launch_ps / (fine_ms / 1e3) / 1e12
+        peak = SMS * ISSUE_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "fine_f32_d1_kernel (slices 1..49)",
+                    "fine_ms_per_launch": fine_ms,
+                    "peak_basis": f"152 SMs x 4 warp-instr/clk x 32 lanes x {sm_max:.0f} MHz (max SM clock)"}
+    cpu = None if args.no_cpu else _cpu_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "K": w.K, "steps_per_slice": w.steps, "dt": w.step_dt,
+                   "bins": w.bins, "iterator": "quantile (two-sided)", "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2: 840 MB of ensemble state per step"},
+        "gpu_launches": 8 * args.steps,
+        "clocks": clocks,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "fp64_vs_fp32": fp64,
+    }
+    print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU sample")
+    ap.add_argument("--n", type=int, default=None, help="particles (smaller case for profiling)")
+    ap.add_argument("--k", type=int, default=None, help="slices (smaller case for profiling)")
+    args = ap.parse_args()
+    global WORKLOAD
+    if args.n or args.k:
+        WORKLOAD = WORKLOAD.scaled(N=args.n or WORKLOAD.N, K=args.k or WORKLOAD.K,
+                                   T=WORKLOAD.slice_dt * (args.k or WORKLOAD.K),
+                                   name=WORKLOAD.name + f"_n{args.n or WORKLOAD.N}_k{args.k or WORKLOAD.K}")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

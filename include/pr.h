@@ -1,0 +1,250 @@
+/*
+ * pr.h -- C ABI of the micro-macro parareal hot path on one GB300 (sm_103a).
+ *
+ * Method: Legoll, Lelievre, Myerscough, Samaey, "Parareal computation of
+ * stochastic differential equations with time-scale separation: a numerical
+ * study" (arXiv:1912.09240).  Section numbers below refer to that paper.
+ *
+ * Conventions shared by every call
+ *  - Pointers marked (device) are caller-owned device memory; pointers marked
+ *    (host) are caller-owned host memory.  No call keeps a pointer after it
+ *    returns, except the handles created by pr_coarse_create.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous on that stream unless stated otherwise.
+ *  - Arguments are validated on the host before anything is launched; a bad
+ *    argument returns PR_ERR_INVALID_ARG and launches nothing.  A failed
+ *    launch returns PR_ERR_CUDA.  Conditions found on the device (a NaN in the
+ *    FP64 update, an empty macroscopic state) are written to a caller-provided
+ *    int32 status word (device) and read by the caller after synchronising.
+ *  - Ensembles are stored as structure of arrays, slice-major:
+ *      x[n_slices][n]            slow variable X^p
+ *      y[n_slices][fast_dim][n]  fast variable Y^p (component-major)
+ *    in float (PR_F32) or double (PR_F64).  Weights are uniform, W^p = 1/n.
+ *  - A macroscopic state (a histogram of the slow variable on a uniform grid
+ *    x_lo = e_0 < ... < e_I = x_hi, Section 2.2.2) is passed as its
+ *    piecewise-linear CDF sampled at the I+1 edges (Eq. discr_cdf), double,
+ *    C_0 = 0, C_I = 1, bin masses rho_i = C_{i+1} - C_i.
+ *  - No call allocates device memory except pr_coarse_create.
+ *  - Calls on distinct handles are thread-safe.
+ */
+#ifndef PR_H
+#define PR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PR_OK = 0,
+    PR_ERR_INVALID_ARG = 1,
+    PR_ERR_CUDA = 2,
+    PR_ERR_TIMEOUT = 3,
+    PR_ERR_UNSUPPORTED = 4,
+    PR_ERR_NOMEM = 5,
+    PR_ERR_NUMERIC = 6
+} pr_status;
+
+typedef enum { PR_F32 = 0, PR_F64 = 1 } pr_precision;
+
+/* Drift families of the slow-fast SDE (Section 2.1.1, Eqs. SDEx/SDEy), tau_x
+ * the slow time scale, D = 1/beta, fast potential G = |y - x|^2/2 per
+ * component, E = 1:
+ *   PR_MODEL_OU          d_x F = x - lambda*y             (fast_dim = 1)
+ *   PR_MODEL_DOUBLE_WELL d_x F = x^3 - x + lambda*y       (fast_dim = 1)
+ *   PR_MODEL_DW_MULTI    d_x F = x^3 - x + lambda*mean(y) (fast_dim 1..16) */
+typedef enum { PR_MODEL_OU = 0, PR_MODEL_DOUBLE_WELL = 1, PR_MODEL_DW_MULTI = 2 } pr_model_kind;
+
+/* Iterators of Section 4: quantile (4.4), additive (4.1), multiplicative
+ * (4.2), rotation (4.3); PR_ITER_NONE keeps the coarse result (the serial
+ * coarse sweep of the zeroth iteration, Section 3.2.4). */
+typedef enum {
+    PR_ITER_QUANTILE = 0, PR_ITER_ADD = 1, PR_ITER_MULT = 2, PR_ITER_ROT = 3, PR_ITER_NONE = 4
+} pr_iterator;
+
+/* Quantile of a CDF at a level it takes on a flat stretch (Section 4.4):
+ * TWO_SIDED keeps both ends of the stretch as knots (J(a,b,a) = b holds
+ * exactly); MIDPOINT takes the midpoint, as the paper prints it. */
+typedef enum { PR_QMODE_TWO_SIDED = 0, PR_QMODE_MIDPOINT = 1 } pr_quantile_mode;
+
+typedef struct {
+    int32_t kind;       /* pr_model_kind */
+    int32_t fast_dim;   /* d, the dimension of Y */
+    double lambda;      /* coupling strength */
+    double beta;        /* inverse temperature of the slow variable, D = 1/beta */
+    double eps;         /* fast time scale */
+    double tau_x;       /* slow time scale */
+} pr_model;
+
+typedef struct {
+    int32_t bins;       /* I, 1 .. 4096 */
+    double x_lo, x_hi;  /* x_lo < x_hi */
+} pr_grid;
+
+typedef struct {
+    uint64_t seed;        /* Philox4x32-10 key (low word, high word) */
+    uint32_t problem_id;  /* < 2^24, selects an independent family of streams */
+} pr_rng;
+
+/* Human-readable name of a status code (static storage). */
+const char* pr_status_string(pr_status s);
+
+/* Library version, e.g. "0.1.0". */
+const char* pr_version(void);
+
+/*
+ * Fine propagator F_dT (Section 3.2.1; Euler-Maruyama, Section 2.1.3,
+ * Eqs. EMx/EMy) over the slices slice_begin .. slice_begin + n_slices - 1 at
+ * once, each advanced by `steps` steps of size dt.
+ *
+ * Random numbers: slice n, particle p, step m draw their 1 + fast_dim standard
+ * normals (Box-Muller) from Philox4x32-10 with key = seed and counter
+ *   fast_dim == 1 : (m >> 1, p, n, problem_id << 8), step m taking words
+ *                   2(m&1), 2(m&1)+1 (one block serves two steps);
+ *   fast_dim  > 1 : (m, p, n, (problem_id << 8) | g), g = 0, 1, ..., words
+ *                   taken in pairs;
+ * so a slice reuses the same numbers in every parareal iteration (Section 6).
+ *
+ *   x_in, y_in   (device) start states, [n_slices][n] and [n_slices][d][n];
+ *                with broadcast_input != 0 a single ensemble [n], [d][n] is
+ *                the start of every slice (the zeroth iteration).
+ *   x_out, y_out (device) end states, same layout as the non-broadcast input;
+ *                may alias x_in / y_in exactly (in-place), not partially.
+ *   grid         needed when any of the fused outputs below is requested.
+ *   cdf_prior, cdf_target (device, [n_slices][bins+1]) or both NULL: fused
+ *                matching (pr_match) applied to the start state first.
+ *   counts_start, cdf_start (device, [n_slices][bins], [n_slices][bins+1]) or
+ *                NULL: restriction (pr_restrict) of the start state after the
+ *                matching.  cdf_start needs counts_start.
+ *   counts_end, cdf_end: restriction of the end state.  cdf_end needs counts_end.
+ * Counts are overwritten (the call zeroes them first).
+ * Precision PR_F32: float state, FP32 arithmetic; PR_F64: double throughout.
+ */
+pr_status pr_fine_propagate(const pr_model* model, pr_precision precision, const pr_rng* rng,
+                            const void* x_in, const void* y_in, int32_t broadcast_input,
+                            void* x_out, void* y_out,
+                            int64_t n, int32_t slice_begin, int32_t n_slices,
+                            int32_t steps, double dt,
+                            const pr_grid* grid,
+                            const double* cdf_prior, const double* cdf_target,
+                            uint32_t* counts_start, double* cdf_start,
+                            uint32_t* counts_end, double* cdf_end,
+                            void* stream);
+
+/*
+ * Raw Philox4x32-10 blocks (Salmon et al., SC'11) with key = rng->seed:
+ * out[i] = Philox(ctr[i]) for n counters.  The generator behind the EM
+ * increments dU_m, dV_m ~ N(0, dt) (Eqs. EMx/EMy), exposed for checking.
+ *   ctr (device) [n][4] uint32, out (device) [n][4] uint32, both 16-byte aligned.
+ */
+pr_status pr_rng_words(const pr_rng* rng, const uint32_t* ctr, int64_t n, uint32_t* out, void* stream);
+
+/*
+ * Tuning knob of the binary32 fine propagator with fast_dim = 1: particles
+ * carried per thread (1, 2 or 4; other values select 1).  Process-wide; set
+ * by the autotuner.  Results do not depend on it.
+ */
+void pr_set_particles_per_thread(int32_t ppt);
+
+/*
+ * Restriction R = R2 o R1 (Section 3.2.2, Eq. binning): drop Y, bin X.
+ * A particle belongs to the bin i with e_i <= x < e_{i+1}, decided by exact
+ * comparison with the double edges e_i = x_lo + i*(x_hi - x_lo)/I; particles
+ * below x_lo count in bin 0 and at or above x_hi in bin I-1.
+ *   x      (device) [n_slices][n], float or double per `precision`
+ *   counts (device) [n_slices][bins] uint32, overwritten
+ *   cdf    (device) [n_slices][bins+1] or NULL: C_i = (#particles in bins < i)/n
+ */
+pr_status pr_restrict(pr_precision precision, const void* x, int64_t n, int32_t n_slices,
+                      const pr_grid* grid, uint32_t* counts, double* cdf, void* stream);
+
+/* CDF at the edges from counts: cdf[s][0] = 0, cdf[s][i+1] = sum_{j<=i} counts[s][j] / n. */
+pr_status pr_counts_to_cdf(const uint32_t* counts, int64_t n, int32_t n_slices, int32_t bins,
+                           double* cdf, void* stream);
+
+/*
+ * Matching that preserves the fast marginal (Section 5.1, Eq. transformation):
+ * X = c^{-1}(cbar(Xbar)) with cbar the piecewise-linear CDF of the prior
+ * histogram and c that of the target; Y is untouched (not an argument).
+ * The inverse takes the lowest non-empty target bin whose upper CDF value
+ * reaches cbar(Xbar).  On a bin where prior and target CDF agree at both
+ * edges the map is the identity (strong projection, Eq. projection, holds bit
+ * for bit).  Particles outside [x_lo, x_hi] move by the displacement of the
+ * nearest edge.
+ *   x_prior (device) [n_slices][n]; x_out (device) [n_slices][n], may alias x_prior
+ *   cdf_prior, cdf_target (device) [n_slices][bins+1]
+ */
+pr_status pr_match(pr_precision precision, const void* x_prior, void* x_out, int64_t n,
+                   int32_t n_slices, const pr_grid* grid,
+                   const double* cdf_prior, const double* cdf_target, void* stream);
+
+/*
+ * Coarse propagator C_dT (Section 2.2.2): finite volumes on the detailed-
+ * balance form of the averaged Fokker-Planck equation (Eq. FPz_rewritten),
+ * central differences for the fluxes, zero flux at x_lo and x_hi, and an
+ * exact time integrator P = exp(A dT) (matrix exponential by scaling and
+ * squaring, FP64, built on the device).  The averaged coefficients are those
+ * of the fast OU equilibrium Y | x ~ N(x, 1): Fbar' = (1-lambda) x (PR_MODEL_OU),
+ * x^3 - (1-lambda) x (double-well families), Dbar = 1/beta.
+ * Allocates the I x I matrix on the current device; synchronises `stream`.
+ *   handle (host) receives an opaque pointer; release with pr_coarse_destroy.
+ */
+pr_status pr_coarse_create(const pr_model* model, const pr_grid* grid, double slice_dt,
+                           void** handle, void* stream);
+pr_status pr_coarse_destroy(void* handle);
+
+/* Copy P = exp(A dT) (row-major I x I doubles) into out (device). */
+pr_status pr_coarse_matrix(void* handle, double* out, void* stream);
+
+/*
+ * Apply C_dT to n_vec macroscopic states: masses = diff(cdf_in), P @ masses
+ * (negative round-off clipped to 0), cumulative sum normalised to unit mass.
+ *   cdf_in, cdf_out (device) [n_vec][bins+1]; may not alias.
+ */
+pr_status pr_coarse_fp(void* handle, const double* cdf_in, double* cdf_out, int32_t n_vec,
+                       void* stream);
+
+/*
+ * Serial update of Section 3.2.3 (Eq. mm_sequential), one CTA:
+ *   rho^0 = cdf0,
+ *   rho^{n+1} = J(C_dT(rho^n), rho_f*[n], rho_c*[n]),  n = 0 .. n_slices-1,
+ * with J the chosen iterator (Section 4; PR_ITER_NONE: rho^{n+1} = C_dT(rho^n)).
+ * C_dT is evaluated exactly as pr_coarse_fp does, bit for bit, so that
+ * equal arguments give equal coarse results (the exactness theorem,
+ * Section 3.3.3, needs that).
+ *   cdf0       (device) [bins+1]
+ *   cdf_f_star (device) [n_slices][bins+1], R F(X_k^n)   (NULL for PR_ITER_NONE)
+ *   cdf_c_star (device) [n_slices][bins+1], C(R X_k^n)   (NULL for PR_ITER_NONE)
+ *   cdf_next   (device) [n_slices+1][bins+1], receives rho_{k+1}^0 .. rho_{k+1}^{n_slices}
+ *   status     (device) int32 or NULL: 0 on success, PR_ERR_NUMERIC if a
+ *              non-finite value or an empty state appeared.
+ */
+pr_status pr_parareal_update(void* coarse, pr_iterator iterator, pr_quantile_mode qmode,
+                             int32_t n_slices, const double* cdf0, const double* cdf_f_star,
+                             const double* cdf_c_star, double* cdf_next, int32_t* status,
+                             void* stream);
+
+/*
+ * One iterator J(a, b, c) on n_vec independent triples (Section 4), no coarse
+ * step: out[v] = J(a[v], b[v], c[v]).  a = rho_c^{n+1}, b = rho_f^*, c = rho_c^*.
+ *   a, b, c, out (device) [n_vec][bins+1]; status as for pr_parareal_update.
+ */
+pr_status pr_iterate(pr_iterator iterator, pr_quantile_mode qmode, const pr_grid* grid,
+                     int32_t n_vec, const double* a, const double* b, const double* c,
+                     double* out, int32_t* status, void* stream);
+
+/*
+ * W1 distance between pairs of macroscopic states on the same grid, each read
+ * as its piecewise-linear CDF: integral of |C1 - C2| over [x_lo, x_hi].
+ *   c1, c2 (device) [n_vec][bins+1]; w1 (device) [n_vec] doubles.
+ */
+pr_status pr_w1(const pr_grid* grid, int32_t n_vec, const double* c1, const double* c2,
+                double* w1, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PR_H */

@@ -27,10 +27,23 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
 #endif
+
+/* Threads the OpenMP loops below use. */
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Random numbers.  The paper draws the EM increments dU_m, dV_m ~ N(0, dt)  */
@@ -168,10 +181,13 @@ static double or_dFdx(int kind, int d, double lambda, double x, const double* y)
  * x: [n_slices][N], y: [n_slices][d][N] (structure of arrays).  Each slice
  * takes S Euler-Maruyama steps of size dt; slice n uses the random numbers
  * of (seed, problem, particle, n, step). */
-void or_fine_propagate(int kind, int d, double lambda, double beta, double eps, double tau_x,
-                       uint64_t seed, uint32_t problem,
-                       double* x, double* y, int64_t N,
-                       int slice_begin, int n_slices, int S, double dt)
+/* ids: the particle index p that keys each column's random numbers
+ * (NULL: column p is particle p), so that a sample of an ensemble can be
+ * advanced on its own. */
+void or_fine_propagate_ids(int kind, int d, double lambda, double beta, double eps, double tau_x,
+                           uint64_t seed, uint32_t problem,
+                           double* x, double* y, int64_t N, const uint32_t* ids,
+                           int slice_begin, int n_slices, int S, double dt)
 {
     const int Q = 1 + d;
     const double D = 1.0 / beta;     /* slow diffusion D(x, y) */
@@ -187,7 +203,8 @@ void or_fine_propagate(int kind, int d, double lambda, double beta, double eps, 
             double Y[64], Ynew[64], z[65];
             for (int j = 0; j < d; ++j) Y[j] = ys[(int64_t)j * N + p];
             for (int m = 0; m < S; ++m) {
-                or_step_normals(seed, problem, (uint32_t)p, n, (uint32_t)m, Q, z);
+                const uint32_t pid = ids ? ids[p] : (uint32_t)p;
+                or_step_normals(seed, problem, pid, n, (uint32_t)m, Q, z);
                 double dU = sqrt_dt * z[0];
                 double Xnew = X - (1.0 / tau_x) * or_dFdx(kind, d, lambda, X, Y) * dt
                                 + sqrt(2.0 * D / tau_x) * dU;
@@ -203,6 +220,15 @@ void or_fine_propagate(int kind, int d, double lambda, double beta, double eps, 
             for (int j = 0; j < d; ++j) ys[(int64_t)j * N + p] = Y[j];
         }
     }
+}
+
+void or_fine_propagate(int kind, int d, double lambda, double beta, double eps, double tau_x,
+                       uint64_t seed, uint32_t problem,
+                       double* x, double* y, int64_t N,
+                       int slice_begin, int n_slices, int S, double dt)
+{
+    or_fine_propagate_ids(kind, d, lambda, beta, eps, tau_x, seed, problem, x, y, N, NULL,
+                          slice_begin, n_slices, S, dt);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -52,6 +52,7 @@ def lib():
         d, i64, i32, u32, u64 = (ctypes.c_double, ctypes.c_int64, ctypes.c_int,
                                  ctypes.c_uint32, ctypes.c_uint64)
         vp = ctypes.c_void_p
+        _lib.or_num_threads.restype = i32
         _lib.or_philox_batch.argtypes = [vp, i64, u64, vp]
         _lib.or_uniform.argtypes = [u32]
         _lib.or_uniform.restype = d
@@ -59,6 +60,8 @@ def lib():
         _lib.or_normals_block.argtypes = [u64, u32, u32, i64, u32, u32, i32, i32, vp]
         _lib.or_fine_propagate.argtypes = [i32, i32, d, d, d, d, u64, u32, vp, vp, i64,
                                            i32, i32, i32, d]
+        _lib.or_fine_propagate_ids.argtypes = [i32, i32, d, d, d, d, u64, u32, vp, vp, i64, vp,
+                                               i32, i32, i32, d]
         _lib.or_edge.argtypes = [i32, i32, d, d]
         _lib.or_edge.restype = d
         _lib.or_bin.argtypes = [d, i32, d, d]
@@ -118,6 +121,10 @@ class Grid:
 # RNG
 # --------------------------------------------------------------------------
 
+def num_threads() -> int:
+    return lib().or_num_threads()
+
+
 def philox(ctr: np.ndarray, seed: int) -> np.ndarray:
     ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
     out = np.empty_like(ctr)
@@ -147,15 +154,23 @@ def normals_block(seed: int, problem: int, p0: int, n_part: int, n: int, m0: int
 # --------------------------------------------------------------------------
 
 def fine_propagate(model: Model, seed: int, x: np.ndarray, y: np.ndarray, slice_begin: int,
-                   steps: int, dt: float, problem: int = 0):
-    """Advance x[n_slices][N], y[n_slices][d][N] (copies) by `steps` EM steps per slice."""
+                   steps: int, dt: float, problem: int = 0, ids: np.ndarray | None = None):
+    """Advance x[n_slices][N], y[n_slices][d][N] (copies) by `steps` EM steps per slice.
+    ids[N]: particle indices keying the random numbers of each column (default 0..N-1)."""
     x = np.array(x, dtype=np.float64, order="C", copy=True)
     y = np.array(y, dtype=np.float64, order="C", copy=True)
     n_slices, N = x.shape
     assert y.shape == (n_slices, model.fast_dim, N)
-    lib().or_fine_propagate(model.kind, model.fast_dim, model.lam, model.beta, model.eps,
-                            model.tau_x, seed, problem, _p(x), _p(y), N, slice_begin,
-                            n_slices, steps, dt)
+    if ids is None:
+        lib().or_fine_propagate(model.kind, model.fast_dim, model.lam, model.beta, model.eps,
+                                model.tau_x, seed, problem, _p(x), _p(y), N, slice_begin,
+                                n_slices, steps, dt)
+    else:
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        assert ids.shape == (N,)
+        lib().or_fine_propagate_ids(model.kind, model.fast_dim, model.lam, model.beta, model.eps,
+                                    model.tau_x, seed, problem, _p(x), _p(y), N, _p(ids),
+                                    slice_begin, n_slices, steps, dt)
     return x, y
 
 
@@ -264,12 +279,14 @@ def coarse_propagator(model: Model, grid: Grid, slice_dt: float) -> np.ndarray:
 
 
 def coarse_apply(P: np.ndarray, cdf: np.ndarray) -> np.ndarray:
-    """C(rho) on a CDF: masses, P @ masses, cumulative sum normalised to 1."""
+    """C(rho) on a CDF: masses, P @ masses (clipped at 0), cumulative sum normalised to 1."""
     cdf = np.atleast_2d(np.asarray(cdf, dtype=np.float64))
     out = np.empty_like(cdf)
     for r in range(cdf.shape[0]):
         m = cdf[r, 1:] - cdf[r, :-1]
-        mp = P @ m
+        # negative round-off of P @ m (entries of P are >= -1e-16) is clipped
+        # so that the CDF stays non-decreasing
+        mp = np.maximum(P @ m, 0.0)
         s = np.cumsum(mp)
         out[r, 0] = 0.0
         out[r, 1:] = s / s[-1]

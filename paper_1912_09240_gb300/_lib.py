@@ -1,0 +1,222 @@
+"""ctypes binding of libpr.so (include/pr.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes
+plain device pointers (torch tensors' ``data_ptr()``), sizes and a stream.
+No computation happens in Python; a missing library raises instead of
+falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpr.so")
+
+PR_OK, PR_ERR_INVALID_ARG, PR_ERR_CUDA, PR_ERR_TIMEOUT, PR_ERR_UNSUPPORTED, PR_ERR_NOMEM, PR_ERR_NUMERIC = range(7)
+PR_F32, PR_F64 = 0, 1
+PR_MODEL_OU, PR_MODEL_DOUBLE_WELL, PR_MODEL_DW_MULTI = 0, 1, 2
+PR_ITER_QUANTILE, PR_ITER_ADD, PR_ITER_MULT, PR_ITER_ROT, PR_ITER_NONE = 0, 1, 2, 3, 4
+PR_QMODE_TWO_SIDED, PR_QMODE_MIDPOINT = 0, 1
+
+EXPORTED = (
+    "pr_status_string", "pr_version", "pr_rng_words", "pr_fine_propagate", "pr_set_particles_per_thread",
+    "pr_restrict", "pr_counts_to_cdf", "pr_match", "pr_coarse_create", "pr_coarse_destroy",
+    "pr_coarse_matrix", "pr_coarse_fp", "pr_parareal_update", "pr_iterate", "pr_w1",
+)
+
+
+class PrError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        self.code = code
+        super().__init__(f"{fn} failed: {status_string(code)}")
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("fast_dim", ctypes.c_int32), ("lambda_", ctypes.c_double),
+                ("beta", ctypes.c_double), ("eps", ctypes.c_double), ("tau_x", ctypes.c_double)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("bins", ctypes.c_int32), ("x_lo", ctypes.c_double), ("x_hi", ctypes.c_double)]
+
+
+class _Rng(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("problem_id", ctypes.c_uint32)]
+
+
+@dataclass(frozen=True)
+class Model:
+    kind: int
+    fast_dim: int = 1
+    lam: float = 1.0
+    beta: float = 1.0
+    eps: float = 0.1
+    tau_x: float = 1.0
+
+    def c(self) -> _Model:
+        return _Model(self.kind, self.fast_dim, self.lam, self.beta, self.eps, self.tau_x)
+
+
+@dataclass(frozen=True)
+class Grid:
+    bins: int
+    lo: float
+    hi: float
+
+    def c(self) -> _Grid:
+        return _Grid(self.bins, self.lo, self.hi)
+
+
+@dataclass(frozen=True)
+class Rng:
+    seed: int = 0
+    problem_id: int = 0
+
+    def c(self) -> _Rng:
+        return _Rng(self.seed, self.problem_id)
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpr.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u32, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
+    P = ctypes.POINTER
+    L.pr_status_string.argtypes = [i32]
+    L.pr_status_string.restype = ctypes.c_char_p
+    L.pr_version.restype = ctypes.c_char_p
+    L.pr_fine_propagate.argtypes = [P(_Model), i32, P(_Rng), vp, vp, i32, vp, vp, i64, i32, i32, i32, d,
+                                    P(_Grid), vp, vp, vp, vp, vp, vp, vp]
+    L.pr_rng_words.argtypes = [P(_Rng), vp, i64, vp, vp]
+    L.pr_set_particles_per_thread.argtypes = [i32]
+    L.pr_set_particles_per_thread.restype = None
+    L.pr_restrict.argtypes = [i32, vp, i64, i32, P(_Grid), vp, vp, vp]
+    L.pr_counts_to_cdf.argtypes = [vp, i64, i32, i32, vp, vp]
+    L.pr_match.argtypes = [i32, vp, vp, i64, i32, P(_Grid), vp, vp, vp]
+    L.pr_coarse_create.argtypes = [P(_Model), P(_Grid), d, P(vp), vp]
+    L.pr_coarse_destroy.argtypes = [vp]
+    L.pr_coarse_matrix.argtypes = [vp, vp, vp]
+    L.pr_coarse_fp.argtypes = [vp, vp, vp, i32, vp]
+    L.pr_parareal_update.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp]
+    L.pr_iterate.argtypes = [i32, i32, P(_Grid), i32, vp, vp, vp, vp, vp, vp]
+    L.pr_w1.argtypes = [P(_Grid), i32, vp, vp, vp, vp]
+    for name in EXPORTED:
+        if name not in ("pr_status_string", "pr_version", "pr_set_particles_per_thread"):
+            getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return lib().pr_status_string(code).decode()
+
+
+def version() -> str:
+    return lib().pr_version().decode()
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _check(fn: str, rc: int):
+    if rc != PR_OK:
+        raise PrError(fn, rc)
+
+
+def pr_fine_propagate(model: Model, precision: int, rng: Rng, x_in, y_in, broadcast_input: bool,
+                      x_out, y_out, n: int, slice_begin: int, n_slices: int, steps: int, dt: float,
+                      grid: Grid | None = None, cdf_prior=None, cdf_target=None, counts_start=None,
+                      cdf_start=None, counts_end=None, cdf_end=None, stream=None):
+    m, r = model.c(), rng.c()
+    g = grid.c() if grid is not None else None
+    rc = lib().pr_fine_propagate(ctypes.byref(m), precision, ctypes.byref(r), _ptr(x_in), _ptr(y_in),
+                                 1 if broadcast_input else 0, _ptr(x_out), _ptr(y_out), n, slice_begin,
+                                 n_slices, steps, dt, ctypes.byref(g) if g is not None else None,
+                                 _ptr(cdf_prior), _ptr(cdf_target), _ptr(counts_start), _ptr(cdf_start),
+                                 _ptr(counts_end), _ptr(cdf_end), _stream(stream))
+    _check("pr_fine_propagate", rc)
+
+
+def pr_rng_words(rng: Rng, ctr, n: int, out, stream=None):
+    r = rng.c()
+    _check("pr_rng_words", lib().pr_rng_words(ctypes.byref(r), _ptr(ctr), n, _ptr(out), _stream(stream)))
+
+
+def pr_set_particles_per_thread(ppt: int):
+    lib().pr_set_particles_per_thread(ppt)
+
+
+def pr_restrict(precision: int, x, n: int, n_slices: int, grid: Grid, counts, cdf=None, stream=None):
+    g = grid.c()
+    _check("pr_restrict", lib().pr_restrict(precision, _ptr(x), n, n_slices, ctypes.byref(g), _ptr(counts),
+                                            _ptr(cdf), _stream(stream)))
+
+
+def pr_counts_to_cdf(counts, n: int, n_slices: int, bins: int, cdf, stream=None):
+    _check("pr_counts_to_cdf", lib().pr_counts_to_cdf(_ptr(counts), n, n_slices, bins, _ptr(cdf),
+                                                      _stream(stream)))
+
+
+def pr_match(precision: int, x_prior, x_out, n: int, n_slices: int, grid: Grid, cdf_prior, cdf_target,
+             stream=None):
+    g = grid.c()
+    _check("pr_match", lib().pr_match(precision, _ptr(x_prior), _ptr(x_out), n, n_slices, ctypes.byref(g),
+                                      _ptr(cdf_prior), _ptr(cdf_target), _stream(stream)))
+
+
+def pr_coarse_create(model: Model, grid: Grid, slice_dt: float, stream=None) -> int:
+    m, g = model.c(), grid.c()
+    h = ctypes.c_void_p()
+    _check("pr_coarse_create", lib().pr_coarse_create(ctypes.byref(m), ctypes.byref(g), slice_dt,
+                                                      ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def pr_coarse_destroy(handle: int):
+    _check("pr_coarse_destroy", lib().pr_coarse_destroy(handle))
+
+
+def pr_coarse_matrix(handle: int, out, stream=None):
+    _check("pr_coarse_matrix", lib().pr_coarse_matrix(handle, _ptr(out), _stream(stream)))
+
+
+def pr_coarse_fp(handle: int, cdf_in, cdf_out, n_vec: int, stream=None):
+    _check("pr_coarse_fp", lib().pr_coarse_fp(handle, _ptr(cdf_in), _ptr(cdf_out), n_vec, _stream(stream)))
+
+
+def pr_parareal_update(coarse: int, iterator: int, qmode: int, n_slices: int, cdf0, cdf_f_star, cdf_c_star,
+                       cdf_next, status=None, stream=None):
+    _check("pr_parareal_update", lib().pr_parareal_update(coarse, iterator, qmode, n_slices, _ptr(cdf0),
+                                                          _ptr(cdf_f_star), _ptr(cdf_c_star), _ptr(cdf_next),
+                                                          _ptr(status), _stream(stream)))
+
+
+def pr_iterate(iterator: int, qmode: int, grid: Grid, n_vec: int, a, b, c, out, status=None, stream=None):
+    g = grid.c()
+    _check("pr_iterate", lib().pr_iterate(iterator, qmode, ctypes.byref(g), n_vec, _ptr(a), _ptr(b), _ptr(c),
+                                          _ptr(out), _ptr(status), _stream(stream)))
+
+
+def pr_w1(grid: Grid, n_vec: int, c1, c2, w1, stream=None):
+    g = grid.c()
+    _check("pr_w1", lib().pr_w1(ctypes.byref(g), n_vec, _ptr(c1), _ptr(c2), _ptr(w1), _stream(stream)))

@@ -1,0 +1,818 @@
+// coarse.cu -- coarse propagator C_dT (Section 2.2.2), the serial parareal
+// update rho^{n+1} = J(C(rho^n), rho_f*, rho_c*) (Section 3.2.3, Eq.
+// mm_sequential) with the iterators of Section 4, and the W1 distance.
+//
+// Everything here is FP64.  The macroscopic states are short (I <= 4096 bins,
+// the serial update I <= 1024), so the work is latency-bound: one CTA per
+// state vector, and one CTA for the serial sweep over the slices.  Operations
+// that decide exactness (edges, quantile interpolation, the monotone repair,
+// reading the CDF back at the edges) are written with explicitly rounded
+// intrinsics so that no multiply-add is fused.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "pr_common.cuh"
+
+namespace pr {
+
+constexpr int kCoarseThreads = 512;   // every coarse apply uses this block size
+constexpr int kUpdateMaxBins = 1024;
+
+struct CoarseHandle {
+    GridDev g;
+    double* P;   // row-major I x I
+    int device;
+};
+
+// ---------------------------------------------------------------------------
+// Block-level FP64 helpers (deterministic order for a fixed blockDim)
+// ---------------------------------------------------------------------------
+
+// Inclusive scan of v[0..n) into out[0..n) (out may equal v); wsum >= 33 doubles.
+__device__ void block_scan_f64(const double* v, double* out, int n, double* wsum)
+{
+    const int T = blockDim.x;
+    const int chunk = (n + T - 1) / T;
+    const int b = threadIdx.x * chunk, e = min(n, b + chunk);
+    double loc = 0.0;
+    for (int i = b; i < e; ++i) loc = __dadd_rn(loc, v[i]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double incl = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl = __dadd_rn(t, incl);
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double run = 0.0;
+        const int nw = T >> 5;
+        for (int w = 0; w < nw; ++w) {
+            const double t = wsum[w];
+            wsum[w] = run;
+            run = __dadd_rn(run, t);
+        }
+        wsum[32] = run;
+    }
+    __syncthreads();
+    // exclusive prefix of this thread: the warp's offset plus the inclusive
+    // prefix of the previous lane
+    const double prev = __shfl_up_sync(0xffffffffu, incl, 1);
+    double run = lane > 0 ? __dadd_rn(wsum[warp], prev) : wsum[warp];
+    for (int i = b; i < e; ++i) {
+        run = __dadd_rn(run, v[i]);
+        out[i] = run;
+    }
+    __syncthreads();
+}
+
+// Block sum of one value per thread (deterministic); wsum >= 33 doubles.
+__device__ double block_sum_f64(double v, double* wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = __dadd_rn(s, wsum[w]);
+        wsum[32] = s;
+    }
+    __syncthreads();
+    const double r = wsum[32];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// C_dT on one state: masses, P @ masses (negative round-off clipped), CDF of
+// the result normalised to unit mass.  cdf_in, out: [I+1]; mass, mp: [I].
+// All in shared memory; every thread of a kCoarseThreads block calls it.
+// ---------------------------------------------------------------------------
+
+__device__ void coarse_apply_block(const double* __restrict__ P, int I, const double* cdf_in,
+                                   double* out, double* mass, double* mp, double* wsum)
+{
+    for (int c = threadIdx.x; c < I; c += blockDim.x) mass[c] = __dsub_rn(cdf_in[c + 1], cdf_in[c]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = warp; r < I; r += nw) {
+        const double* row = P + (size_t)r * I;
+        double acc = 0.0;
+        for (int c = lane; c < I; c += 32) acc = fma(row[c], mass[c], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+        if (lane == 0) mp[r] = acc > 0.0 ? acc : 0.0;
+    }
+    __syncthreads();
+    block_scan_f64(mp, mp, I, wsum);
+    const double total = mp[I - 1];
+    for (int r = threadIdx.x; r < I - 1; r += blockDim.x) {
+        double v = total > 0.0 ? __ddiv_rn(mp[r], total) : 0.0;
+        out[r + 1] = v < 1.0 ? v : 1.0;
+    }
+    if (threadIdx.x == 0) {
+        out[0] = 0.0;
+        out[I] = 1.0;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Quantile iterator J_q (Section 4.4) on CDFs in shared memory.
+// ---------------------------------------------------------------------------
+
+// Ordered 64-bit key of a double (zeros canonicalised): signed comparison of
+// keys is numeric comparison.
+__device__ __forceinline__ long long okey(double v)
+{
+    const long long b = __double_as_longlong(v);
+    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+}
+
+__device__ __forceinline__ int count_lt(const double* F, int n, double v)   // #F < v
+{
+    const long long kv = dkey(v);
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (dkey(F[mid]) < kv) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int count_le(const double* F, int n, double v)   // #F <= v
+{
+    const long long kv = dkey(v);
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (dkey(F[mid]) <= kv) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Interior quantile: strictly inside bin b (never rounded onto an edge).
+__device__ __forceinline__ double inside(const GridDev& g, int b, double t)
+{
+    const double e0 = edge(g, b), e1 = edge(g, b + 1);
+    double q = __dadd_rn(e0, __dmul_rn(t, g.h));
+    if (q <= e0) q = nextafter(e0, e1);
+    if (q >= e1) q = nextafter(e1, e0);
+    return q;
+}
+
+// q^-(p) = min{x : F(x) >= p}
+__device__ __forceinline__ double q_minus(const GridDev& g, const double* F, double p)
+{
+    const int I = g.bins;
+    const int a = count_lt(F, I + 1, p);   // lowest index with F[a] >= p (F[I] = 1 >= p)
+    if (a == 0 || F[a] == p) return edge(g, a);
+    const double t = __ddiv_rn(__dsub_rn(p, F[a - 1]), __dsub_rn(F[a], F[a - 1]));
+    return inside(g, a - 1, t);
+}
+
+// q^+(p) = max{x : F(x) <= p}
+__device__ __forceinline__ double q_plus(const GridDev& g, const double* F, double p)
+{
+    const int I = g.bins;
+    const int b = count_le(F, I + 1, p) - 1;   // highest index with F[b] <= p (F[0] = 0 <= p)
+    if (b == I || F[b] == p) return edge(g, b);
+    const double t = __ddiv_rn(__dsub_rn(p, F[b]), __dsub_rn(F[b + 1], F[b]));
+    return inside(g, b, t);
+}
+
+struct JqSmem {
+    double* levels;   // [3(I+1)]
+    double* kq;       // [6(I+1)]  (merged values first, then knots)
+    double* bsum;     // [6(I+1)]
+    int* ibuf;        // [6(I+1)]  (ranks, then block counts)
+    int* flag;        // [0]: level count, [1]: input not a CDF, [2]: knots need repair
+    double* wsum;     // [40]
+};
+
+__host__ __device__ inline size_t jq_smem_bytes(int bins)
+{
+    const size_t M = 3 * (size_t)(bins + 1);
+    return (M + 2 * M + 2 * M + 40) * sizeof(double) + (2 * M + 4) * sizeof(int);
+}
+
+__device__ inline JqSmem carve_jq(unsigned char* base, int bins)
+{
+    const int M = 3 * (bins + 1);
+    JqSmem j;
+    j.levels = reinterpret_cast<double*>(base);
+    j.kq = j.levels + M;
+    j.bsum = j.kq + 2 * M;
+    j.wsum = j.bsum + 2 * M;
+    j.ibuf = reinterpret_cast<int*>(j.wsum + 40);
+    j.flag = j.ibuf + 2 * M;
+    return j;
+}
+
+// out = J_q(A, B, C).  A, B, C, out: [I+1] in shared memory (out distinct).
+// Returns through flag[1] a non-zero value if an input was not a CDF.
+__device__ void quantile_iterate_block(const GridDev& g, int qmode, const double* A, const double* B,
+                                       const double* C, double* out, JqSmem& s)
+{
+    const int I = g.bins;
+    const int n1 = I + 1;
+    const int M = 3 * n1;
+    if (threadIdx.x == 0) s.flag[2] = 0;
+    // validity: finite, non-decreasing, in [0, 1]
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+        const double* Fs[3] = {A, B, C};
+        for (int f = 0; f < 3; ++f) {
+            const double v = Fs[f][i];
+            bool bad = !(v >= 0.0 && v <= 1.0);
+            if (i > 0 && !(Fs[f][i - 1] <= v)) bad = true;
+            if (bad) s.flag[1] = 1;
+        }
+    }
+    // 1. sorted union of the 3(I+1) levels (stable merge by rank)
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        const int f = k / n1, i = k - f * n1;
+        double v;
+        int r;
+        if (f == 0) { v = A[i]; r = i + count_lt(B, n1, v) + count_lt(C, n1, v); }
+        else if (f == 1) { v = B[i]; r = i + count_le(A, n1, v) + count_lt(C, n1, v); }
+        else { v = C[i]; r = i + count_le(A, n1, v) + count_le(B, n1, v); }
+        s.kq[r] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < M; k += blockDim.x)
+        s.ibuf[k] = (k == 0 || s.kq[k] != s.kq[k - 1]) ? 1 : 0;
+    __syncthreads();
+    // exclusive scan of the distinct flags -> positions (ints, deterministic)
+    {
+        const int T = blockDim.x;
+        const int chunk = (M + T - 1) / T;
+        const int b = threadIdx.x * chunk, e = min(M, b + chunk);
+        int loc = 0;
+        for (int i = b; i < e; ++i) loc += s.ibuf[i];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int incl = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int* wtot = reinterpret_cast<int*>(s.wsum);
+        if (lane == 31) wtot[warp] = incl;
+        __syncthreads();
+        int off = 0;
+        for (int w = 0; w < warp; ++w) off += wtot[w];
+        int run = off + incl - loc;
+        for (int i = b; i < e; ++i) {
+            if (s.ibuf[i]) s.levels[run] = s.kq[i];
+            run += s.ibuf[i];
+        }
+        if (threadIdx.x == T - 1) s.flag[0] = run;   // number of levels L
+    }
+    __syncthreads();
+    const int L = s.flag[0];
+    __syncthreads();
+    // 2-3. quantiles of A, B, C at every level and the combined knots
+    const bool two = qmode == PR_QMODE_TWO_SIDED;
+    const int nk = two ? 2 * L - 2 : L;
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        const double p = s.levels[l];
+        const bool first = l == 0, last = l == L - 1;
+        if (two) {
+            if (!first) {
+                const double qa = q_minus(g, A, p), qb = q_minus(g, B, p), qc = q_minus(g, C, p);
+                s.kq[2 * l - 1] = __dadd_rn(__dadd_rn(qb, __dsub_rn(qa, qc)), 0.0);
+            }
+            if (!last) {
+                const double qa = q_plus(g, A, p), qb = q_plus(g, B, p), qc = q_plus(g, C, p);
+                s.kq[2 * l] = __dadd_rn(__dadd_rn(qb, __dsub_rn(qa, qc)), 0.0);
+            }
+        } else {
+            double qa, qb, qc;
+            if (first) { qa = q_plus(g, A, p); qb = q_plus(g, B, p); qc = q_plus(g, C, p); }
+            else if (last) { qa = q_minus(g, A, p); qb = q_minus(g, B, p); qc = q_minus(g, C, p); }
+            else {
+                qa = __dmul_rn(0.5, __dadd_rn(q_minus(g, A, p), q_plus(g, A, p)));
+                qb = __dmul_rn(0.5, __dadd_rn(q_minus(g, B, p), q_plus(g, B, p)));
+                qc = __dmul_rn(0.5, __dadd_rn(q_minus(g, C, p), q_plus(g, C, p)));
+            }
+            s.kq[l] = __dadd_rn(__dadd_rn(qb, __dsub_rn(qa, qc)), 0.0);
+        }
+    }
+    __syncthreads();
+    // 4. monotone repair: pool adjacent violators (equal weights), only if needed
+    for (int k = threadIdx.x; k + 1 < nk; k += blockDim.x)
+        if (s.kq[k + 1] < s.kq[k]) s.flag[2] = 1;
+    __syncthreads();
+    if (s.flag[2] && threadIdx.x == 0) {
+        double* bsum = s.bsum;
+        int* bcnt = s.ibuf;
+        int nb = 0;
+        for (int k = 0; k < nk; ++k) {
+            bsum[nb] = s.kq[k];
+            bcnt[nb] = 1;
+            ++nb;
+            while (nb >= 2 && __ddiv_rn(bsum[nb - 2], (double)bcnt[nb - 2]) >
+                                  __ddiv_rn(bsum[nb - 1], (double)bcnt[nb - 1])) {
+                bsum[nb - 2] = __dadd_rn(bsum[nb - 2], bsum[nb - 1]);
+                bcnt[nb - 2] += bcnt[nb - 1];
+                --nb;
+            }
+        }
+        int k = 0;
+        for (int b = 0; b < nb; ++b) {
+            if (bcnt[b] == 1) { ++k; continue; }
+            const double mean = __dadd_rn(__ddiv_rn(bsum[b], (double)bcnt[b]), 0.0);
+            for (int c = 0; c < bcnt[b]; ++c) s.kq[k++] = mean;
+        }
+    }
+    __syncthreads();
+    // 5. PL CDF through the knots, right-continuous, read at the interior edges
+    for (int i = 1 + threadIdx.x; i < I; i += blockDim.x) {
+        const double x = edge(g, i);
+        const long long kx = okey(x);
+        int lo = 0, hi = nk;   // first knot with kq > x
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (okey(s.kq[mid]) <= kx) lo = mid + 1; else hi = mid;
+        }
+        const int j = lo - 1;
+        double v;
+        if (j < 0) v = 0.0;
+        else {
+            const double pj = s.levels[two ? (j + 1) >> 1 : j];
+            if (j == nk - 1) v = pj;
+            else {
+                const double pn = s.levels[two ? (j + 2) >> 1 : j + 1];
+                const double t = __ddiv_rn(__dsub_rn(x, s.kq[j]), __dsub_rn(s.kq[j + 1], s.kq[j]));
+                v = __dadd_rn(pj, __dmul_rn(t, __dsub_rn(pn, pj)));
+            }
+        }
+        if (v < 0.0) v = 0.0;
+        if (v > 1.0) v = 1.0;
+        out[i] = v;
+    }
+    if (threadIdx.x == 0) {
+        out[0] = 0.0;
+        out[I] = 1.0;
+    }
+    __syncthreads();
+}
+
+// Additive (4.1), multiplicative (4.2) and rotation (4.3) iterators on masses.
+__device__ void mass_iterate_block(int kind, int I, const double* A, const double* B, const double* C,
+                                   double* out, double* r, double* wsum)
+{
+    double pu = 0.0, pv = 0.0, pw = 0.0;
+    for (int i = threadIdx.x; i < I; i += blockDim.x) {
+        const double a = __dsub_rn(A[i + 1], A[i]), b = __dsub_rn(B[i + 1], B[i]), c = __dsub_rn(C[i + 1], C[i]);
+        if (kind == PR_ITER_ADD) {
+            const double v = __dsub_rn(__dadd_rn(a, b), c);
+            r[i] = v < 0.0 ? 0.0 : v;
+        } else if (kind == PR_ITER_MULT) {
+            r[i] = c > 0.0 ? __dmul_rn(a, __ddiv_rn(b, c)) : 0.0;
+        } else {
+            pu = __dadd_rn(pu, sqrt(__dmul_rn(b, c)));
+            pv = __dadd_rn(pv, sqrt(__dmul_rn(b, a)));
+            pw = __dadd_rn(pw, sqrt(__dmul_rn(c, a)));
+        }
+    }
+    if (kind == PR_ITER_ROT) {
+        const double u = block_sum_f64(pu, wsum);
+        const double v = block_sum_f64(pv, wsum);
+        const double w = block_sum_f64(pw, wsum);
+        const double ca = __ddiv_rn(__dsub_rn(__dadd_rn(u, __dmul_rn(__dmul_rn(2.0, u), w)), v), __dadd_rn(1.0, w));
+        const double cc = __ddiv_rn(__dadd_rn(u, v), __dadd_rn(1.0, w));
+        for (int i = threadIdx.x; i < I; i += blockDim.x) {
+            const double a = __dsub_rn(A[i + 1], A[i]), b = __dsub_rn(B[i + 1], B[i]), c = __dsub_rn(C[i + 1], C[i]);
+            const double sv = __dsub_rn(__dadd_rn(__dmul_rn(ca, sqrt(a)), sqrt(b)), __dmul_rn(cc, sqrt(c)));
+            r[i] = __dmul_rn(sv, sv);
+        }
+    }
+    __syncthreads();
+    block_scan_f64(r, r, I, wsum);
+    const double total = r[I - 1];
+    for (int i = threadIdx.x; i < I - 1; i += blockDim.x) {
+        const double v = total > 0.0 ? __ddiv_rn(r[i], total) : 0.0;
+        out[i + 1] = v < 1.0 ? v : 1.0;
+    }
+    if (threadIdx.x == 0) {
+        out[0] = 0.0;
+        out[I] = 1.0;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+__global__ void assemble_generator_kernel(GridDev g, int kind, double lam, double beta, double tau_x,
+                                          double slice_dt, double* __restrict__ A)
+{
+    const int I = g.bins;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= I) return;
+    const double Dbar = 1.0 / beta;
+    // log rho_inf(x) = log(1/Dbar) - Fbar(x)/Dbar, Fbar the averaged potential
+    auto fbar = [&](double x) {
+        return kind == PR_MODEL_OU ? 0.5 * (1.0 - lam) * x * x
+                                   : 0.25 * x * x * x * x - 0.5 * (1.0 - lam) * x * x;
+    };
+    auto log_rho_inf = [&](double x) { return log(1.0 / Dbar) - fbar(x) / Dbar; };
+    auto centre = [&](int k) { return 0.5 * (edge(g, k) + edge(g, k + 1)); };
+    auto width = [&](int k) { return edge(g, k + 1) - edge(g, k); };
+    double* row = A + (size_t)c * I;
+    for (int k = 0; k < I; ++k) row[k] = 0.0;
+    double diag = 0.0;
+    // left edge e = c: cell c loses phi_c
+    if (c >= 1) {
+        const int e = c;
+        const double xe = edge(g, e);
+        const double coef = Dbar / (centre(e) - centre(e - 1));
+        const double rr = exp(log_rho_inf(xe) - log_rho_inf(centre(e))) / width(e);
+        const double rl = exp(log_rho_inf(xe) - log_rho_inf(centre(e - 1))) / width(e - 1);
+        diag -= coef * rr / tau_x;
+        row[c - 1] += coef * rl / tau_x;
+    }
+    // right edge e = c+1: cell c gains phi_{c+1}
+    if (c + 1 <= I - 1) {
+        const int e = c + 1;
+        const double xe = edge(g, e);
+        const double coef = Dbar / (centre(e) - centre(e - 1));
+        const double rr = exp(log_rho_inf(xe) - log_rho_inf(centre(e))) / width(e);
+        const double rl = exp(log_rho_inf(xe) - log_rho_inf(centre(e - 1))) / width(e - 1);
+        row[c + 1] += coef * rr / tau_x;
+        diag -= coef * rl / tau_x;
+    }
+    row[c] = diag;
+    for (int k = 0; k < I; ++k) row[k] *= slice_dt;
+}
+
+__global__ void norm1_kernel(const double* __restrict__ A, int n, double* out)
+{
+    // max over columns of the absolute column sum; one block
+    __shared__ double best[256];
+    double m = 0.0;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r < n; ++r) s += fabs(A[(size_t)r * n + c]);
+        m = fmax(m, s);
+    }
+    best[threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int i = 0; i < (int)blockDim.x; ++i) v = fmax(v, best[i]);
+        *out = v;
+    }
+}
+
+__global__ void scale_kernel(double* A, size_t n, double s)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        A[i] *= s;
+}
+
+__global__ void identity_kernel(double* A, int n)
+{
+    const size_t nn = (size_t)n * n;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (size_t)gridDim.x * blockDim.x)
+        A[i] = (i / n == i % n) ? 1.0 : 0.0;
+}
+
+// C = alpha * A B + beta * I   (n x n, row-major), 64x64 tiles, 256 threads x 4x4.
+__global__ void __launch_bounds__(256) dgemm_kernel(int n, const double* __restrict__ A,
+                                                    const double* __restrict__ B, double* __restrict__ C,
+                                                    double alpha, double beta_identity)
+{
+    __shared__ double As[16][64 + 1];
+    __shared__ double Bs[16][64 + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < n; k0 += 16) {
+        for (int t = threadIdx.x; t < 16 * 64; t += 256) {
+            const int kk = t / 64, rr = t % 64;
+            const int ar = row0 + rr, ak = k0 + kk;
+            As[kk][rr] = (ar < n && ak < n) ? A[(size_t)ar * n + ak] : 0.0;
+            const int bk = k0 + kk, bc = col0 + rr;
+            Bs[kk][rr] = (bk < n && bc < n) ? B[(size_t)bk * n + bc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = row0 + ty * 4 + i;
+        if (r >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = col0 + tx * 4 + j;
+            if (c >= n) continue;
+            C[(size_t)r * n + c] = alpha * acc[i][j] + (r == c ? beta_identity : 0.0);
+        }
+    }
+}
+
+__host__ __device__ inline size_t coarse_apply_smem(int bins)
+{
+    return ((size_t)2 * (bins + 1) + 2 * (size_t)bins + 40) * sizeof(double);
+}
+
+__global__ void __launch_bounds__(kCoarseThreads)
+coarse_fp_kernel(const double* __restrict__ P, int I, const double* __restrict__ cin, double* __restrict__ cout)
+{
+    extern __shared__ __align__(16) double dsm[];
+    double* in = dsm;
+    double* out = in + (I + 1);
+    double* mass = out + (I + 1);
+    double* mp = mass + I;
+    double* wsum = mp + I;
+    const double* src = cin + (size_t)blockIdx.x * (I + 1);
+    for (int i = threadIdx.x; i <= I; i += blockDim.x) in[i] = src[i];
+    __syncthreads();
+    coarse_apply_block(P, I, in, out, mass, mp, wsum);
+    double* dst = cout + (size_t)blockIdx.x * (I + 1);
+    for (int i = threadIdx.x; i <= I; i += blockDim.x) dst[i] = out[i];
+}
+
+__host__ __device__ inline size_t update_smem(int bins)
+{
+    return (size_t)5 * (bins + 1) * sizeof(double) + jq_smem_bytes(bins);
+}
+
+// The serial sweep of Section 3.2.3 on one CTA.
+__global__ void __launch_bounds__(kCoarseThreads)
+parareal_update_kernel(const double* __restrict__ P, GridDev g, int iterator, int qmode, int K,
+                       const double* __restrict__ cdf0, const double* __restrict__ fstar,
+                       const double* __restrict__ cstar, double* __restrict__ next, int32_t* status)
+{
+    extern __shared__ __align__(16) unsigned char usm[];
+    const int I = g.bins;
+    double* cur = reinterpret_cast<double*>(usm);
+    double* Ab = cur + (I + 1);
+    double* Bb = Ab + (I + 1);
+    double* Cb = Bb + (I + 1);
+    double* Ob = Cb + (I + 1);
+    JqSmem js = carve_jq(reinterpret_cast<unsigned char*>(Ob + (I + 1)), I);
+    double* mass = js.levels;       // coarse scratch aliases the level list
+    double* mp = js.levels + I;
+    if (threadIdx.x == 0) js.flag[1] = 0;
+    for (int i = threadIdx.x; i <= I; i += blockDim.x) {
+        cur[i] = cdf0[i];
+        next[i] = cdf0[i];
+    }
+    __syncthreads();
+    for (int n = 0; n < K; ++n) {
+        coarse_apply_block(P, I, cur, Ab, mass, mp, js.wsum);
+        double* res = Ab;
+        if (iterator != PR_ITER_NONE) {
+            for (int i = threadIdx.x; i <= I; i += blockDim.x) {
+                Bb[i] = fstar[(size_t)n * (I + 1) + i];
+                Cb[i] = cstar[(size_t)n * (I + 1) + i];
+            }
+            __syncthreads();
+            if (iterator == PR_ITER_QUANTILE) quantile_iterate_block(g, qmode, Ab, Bb, Cb, Ob, js);
+            else mass_iterate_block(iterator, I, Ab, Bb, Cb, Ob, js.kq, js.wsum);
+            res = Ob;
+        }
+        for (int i = threadIdx.x; i <= I; i += blockDim.x) {
+            const double v = res[i];
+            if (!isfinite(v)) js.flag[1] = 1;
+            cur[i] = v;
+            next[(size_t)(n + 1) * (I + 1) + i] = v;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && status) *status = js.flag[1] ? PR_ERR_NUMERIC : PR_OK;
+}
+
+__global__ void __launch_bounds__(kCoarseThreads)
+iterate_kernel(GridDev g, int iterator, int qmode, const double* __restrict__ a, const double* __restrict__ b,
+               const double* __restrict__ c, double* __restrict__ out, int32_t* status)
+{
+    extern __shared__ __align__(16) unsigned char usm[];
+    const int I = g.bins;
+    double* Ab = reinterpret_cast<double*>(usm);
+    double* Bb = Ab + (I + 1);
+    double* Cb = Bb + (I + 1);
+    double* Ob = Cb + (I + 1);
+    JqSmem js = carve_jq(reinterpret_cast<unsigned char*>(Ob + (I + 1)), I);
+    if (threadIdx.x == 0) js.flag[1] = 0;
+    const size_t off = (size_t)blockIdx.x * (I + 1);
+    for (int i = threadIdx.x; i <= I; i += blockDim.x) {
+        Ab[i] = a[off + i];
+        Bb[i] = b[off + i];
+        Cb[i] = c[off + i];
+    }
+    __syncthreads();
+    if (iterator == PR_ITER_QUANTILE) quantile_iterate_block(g, qmode, Ab, Bb, Cb, Ob, js);
+    else mass_iterate_block(iterator, I, Ab, Bb, Cb, Ob, js.kq, js.wsum);
+    for (int i = threadIdx.x; i <= I; i += blockDim.x) out[off + i] = Ob[i];
+    if (threadIdx.x == 0 && status && js.flag[1]) atomicExch(status, (int32_t)PR_ERR_NUMERIC);
+}
+
+__global__ void __launch_bounds__(256)
+w1_kernel(GridDev g, const double* __restrict__ c1, const double* __restrict__ c2, double* __restrict__ w1)
+{
+    __shared__ double wsum[40];
+    const int I = g.bins;
+    const size_t off = (size_t)blockIdx.x * (I + 1);
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < I; i += blockDim.x) {
+        const double d0 = c1[off + i] - c2[off + i], d1 = c1[off + i + 1] - c2[off + i + 1];
+        const double a0 = fabs(d0), a1 = fabs(d1);
+        if ((d0 >= 0.0 && d1 >= 0.0) || (d0 <= 0.0 && d1 <= 0.0)) acc += 0.5 * g.h * (a0 + a1);
+        else acc += g.h * (d0 * d0 + d1 * d1) / (2.0 * (a0 + a1));
+    }
+    const double s = block_sum_f64(acc, wsum);
+    if (threadIdx.x == 0) w1[blockIdx.x] = s;
+}
+
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace pr
+
+using namespace pr;
+
+extern "C" pr_status pr_coarse_create(const pr_model* model, const pr_grid* grid, double slice_dt,
+                                      void** handle, void* stream)
+{
+    if (!model || !grid_ok(grid) || !handle || !(slice_dt > 0.0) || !std::isfinite(slice_dt)) return PR_ERR_INVALID_ARG;
+    if (model->kind < PR_MODEL_OU || model->kind > PR_MODEL_DW_MULTI) return PR_ERR_INVALID_ARG;
+    if (!(model->beta > 0.0) || !(model->tau_x > 0.0) || !std::isfinite(model->lambda)) return PR_ERR_INVALID_ARG;
+    *handle = nullptr;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int I = grid->bins;
+    const size_t nn = (size_t)I * I;
+    double *B = nullptr, *X = nullptr, *Y = nullptr, *nrm = nullptr;
+    auto release = [&]() {
+        if (B) cudaFree(B);
+        if (X) cudaFree(X);
+        if (Y) cudaFree(Y);
+        if (nrm) cudaFree(nrm);
+    };
+    if (cudaMalloc(&B, nn * 8) != cudaSuccess || cudaMalloc(&X, nn * 8) != cudaSuccess ||
+        cudaMalloc(&Y, nn * 8) != cudaSuccess || cudaMalloc(&nrm, 8) != cudaSuccess) {
+        release();
+        return PR_ERR_NOMEM;
+    }
+    const GridDev g = make_grid(*grid);
+    assemble_generator_kernel<<<(I + 127) / 128, 128, 0, st>>>(g, model->kind, model->lambda, model->beta,
+                                                               model->tau_x, slice_dt, B);
+    norm1_kernel<<<1, 256, 0, st>>>(B, I, nrm);
+    double norm = 0.0;
+    if (cudaMemcpyAsync(&norm, nrm, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || !std::isfinite(norm)) {
+        release();
+        return PR_ERR_CUDA;
+    }
+    // scaling and squaring: ||B / 2^s||_1 <= 1/4, Taylor polynomial of degree 18
+    int s = 0;
+    while (norm / std::ldexp(1.0, s) > 0.25 && s < 1000) ++s;
+    const int blocks = 4 * num_sms();
+    scale_kernel<<<blocks, 256, 0, st>>>(B, nn, std::ldexp(1.0, -s));
+    double* T = X;   // current iterate
+    double* W = Y;   // work
+    identity_kernel<<<blocks, 256, 0, st>>>(T, I);
+    dim3 gg((I + 63) / 64, (I + 63) / 64);
+    const int degree = 18;
+    for (int k = degree; k >= 1; --k) {   // T <- I + (B T)/k  (Horner)
+        dgemm_kernel<<<gg, 256, 0, st>>>(I, B, T, W, 1.0 / k, 1.0);
+        std::swap(T, W);
+    }
+    for (int q = 0; q < s; ++q) {         // T <- T T
+        dgemm_kernel<<<gg, 256, 0, st>>>(I, T, T, W, 1.0, 0.0);
+        std::swap(T, W);
+    }
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+        release();
+        return PR_ERR_CUDA;
+    }
+    // keep T as P, free the rest
+    double* P = T;
+    if (T == X) X = nullptr; else Y = nullptr;
+    release();
+    auto* h = new CoarseHandle;
+    h->g = g;
+    h->P = P;
+    cudaGetDevice(&h->device);
+    *handle = h;
+    return PR_OK;
+}
+
+extern "C" pr_status pr_coarse_destroy(void* handle)
+{
+    if (!handle) return PR_ERR_INVALID_ARG;
+    auto* h = static_cast<CoarseHandle*>(handle);
+    cudaFree(h->P);
+    delete h;
+    return PR_OK;
+}
+
+extern "C" pr_status pr_coarse_matrix(void* handle, double* out, void* stream)
+{
+    if (!handle || !out) return PR_ERR_INVALID_ARG;
+    auto* h = static_cast<CoarseHandle*>(handle);
+    const size_t bytes = (size_t)h->g.bins * h->g.bins * sizeof(double);
+    PR_TRY_CUDA(cudaMemcpyAsync(out, h->P, bytes, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+    return PR_OK;
+}
+
+extern "C" pr_status pr_coarse_fp(void* handle, const double* cdf_in, double* cdf_out, int32_t n_vec, void* stream)
+{
+    if (!handle || !cdf_in || !cdf_out || n_vec < 1 || cdf_in == cdf_out) return PR_ERR_INVALID_ARG;
+    auto* h = static_cast<CoarseHandle*>(handle);
+    const int I = h->g.bins;
+    const size_t smem = coarse_apply_smem(I);
+    PR_TRY_CUDA(allow_smem(coarse_fp_kernel, smem));
+    coarse_fp_kernel<<<n_vec, kCoarseThreads, smem, static_cast<cudaStream_t>(stream)>>>(h->P, I, cdf_in, cdf_out);
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}
+
+extern "C" pr_status pr_parareal_update(void* coarse, pr_iterator iterator, pr_quantile_mode qmode, int32_t n_slices,
+                                        const double* cdf0, const double* cdf_f_star, const double* cdf_c_star,
+                                        double* cdf_next, int32_t* status, void* stream)
+{
+    if (!coarse || !cdf0 || !cdf_next || n_slices < 1) return PR_ERR_INVALID_ARG;
+    if (iterator < PR_ITER_QUANTILE || iterator > PR_ITER_NONE) return PR_ERR_INVALID_ARG;
+    if (qmode != PR_QMODE_TWO_SIDED && qmode != PR_QMODE_MIDPOINT) return PR_ERR_INVALID_ARG;
+    if (iterator != PR_ITER_NONE && (!cdf_f_star || !cdf_c_star)) return PR_ERR_INVALID_ARG;
+    auto* h = static_cast<CoarseHandle*>(coarse);
+    if (h->g.bins > kUpdateMaxBins) return PR_ERR_UNSUPPORTED;
+    const size_t smem = update_smem(h->g.bins);
+    PR_TRY_CUDA(allow_smem(parareal_update_kernel, smem));
+    parareal_update_kernel<<<1, kCoarseThreads, smem, static_cast<cudaStream_t>(stream)>>>(
+        h->P, h->g, (int)iterator, (int)qmode, n_slices, cdf0, cdf_f_star, cdf_c_star, cdf_next, status);
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}
+
+extern "C" pr_status pr_iterate(pr_iterator iterator, pr_quantile_mode qmode, const pr_grid* grid, int32_t n_vec,
+                                const double* a, const double* b, const double* c, double* out, int32_t* status,
+                                void* stream)
+{
+    if (!grid_ok(grid) || n_vec < 1 || !a || !b || !c || !out) return PR_ERR_INVALID_ARG;
+    if (iterator < PR_ITER_QUANTILE || iterator > PR_ITER_ROT) return PR_ERR_INVALID_ARG;
+    if (qmode != PR_QMODE_TWO_SIDED && qmode != PR_QMODE_MIDPOINT) return PR_ERR_INVALID_ARG;
+    if (grid->bins > kUpdateMaxBins) return PR_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (status) PR_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+    const GridDev g = make_grid(*grid);
+    const size_t smem = (size_t)4 * (grid->bins + 1) * sizeof(double) + jq_smem_bytes(grid->bins);
+    PR_TRY_CUDA(allow_smem(iterate_kernel, smem));
+    iterate_kernel<<<n_vec, kCoarseThreads, smem, st>>>(g, (int)iterator, (int)qmode, a, b, c, out, status);
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}
+
+extern "C" pr_status pr_w1(const pr_grid* grid, int32_t n_vec, const double* c1, const double* c2, double* w1,
+                           void* stream)
+{
+    if (!grid_ok(grid) || n_vec < 1 || !c1 || !c2 || !w1) return PR_ERR_INVALID_ARG;
+    const GridDev g = make_grid(*grid);
+    w1_kernel<<<n_vec, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, c1, c2, w1);
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}
+
+extern "C" const char* pr_status_string(pr_status s)
+{
+    switch (s) {
+    case PR_OK: return "PR_OK";
+    case PR_ERR_INVALID_ARG: return "PR_ERR_INVALID_ARG";
+    case PR_ERR_CUDA: return "PR_ERR_CUDA";
+    case PR_ERR_TIMEOUT: return "PR_ERR_TIMEOUT";
+    case PR_ERR_UNSUPPORTED: return "PR_ERR_UNSUPPORTED";
+    case PR_ERR_NOMEM: return "PR_ERR_NOMEM";
+    case PR_ERR_NUMERIC: return "PR_ERR_NUMERIC";
+    }
+    return "PR_ERR_UNKNOWN";
+}
+
+extern "C" const char* pr_version(void) { return "0.1.0"; }

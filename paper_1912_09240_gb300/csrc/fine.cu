@@ -1,0 +1,782 @@
+// fine.cu -- fine propagator F_dT (Euler-Maruyama on a particle ensemble,
+// Section 2.1.3, Eqs. EMx/EMy) for every parareal slice at once, with the
+// restriction (Section 3.2.2, Eq. binning) fused into its epilogue and the
+// matching (Section 5.1) optionally fused into its prologue; plus the
+// standalone restriction, matching and counts-to-CDF kernels.
+//
+// Work decomposition: blockIdx.y is the slice, blockIdx.x a tile of
+// blockDim.x * PPT particles of that slice; each thread carries PPT particles
+// in registers through all `steps` steps of the slice.  State is read once
+// and written once per slice (structure of arrays, coalesced).  The step loop
+// draws its normals from Philox4x32-10 keyed by the seed and counted by
+// (step, particle, slice, problem), so nothing random is stored.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "match.cuh"
+#include "pr_common.cuh"
+
+namespace pr {
+
+int num_sms()
+{
+    static std::mutex mu;
+    static std::vector<int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1, 0);
+    if (cache[dev] == 0) {
+        int v = 1;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = v > 0 ? v : 1;
+    }
+    return cache[dev];
+}
+
+// Arguments of one fine launch, after host-side validation.
+struct FineArgs {
+    const void* x_in;
+    const void* y_in;
+    void* x_out;
+    void* y_out;
+    int64_t n;
+    int64_t in_slice_stride;   // elements of x between input slices (0 = broadcast)
+    int slice_begin;
+    int steps;
+    int fast_dim;
+    // model constants
+    double lam;
+    double drift_dt;   // dt / tau_x
+    double relax;      // dt / eps
+    double sx;         // sqrt(2 D / tau_x) sqrt(dt), D = 1/beta
+    double sy;         // sqrt(2 E / eps) sqrt(dt), E = 1
+    // random numbers
+    uint32_t k0, k1, ctr_hi;   // key words; (problem_id << 8)
+    // fused restriction / matching
+    GridDev g;
+    float lo_f, inv_h_f;
+    const double* cdf_prior;
+    const double* cdf_target;
+    uint32_t* counts_start;
+    uint32_t* counts_end;
+};
+
+// Dynamic shared memory of the fine kernels: [thresholds | hist_start |
+// hist_end | match table], each section 16-byte aligned.
+struct FineSmem {
+    size_t thr, hs, he, match, total;
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+inline FineSmem fine_smem_layout(int bins, bool any_grid, bool match)
+{
+    FineSmem L{0, 0, 0, 0, 0};
+    if (!any_grid) return L;
+    size_t off = 0;
+    L.thr = off;
+    off += align16((size_t)(bins + 1) * sizeof(float));
+    L.hs = off;
+    off += align16((size_t)bins * sizeof(uint32_t));
+    L.he = off;
+    off += align16((size_t)bins * sizeof(uint32_t));
+    L.match = off;
+    if (match) off += match_smem_bytes(bins);
+    L.total = off;
+    return L;
+}
+
+struct FineSmemOffsets {
+    unsigned thr, hs, he, match;
+};
+
+// ---------------------------------------------------------------------------
+// Drift of the slow variable, d_x F (Section 2.1.1)
+// ---------------------------------------------------------------------------
+
+template <int KIND, typename T>
+__device__ __forceinline__ T slow_force(T x, T ymean, T lam)
+{
+    if (KIND == PR_MODEL_OU) return x - lam * ymean;
+    return x * x * x - x + lam * ymean;
+}
+
+// ---------------------------------------------------------------------------
+// binary32 kernel, fast_dim = 1
+// ---------------------------------------------------------------------------
+
+template <int KIND, int PPT>
+__global__ void __launch_bounds__(256)
+fine_f32_d1_kernel(FineArgs a, FineSmemOffsets so, int flags)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const bool any_grid = flags & 1, do_match = flags & 2, do_hs = flags & 4, do_he = flags & 8;
+    const int s = blockIdx.y;
+    const uint32_t slice = (uint32_t)(a.slice_begin + s);
+    const int bins = a.g.bins;
+    float* thr = reinterpret_cast<float*>(smem + so.thr);
+    uint32_t* hist_s = reinterpret_cast<uint32_t*>(smem + so.hs);
+    uint32_t* hist_e = reinterpret_cast<uint32_t*>(smem + so.he);
+    MatchSmem ms;
+    if (any_grid) {
+        build_thresholds(a.g, thr);
+        for (int i = threadIdx.x; i < bins; i += blockDim.x) {
+            hist_s[i] = 0u;
+            hist_e[i] = 0u;
+        }
+        if (do_match) {
+            ms = carve_match_smem(smem + so.match, bins);
+            build_match_table(a.g, a.cdf_prior + (size_t)s * (bins + 1),
+                              a.cdf_target + (size_t)s * (bins + 1), ms);
+        }
+        __syncthreads();
+    }
+
+    const int64_t N = a.n;
+    const float* __restrict__ xin = static_cast<const float*>(a.x_in) + (int64_t)s * a.in_slice_stride;
+    const float* __restrict__ yin = static_cast<const float*>(a.y_in) + (int64_t)s * a.in_slice_stride;
+    float* __restrict__ xout = static_cast<float*>(a.x_out) + (int64_t)s * N;
+    float* __restrict__ yout = static_cast<float*>(a.y_out) + (int64_t)s * N;
+
+    const float lam = (float)a.lam, ddt = (float)a.drift_dt, rel = (float)a.relax;
+    const float sx = (float)a.sx, sy = (float)a.sy;
+
+    float x[PPT], y[PPT];
+    uint32_t pid[PPT];
+    bool ok[PPT];
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x * PPT + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int64_t p = base + (int64_t)k * blockDim.x;
+        ok[k] = p < N;
+        pid[k] = (uint32_t)p;
+        x[k] = ok[k] ? xin[p] : 0.0f;
+        y[k] = ok[k] ? yin[p] : 0.0f;
+    }
+    if (do_match) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k)
+            if (ok[k]) x[k] = match_one_f32(ms, thr, bins, a.lo_f, a.inv_h_f, x[k]);
+    }
+    if (do_hs) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k)
+            if (ok[k]) atomicAdd(&hist_s[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x[k])], 1u);
+    }
+
+    const uint32_t k0 = a.k0, k1 = a.k1, chi = a.ctr_hi;
+    const int pairs = a.steps >> 1;
+    for (int mp = 0; mp < pairs; ++mp) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)mp, pid[k], slice, chi), k0, k1);
+            float z0, z1, z2, z3;
+            box_muller_f32(w.x, w.y, z0, z1);
+            box_muller_f32(w.z, w.w, z2, z3);
+            float xv = x[k], yv = y[k];
+            // step 2 mp
+            float f = slow_force<KIND>(xv, yv, lam);
+            float xn = fmaf(sx, z0, fmaf(-f, ddt, xv));
+            float yn = fmaf(sy, z1, fmaf(xv - yv, rel, yv));
+            // step 2 mp + 1
+            f = slow_force<KIND>(xn, yn, lam);
+            x[k] = fmaf(sx, z2, fmaf(-f, ddt, xn));
+            y[k] = fmaf(sy, z3, fmaf(xn - yn, rel, yn));
+        }
+    }
+    if (a.steps & 1) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)pairs, pid[k], slice, chi), k0, k1);
+            float z0, z1;
+            box_muller_f32(w.x, w.y, z0, z1);
+            const float xv = x[k], yv = y[k];
+            const float f = slow_force<KIND>(xv, yv, lam);
+            x[k] = fmaf(sx, z0, fmaf(-f, ddt, xv));
+            y[k] = fmaf(sy, z1, fmaf(xv - yv, rel, yv));
+        }
+    }
+
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (!ok[k]) continue;
+        const int64_t p = base + (int64_t)k * blockDim.x;
+        xout[p] = x[k];
+        yout[p] = y[k];
+        if (do_he) atomicAdd(&hist_e[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x[k])], 1u);
+    }
+    if (do_hs || do_he) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < bins; i += blockDim.x) {
+            if (do_hs && hist_s[i]) atomicAdd(&a.counts_start[(size_t)s * bins + i], hist_s[i]);
+            if (do_he && hist_e[i]) atomicAdd(&a.counts_end[(size_t)s * bins + i], hist_e[i]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// binary32 kernel, fast_dim = D > 1 (coupling through mean(y)), one particle
+// per thread.  Normals: ceil((1+D)/4) Philox blocks per step.
+// ---------------------------------------------------------------------------
+
+template <int KIND, int D>
+__global__ void __launch_bounds__(256)
+fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const bool any_grid = flags & 1, do_match = flags & 2, do_hs = flags & 4, do_he = flags & 8;
+    const int s = blockIdx.y;
+    const uint32_t slice = (uint32_t)(a.slice_begin + s);
+    const int bins = a.g.bins;
+    float* thr = reinterpret_cast<float*>(smem + so.thr);
+    uint32_t* hist_s = reinterpret_cast<uint32_t*>(smem + so.hs);
+    uint32_t* hist_e = reinterpret_cast<uint32_t*>(smem + so.he);
+    MatchSmem ms;
+    if (any_grid) {
+        build_thresholds(a.g, thr);
+        for (int i = threadIdx.x; i < bins; i += blockDim.x) {
+            hist_s[i] = 0u;
+            hist_e[i] = 0u;
+        }
+        if (do_match) {
+            ms = carve_match_smem(smem + so.match, bins);
+            build_match_table(a.g, a.cdf_prior + (size_t)s * (bins + 1),
+                              a.cdf_target + (size_t)s * (bins + 1), ms);
+        }
+        __syncthreads();
+    }
+    const int64_t N = a.n;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = p < N;
+    const float* __restrict__ xin = static_cast<const float*>(a.x_in) + (int64_t)s * a.in_slice_stride;
+    const float* __restrict__ yin = static_cast<const float*>(a.y_in) + (int64_t)s * a.in_slice_stride * D;
+    float* __restrict__ xout = static_cast<float*>(a.x_out) + (int64_t)s * N;
+    float* __restrict__ yout = static_cast<float*>(a.y_out) + (int64_t)s * N * D;
+
+    float x = ok ? xin[p] : 0.0f;
+    float y[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) y[j] = ok ? yin[(int64_t)j * N + p] : 0.0f;
+    if (do_match && ok) x = match_one_f32(ms, thr, bins, a.lo_f, a.inv_h_f, x);
+    if (do_hs && ok) atomicAdd(&hist_s[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x)], 1u);
+
+    const float lam = (float)a.lam, ddt = (float)a.drift_dt, rel = (float)a.relax;
+    const float sx = (float)a.sx, sy = (float)a.sy;
+    const float invD = 1.0f / (float)D;
+    constexpr int Q = 1 + D;
+    constexpr int PAIRS = (Q + 1) / 2;
+    constexpr int G = (PAIRS + 1) / 2;
+    const uint32_t k0 = a.k0, k1 = a.k1, chi = a.ctr_hi, pid = (uint32_t)p;
+    for (int m = 0; m < a.steps; ++m) {
+        float z[2 * PAIRS];
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)m, pid, slice, chi | (uint32_t)gi), k0, k1);
+            box_muller_f32(w.x, w.y, z[4 * gi], z[4 * gi + 1]);
+            if (2 * gi + 1 < PAIRS) box_muller_f32(w.z, w.w, z[4 * gi + 2], z[4 * gi + 3]);
+        }
+        float ysum = 0.0f;
+#pragma unroll
+        for (int j = 0; j < D; ++j) ysum += y[j];
+        const float f = slow_force<KIND>(x, ysum * invD, lam);
+        const float xn = fmaf(sx, z[0], fmaf(-f, ddt, x));
+#pragma unroll
+        for (int j = 0; j < D; ++j) y[j] = fmaf(sy, z[1 + j], fmaf(x - y[j], rel, y[j]));
+        x = xn;
+    }
+    if (ok) {
+        xout[p] = x;
+#pragma unroll
+        for (int j = 0; j < D; ++j) yout[(int64_t)j * N + p] = y[j];
+        if (do_he) atomicAdd(&hist_e[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x)], 1u);
+    }
+    if (do_hs || do_he) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < bins; i += blockDim.x) {
+            if (do_hs && hist_s[i]) atomicAdd(&a.counts_start[(size_t)s * bins + i], hist_s[i]);
+            if (do_he && hist_e[i]) atomicAdd(&a.counts_end[(size_t)s * bins + i], hist_e[i]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// binary64 kernel (the plain FP64 path), any fast_dim <= 16, one particle per
+// thread, FP64 normals and arithmetic.
+// ---------------------------------------------------------------------------
+
+template <int KIND>
+__global__ void __launch_bounds__(128)
+fine_f64_kernel(FineArgs a, FineSmemOffsets so, int flags)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const bool any_grid = flags & 1, do_match = flags & 2, do_hs = flags & 4, do_he = flags & 8;
+    const int s = blockIdx.y;
+    const uint32_t slice = (uint32_t)(a.slice_begin + s);
+    const int bins = a.g.bins;
+    uint32_t* hist_s = reinterpret_cast<uint32_t*>(smem + so.hs);
+    uint32_t* hist_e = reinterpret_cast<uint32_t*>(smem + so.he);
+    MatchSmem ms;
+    if (any_grid) {
+        for (int i = threadIdx.x; i < bins; i += blockDim.x) {
+            hist_s[i] = 0u;
+            hist_e[i] = 0u;
+        }
+        if (do_match) {
+            ms = carve_match_smem(smem + so.match, bins);
+            build_match_index(a.g, a.cdf_prior + (size_t)s * (bins + 1),
+                              a.cdf_target + (size_t)s * (bins + 1), ms);
+        }
+        __syncthreads();
+    }
+    const int D = a.fast_dim;
+    const int64_t N = a.n;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = p < N;
+    const double* __restrict__ xin = static_cast<const double*>(a.x_in) + (int64_t)s * a.in_slice_stride;
+    const double* __restrict__ yin = static_cast<const double*>(a.y_in) + (int64_t)s * a.in_slice_stride * D;
+    double* __restrict__ xout = static_cast<double*>(a.x_out) + (int64_t)s * N;
+    double* __restrict__ yout = static_cast<double*>(a.y_out) + (int64_t)s * N * D;
+
+    double x = ok ? xin[p] : 0.0;
+    double y[PR_MAX_FAST_DIM];
+    for (int j = 0; j < D; ++j) y[j] = ok ? yin[(int64_t)j * N + p] : 0.0;
+    if (do_match && ok) x = match_one_f64(ms, a.g, x);
+    if (do_hs && ok) atomicAdd(&hist_s[bin_of_f64(a.g, x)], 1u);
+
+    const uint32_t k0 = a.k0, k1 = a.k1, chi = a.ctr_hi, pid = (uint32_t)p;
+    const int Q = 1 + D;
+    for (int m = 0; m < a.steps; ++m) {
+        double z[PR_MAX_FAST_DIM + 3];
+        if (Q <= 2) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)(m >> 1), pid, slice, chi), k0, k1);
+            if (m & 1) box_muller_f64(w.z, w.w, z[0], z[1]);
+            else box_muller_f64(w.x, w.y, z[0], z[1]);
+        } else {
+            int got = 0;
+            for (uint32_t gi = 0; got < Q; ++gi) {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)m, pid, slice, chi | gi), k0, k1);
+                box_muller_f64(w.x, w.y, z[got], z[got + 1]);
+                got += 2;
+                if (got < Q) {
+                    box_muller_f64(w.z, w.w, z[got], z[got + 1]);
+                    got += 2;
+                }
+            }
+        }
+        double ysum = 0.0;
+        for (int j = 0; j < D; ++j) ysum += y[j];
+        const double ym = (KIND == PR_MODEL_DW_MULTI) ? ysum / (double)D : y[0];
+        const double f = slow_force<KIND == PR_MODEL_OU ? 0 : 1>(x, ym, a.lam);
+        const double xn = x - f * a.drift_dt + a.sx * z[0];
+        for (int j = 0; j < D; ++j) y[j] = y[j] - (y[j] - x) * a.relax + a.sy * z[1 + j];
+        x = xn;
+    }
+    if (ok) {
+        xout[p] = x;
+        for (int j = 0; j < D; ++j) yout[(int64_t)j * N + p] = y[j];
+        if (do_he) atomicAdd(&hist_e[bin_of_f64(a.g, x)], 1u);
+    }
+    if (do_hs || do_he) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < bins; i += blockDim.x) {
+            if (do_hs && hist_s[i]) atomicAdd(&a.counts_start[(size_t)s * bins + i], hist_s[i]);
+            if (do_he && hist_e[i]) atomicAdd(&a.counts_end[(size_t)s * bins + i], hist_e[i]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// counts -> CDF at the edges (exact integer prefix sums, one division each)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256)
+counts_to_cdf_kernel(const uint32_t* __restrict__ counts, int64_t n, int bins, double* __restrict__ cdf)
+{
+    __shared__ unsigned long long warp_tot[8];
+    const int s = blockIdx.x;
+    const uint32_t* c = counts + (size_t)s * bins;
+    double* C = cdf + (size_t)s * (bins + 1);
+    const int T = blockDim.x;
+    const int chunk = (bins + T - 1) / T;
+    const int b = threadIdx.x * chunk, e = min(bins, b + chunk);
+    unsigned long long loc = 0;
+    for (int i = b; i < e; ++i) loc += c[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long incl = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    unsigned long long off = 0;
+    for (int w = 0; w < warp; ++w) off += warp_tot[w];
+    unsigned long long run = off + incl - loc;
+    const double dn = (double)n;
+    for (int i = b; i < e; ++i) {
+        run += c[i];
+        C[i + 1] = (double)run / dn;
+    }
+    if (threadIdx.x == 0) C[0] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// standalone restriction: histogram per slice, binary32 or binary64 input
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(1024)
+restrict_kernel(const T* __restrict__ x, int64_t n, GridDev g, float lo_f, float inv_h_f,
+                uint32_t* __restrict__ counts, int64_t per_block)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int bins = g.bins;
+    float* thr = reinterpret_cast<float*>(smem);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + align16((size_t)(bins + 1) * sizeof(float)));
+    const int s = blockIdx.y;
+    if (sizeof(T) == 4) build_thresholds(g, thr);
+    for (int i = threadIdx.x; i < bins; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const T* xs = x + (int64_t)s * n;
+    const int64_t b = (int64_t)blockIdx.x * per_block;
+    const int64_t e = min(n, b + per_block);
+    for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
+        const T v = xs[p];
+        int i;
+        if (sizeof(T) == 4) i = bin_of_f32(thr, bins, lo_f, inv_h_f, (float)v);
+        else i = bin_of_f64(g, (double)v);
+        atomicAdd(&hist[i], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < bins; i += blockDim.x)
+        if (hist[i]) atomicAdd(&counts[(size_t)s * bins + i], hist[i]);
+}
+
+// ---------------------------------------------------------------------------
+// standalone matching
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(512)
+match_f32_kernel(const float* __restrict__ xp, float* __restrict__ xo, int64_t n, GridDev g,
+                 float lo_f, float inv_h_f, const double* __restrict__ cp,
+                 const double* __restrict__ ct, int64_t per_block)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int bins = g.bins;
+    float* thr = reinterpret_cast<float*>(smem);
+    MatchSmem ms = carve_match_smem(smem + align16((size_t)(bins + 1) * sizeof(float)), bins);
+    const int s = blockIdx.y;
+    build_thresholds(g, thr);
+    build_match_table(g, cp + (size_t)s * (bins + 1), ct + (size_t)s * (bins + 1), ms);
+    const int64_t b = (int64_t)blockIdx.x * per_block;
+    const int64_t e = min(n, b + per_block);
+    const float* xs = xp + (int64_t)s * n;
+    float* os = xo + (int64_t)s * n;
+    for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x)
+        os[p] = match_one_f32(ms, thr, bins, lo_f, inv_h_f, xs[p]);
+}
+
+__global__ void __launch_bounds__(256)
+match_f64_kernel(const double* __restrict__ xp, double* __restrict__ xo, int64_t n, GridDev g,
+                 const double* __restrict__ cp, const double* __restrict__ ct, int64_t per_block)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int bins = g.bins;
+    MatchSmem ms = carve_match_smem(smem, bins);
+    const int s = blockIdx.y;
+    build_match_index(g, cp + (size_t)s * (bins + 1), ct + (size_t)s * (bins + 1), ms);
+    const int64_t b = (int64_t)blockIdx.x * per_block;
+    const int64_t e = min(n, b + per_block);
+    const double* xs = xp + (int64_t)s * n;
+    double* os = xo + (int64_t)s * n;
+    for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) os[p] = match_one_f64(ms, g, xs[p]);
+}
+
+// raw Philox blocks for caller-given counters
+__global__ void rng_words_kernel(const uint4* __restrict__ ctr, int64_t n, uint32_t k0, uint32_t k1,
+                                 uint4* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static bool model_ok(const pr_model* m)
+{
+    if (!m) return false;
+    if (m->kind < PR_MODEL_OU || m->kind > PR_MODEL_DW_MULTI) return false;
+    if (m->fast_dim < 1 || m->fast_dim > PR_MAX_FAST_DIM) return false;
+    if (m->kind != PR_MODEL_DW_MULTI && m->fast_dim != 1) return false;
+    if (!(m->beta > 0.0) || !(m->eps > 0.0) || !(m->tau_x > 0.0)) return false;
+    if (!isfinite(m->lambda)) return false;
+    return true;
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int KIND, int PPT>
+static pr_status launch_f32_d1(const FineArgs& a, FineSmemOffsets so, int flags, size_t smem,
+                               int n_slices, cudaStream_t st)
+{
+    const int threads = a.n >= 4096 ? 256 : 64;
+    const int64_t per = (int64_t)threads * PPT;
+    dim3 grid((unsigned)((a.n + per - 1) / per), (unsigned)n_slices);
+    auto k = fine_f32_d1_kernel<KIND, PPT>;
+    PR_TRY_CUDA(set_smem(k, smem));
+    k<<<grid, threads, smem, st>>>(a, so, flags);
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}
+
+template <int KIND, int D>
+static pr_status launch_f32_dn(const FineArgs& a, FineSmemOffsets so, int flags, size_t smem,
+                               int n_slices, cudaStream_t st)
+{
+    const int threads = a.n >= 4096 ? 256 : 64;
+    dim3 grid((unsigned)((a.n + threads - 1) / threads), (unsigned)n_slices);
+    auto k = fine_f32_dn_kernel<KIND, D>;
+    PR_TRY_CUDA(set_smem(k, smem));
+    k<<<grid, threads, smem, st>>>(a, so, flags);
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}
+
+static pr_status launch_f32_multi(int D, const FineArgs& a, FineSmemOffsets so, int flags,
+                                  size_t smem, int n_slices, cudaStream_t st)
+{
+    switch (D) {
+    case 1: return launch_f32_dn<PR_MODEL_DW_MULTI, 1>(a, so, flags, smem, n_slices, st);
+    case 2: return launch_f32_dn<PR_MODEL_DW_MULTI, 2>(a, so, flags, smem, n_slices, st);
+    case 3: return launch_f32_dn<PR_MODEL_DW_MULTI, 3>(a, so, flags, smem, n_slices, st);
+    case 4: return launch_f32_dn<PR_MODEL_DW_MULTI, 4>(a, so, flags, smem, n_slices, st);
+    case 8: return launch_f32_dn<PR_MODEL_DW_MULTI, 8>(a, so, flags, smem, n_slices, st);
+    case 16: return launch_f32_dn<PR_MODEL_DW_MULTI, 16>(a, so, flags, smem, n_slices, st);
+    default: return PR_ERR_UNSUPPORTED;
+    }
+}
+
+static int g_ppt = 1;   // particles per thread of the binary32 d = 1 kernel
+
+}  // namespace pr
+
+using namespace pr;
+
+extern "C" void pr_set_particles_per_thread(int32_t ppt) { g_ppt = (ppt == 2 || ppt == 4) ? ppt : 1; }
+
+extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision precision, const pr_rng* rng,
+                                       const void* x_in, const void* y_in, int32_t broadcast_input,
+                                       void* x_out, void* y_out, int64_t n, int32_t slice_begin,
+                                       int32_t n_slices, int32_t steps, double dt, const pr_grid* grid,
+                                       const double* cdf_prior, const double* cdf_target,
+                                       uint32_t* counts_start, double* cdf_start,
+                                       uint32_t* counts_end, double* cdf_end, void* stream)
+{
+    if (!model_ok(model) || !rng) return PR_ERR_INVALID_ARG;
+    if (precision != PR_F32 && precision != PR_F64) return PR_ERR_INVALID_ARG;
+    if (!x_in || !y_in || !x_out || !y_out) return PR_ERR_INVALID_ARG;
+    if (n < 1 || n > 0xFFFFFFFFll || n_slices < 1 || n_slices > 65535 || slice_begin < 0) return PR_ERR_INVALID_ARG;
+    if (steps < 0 || !(dt > 0.0) || !isfinite(dt)) return PR_ERR_INVALID_ARG;
+    if (rng->problem_id >= (1u << 24)) return PR_ERR_INVALID_ARG;
+    if ((cdf_prior == nullptr) != (cdf_target == nullptr)) return PR_ERR_INVALID_ARG;
+    if (cdf_start && !counts_start) return PR_ERR_INVALID_ARG;
+    if (cdf_end && !counts_end) return PR_ERR_INVALID_ARG;
+    const bool do_match = cdf_prior != nullptr;
+    const bool any_grid = do_match || counts_start || counts_end;
+    if (any_grid && !grid_ok(grid)) return PR_ERR_INVALID_ARG;
+    const int D = model->fast_dim;
+    const size_t esz = precision == PR_F32 ? 4 : 8;
+    // in-place is allowed only as exact aliasing of whole arrays
+    if (x_in == x_out && (broadcast_input || y_in != y_out)) return PR_ERR_INVALID_ARG;
+    (void)esz;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    FineArgs a{};
+    a.x_in = x_in;
+    a.y_in = y_in;
+    a.x_out = x_out;
+    a.y_out = y_out;
+    a.n = n;
+    a.in_slice_stride = broadcast_input ? 0 : n;
+    a.slice_begin = slice_begin;
+    a.steps = steps;
+    a.fast_dim = D;
+    a.lam = model->lambda;
+    a.drift_dt = dt / model->tau_x;
+    a.relax = dt / model->eps;
+    a.sx = sqrt(2.0 * (1.0 / model->beta) / model->tau_x) * sqrt(dt);
+    a.sy = sqrt(2.0 * 1.0 / model->eps) * sqrt(dt);
+    a.k0 = (uint32_t)(rng->seed & 0xFFFFFFFFull);
+    a.k1 = (uint32_t)(rng->seed >> 32);
+    a.ctr_hi = rng->problem_id << 8;
+    if (any_grid) {
+        a.g = make_grid(*grid);
+        a.lo_f = (float)grid->x_lo;
+        a.inv_h_f = (float)(1.0 / a.g.h);
+    } else {
+        a.g = GridDev{1, 0.0, 1.0, 1.0};
+    }
+    a.cdf_prior = cdf_prior;
+    a.cdf_target = cdf_target;
+    a.counts_start = counts_start;
+    a.counts_end = counts_end;
+    const int bins = any_grid ? grid->bins : 1;
+    if (counts_start) PR_TRY_CUDA(cudaMemsetAsync(counts_start, 0, (size_t)n_slices * bins * 4, st));
+    if (counts_end) PR_TRY_CUDA(cudaMemsetAsync(counts_end, 0, (size_t)n_slices * bins * 4, st));
+
+    const FineSmem L = fine_smem_layout(bins, any_grid, do_match);
+    FineSmemOffsets so{(unsigned)L.thr, (unsigned)L.hs, (unsigned)L.he, (unsigned)L.match};
+    const int flags = (any_grid ? 1 : 0) | (do_match ? 2 : 0) | (counts_start ? 4 : 0) | (counts_end ? 8 : 0);
+    pr_status rc = PR_OK;
+    if (precision == PR_F32) {
+        if (model->kind == PR_MODEL_DW_MULTI && D > 1) {
+            rc = launch_f32_multi(D, a, so, flags, L.total, n_slices, st);
+        } else {
+            // (the multi-component family with one component is the double well)
+            const bool ou = model->kind == PR_MODEL_OU;
+            switch (g_ppt) {
+            case 2:
+                rc = ou ? launch_f32_d1<PR_MODEL_OU, 2>(a, so, flags, L.total, n_slices, st)
+                        : launch_f32_d1<PR_MODEL_DOUBLE_WELL, 2>(a, so, flags, L.total, n_slices, st);
+                break;
+            case 4:
+                rc = ou ? launch_f32_d1<PR_MODEL_OU, 4>(a, so, flags, L.total, n_slices, st)
+                        : launch_f32_d1<PR_MODEL_DOUBLE_WELL, 4>(a, so, flags, L.total, n_slices, st);
+                break;
+            default:
+                rc = ou ? launch_f32_d1<PR_MODEL_OU, 1>(a, so, flags, L.total, n_slices, st)
+                        : launch_f32_d1<PR_MODEL_DOUBLE_WELL, 1>(a, so, flags, L.total, n_slices, st);
+            }
+        }
+    } else {
+        const int threads = 128;
+        dim3 g((unsigned)((n + threads - 1) / threads), (unsigned)n_slices);
+        switch (model->kind) {
+        case PR_MODEL_OU: {
+            auto k = fine_f64_kernel<PR_MODEL_OU>;
+            PR_TRY_CUDA(set_smem(k, L.total));
+            k<<<g, threads, L.total, st>>>(a, so, flags);
+            break;
+        }
+        case PR_MODEL_DOUBLE_WELL: {
+            auto k = fine_f64_kernel<PR_MODEL_DOUBLE_WELL>;
+            PR_TRY_CUDA(set_smem(k, L.total));
+            k<<<g, threads, L.total, st>>>(a, so, flags);
+            break;
+        }
+        default: {
+            auto k = fine_f64_kernel<PR_MODEL_DW_MULTI>;
+            PR_TRY_CUDA(set_smem(k, L.total));
+            k<<<g, threads, L.total, st>>>(a, so, flags);
+        }
+        }
+        PR_CHECK_LAUNCH();
+    }
+    if (rc != PR_OK) return rc;
+    if (cdf_start) {
+        counts_to_cdf_kernel<<<n_slices, 256, 0, st>>>(counts_start, n, bins, cdf_start);
+        PR_CHECK_LAUNCH();
+    }
+    if (cdf_end) {
+        counts_to_cdf_kernel<<<n_slices, 256, 0, st>>>(counts_end, n, bins, cdf_end);
+        PR_CHECK_LAUNCH();
+    }
+    return PR_OK;
+}
+
+extern "C" pr_status pr_rng_words(const pr_rng* rng, const uint32_t* ctr, int64_t n, uint32_t* out, void* stream)
+{
+    if (!rng || !ctr || !out || n < 1) return PR_ERR_INVALID_ARG;
+    if (((uintptr_t)ctr & 15) || ((uintptr_t)out & 15)) return PR_ERR_INVALID_ARG;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * (int64_t)num_sms());
+    rng_words_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const uint4*>(ctr), n, (uint32_t)(rng->seed & 0xFFFFFFFFull), (uint32_t)(rng->seed >> 32),
+        reinterpret_cast<uint4*>(out));
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}
+
+extern "C" pr_status pr_counts_to_cdf(const uint32_t* counts, int64_t n, int32_t n_slices, int32_t bins,
+                                      double* cdf, void* stream)
+{
+    if (!counts || !cdf || n < 1 || n_slices < 1 || bins < 1 || bins > PR_MAX_BINS) return PR_ERR_INVALID_ARG;
+    counts_to_cdf_kernel<<<n_slices, 256, 0, static_cast<cudaStream_t>(stream)>>>(counts, n, bins, cdf);
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}
+
+extern "C" pr_status pr_restrict(pr_precision precision, const void* x, int64_t n, int32_t n_slices,
+                                 const pr_grid* grid, uint32_t* counts, double* cdf, void* stream)
+{
+    if (precision != PR_F32 && precision != PR_F64) return PR_ERR_INVALID_ARG;
+    if (!x || !counts || n < 1 || n_slices < 1 || n_slices > 65535 || !grid_ok(grid)) return PR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int bins = grid->bins;
+    PR_TRY_CUDA(cudaMemsetAsync(counts, 0, (size_t)n_slices * bins * 4, st));
+    const GridDev g = make_grid(*grid);
+    const float lo_f = (float)grid->x_lo, inv_h_f = (float)(1.0 / g.h);
+    // enough CTAs for ~4 per SM over all slices, each a contiguous range
+    const int sms = num_sms();
+    int64_t blocks_per_slice = ((int64_t)sms * 4 + n_slices - 1) / n_slices;
+    const int64_t min_per = 8192;
+    blocks_per_slice = std::max<int64_t>(1, std::min<int64_t>(blocks_per_slice, (n + min_per - 1) / min_per));
+    const int64_t per_block = (n + blocks_per_slice - 1) / blocks_per_slice;
+    const size_t smem = align16((size_t)(bins + 1) * 4) + align16((size_t)bins * 4);
+    dim3 gr((unsigned)blocks_per_slice, (unsigned)n_slices);
+    if (precision == PR_F32) {
+        restrict_kernel<float><<<gr, 1024, smem, st>>>(static_cast<const float*>(x), n, g, lo_f, inv_h_f, counts, per_block);
+    } else {
+        restrict_kernel<double><<<gr, 1024, smem, st>>>(static_cast<const double*>(x), n, g, lo_f, inv_h_f, counts, per_block);
+    }
+    PR_CHECK_LAUNCH();
+    if (cdf) {
+        counts_to_cdf_kernel<<<n_slices, 256, 0, st>>>(counts, n, bins, cdf);
+        PR_CHECK_LAUNCH();
+    }
+    return PR_OK;
+}
+
+extern "C" pr_status pr_match(pr_precision precision, const void* x_prior, void* x_out, int64_t n,
+                              int32_t n_slices, const pr_grid* grid, const double* cdf_prior,
+                              const double* cdf_target, void* stream)
+{
+    if (precision != PR_F32 && precision != PR_F64) return PR_ERR_INVALID_ARG;
+    if (!x_prior || !x_out || !cdf_prior || !cdf_target) return PR_ERR_INVALID_ARG;
+    if (n < 1 || n_slices < 1 || n_slices > 65535 || !grid_ok(grid)) return PR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int bins = grid->bins;
+    const GridDev g = make_grid(*grid);
+    const int sms = num_sms();
+    int64_t blocks_per_slice = ((int64_t)sms * 2 + n_slices - 1) / n_slices;
+    const int64_t min_per = 16384;
+    blocks_per_slice = std::max<int64_t>(1, std::min<int64_t>(blocks_per_slice, (n + min_per - 1) / min_per));
+    const int64_t per_block = (n + blocks_per_slice - 1) / blocks_per_slice;
+    dim3 gr((unsigned)blocks_per_slice, (unsigned)n_slices);
+    if (precision == PR_F32) {
+        const size_t smem = align16((size_t)(bins + 1) * 4) + match_smem_bytes(bins);
+        PR_TRY_CUDA(set_smem(match_f32_kernel, smem));
+        match_f32_kernel<<<gr, 512, smem, st>>>(static_cast<const float*>(x_prior), static_cast<float*>(x_out), n, g,
+                                                (float)grid->x_lo, (float)(1.0 / g.h), cdf_prior, cdf_target, per_block);
+    } else {
+        const size_t smem = match_smem_bytes(bins);
+        PR_TRY_CUDA(set_smem(match_f64_kernel, smem));
+        match_f64_kernel<<<gr, 256, smem, st>>>(static_cast<const double*>(x_prior), static_cast<double*>(x_out), n, g,
+                                                cdf_prior, cdf_target, per_block);
+    }
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}

@@ -1,0 +1,176 @@
+// pr_common.cuh -- device helpers shared by the kernels of libpr.so:
+// counter-based random numbers, uniform/normal conversion, grid edges and
+// bin lookup, launch bookkeeping.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pr.h"
+
+#define PR_MAX_BINS 4096
+#define PR_MAX_FAST_DIM 16
+
+// ---------------------------------------------------------------------------
+// Host-side helpers
+// ---------------------------------------------------------------------------
+
+#define PR_CHECK_LAUNCH()                                   \
+    do {                                                    \
+        cudaError_t _e = cudaGetLastError();                \
+        if (_e != cudaSuccess) return PR_ERR_CUDA;          \
+    } while (0)
+
+#define PR_TRY_CUDA(call)                                   \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) return PR_ERR_CUDA;          \
+    } while (0)
+
+namespace pr {
+
+inline bool grid_ok(const pr_grid* g)
+{
+    return g && g->bins >= 1 && g->bins <= PR_MAX_BINS && g->x_lo < g->x_hi &&
+           g->x_hi - g->x_lo < 1e300;
+}
+
+int num_sms();   // of the current device, cached per device
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
+// multiply-xor S-box, the key advanced by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u;
+constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u;
+constexpr uint32_t kPhiloxWeylB = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi_a = __umulhi(kPhiloxMulA, c.x);
+        const uint32_t lo_a = kPhiloxMulA * c.x;
+        const uint32_t hi_b = __umulhi(kPhiloxMulB, c.z);
+        const uint32_t lo_b = kPhiloxMulB * c.z;
+        c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+        k0 += kPhiloxWeylA;
+        k1 += kPhiloxWeylB;
+    }
+    return c;
+}
+
+// Uniform in (0,1): the odd 24-bit integer 2*(w >> 9) + 1 times 2^-24.
+// In binary32 this is built from the exponent bits of 1.0: the float
+// 1 + (w>>9) 2^-23 minus (1 - 2^-24), an exact subtraction (Sterbenz).
+__device__ __forceinline__ float uniform_f32(uint32_t w)
+{
+    return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994039535522461f;
+}
+
+__device__ __forceinline__ double uniform_f64(uint32_t w)
+{
+    return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+// Box-Muller in binary32 on the special-function unit: r = sqrt(-2 ln u0),
+// theta = 2 pi u1.  -2 ln u0 = -2 ln2 * log2(u0).
+__device__ __forceinline__ float sqrt_approx(float v)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ void box_muller_f32(uint32_t w0, uint32_t w1, float& z0, float& z1)
+{
+    const float u0 = uniform_f32(w0);
+    const float u1 = uniform_f32(w1);
+    const float r = sqrt_approx(-1.38629436111989061883f * __log2f(u0));
+    const float th = 6.28318530717958647693f * u1;
+    float s, c;
+    __sincosf(th, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+__device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, double& z0, double& z1)
+{
+    const double u0 = uniform_f64(w0);
+    const double u1 = uniform_f64(w1);
+    const double r = sqrt(-2.0 * log(u0));
+    double s, c;
+    sincospi(2.0 * u1, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+// ---------------------------------------------------------------------------
+// Uniform grid.  Edges are e_i = x_lo + i*h with h = (x_hi - x_lo)/I, each
+// operation rounded on its own (no fused multiply-add) so that every edge is
+// the same double on the host, in the CPU reference and on the device.
+// ---------------------------------------------------------------------------
+
+struct GridDev {
+    int bins;
+    double lo, hi, h;
+};
+
+__host__ __device__ inline GridDev make_grid(const pr_grid& g)
+{
+    GridDev d;
+    d.bins = g.bins;
+    d.lo = g.x_lo;
+    d.hi = g.x_hi;
+#ifdef __CUDA_ARCH__
+    d.h = __ddiv_rn(__dsub_rn(g.x_hi, g.x_lo), (double)g.bins);
+#else
+    d.h = (g.x_hi - g.x_lo) / (double)g.bins;
+#endif
+    return d;
+}
+
+__device__ __forceinline__ double edge(const GridDev& g, int i)
+{
+    return __dadd_rn(g.lo, __dmul_rn((double)i, g.h));
+}
+
+// Bin of a double: e_i <= x < e_{i+1}, clamped into [0, I-1].
+__device__ __forceinline__ int bin_of_f64(const GridDev& g, double x)
+{
+    if (!(x >= g.lo)) return 0;
+    if (x >= g.hi) return g.bins - 1;
+    int i = (int)floor(__ddiv_rn(__dsub_rn(x, g.lo), g.h));
+    i = max(0, min(i, g.bins - 1));
+    while (i > 0 && x < edge(g, i)) --i;
+    while (i < g.bins - 1 && x >= edge(g, i + 1)) ++i;
+    return i;
+}
+
+// Bin of a float with binary32 arithmetic only.  thr[i] is the smallest float
+// not below e_i, so for a float x: x < e_i  <=>  x < thr[i].  A first guess
+// from one multiply is corrected by those exact comparisons.
+__device__ __forceinline__ int bin_of_f32(const float* __restrict__ thr, int bins, float lo_f,
+                                          float inv_h_f, float x)
+{
+    if (!(x >= thr[0])) return 0;
+    if (x >= thr[bins]) return bins - 1;
+    int i = __float2int_rd((x - lo_f) * inv_h_f);
+    i = max(0, min(i, bins - 1));
+    while (i > 0 && x < thr[i]) --i;
+    while (i < bins - 1 && x >= thr[i + 1]) ++i;
+    return i;
+}
+
+// thr[i] for i = 0..bins, cooperatively by the block.
+__device__ __forceinline__ void build_thresholds(const GridDev& g, float* thr)
+{
+    for (int i = threadIdx.x; i <= g.bins; i += blockDim.x) thr[i] = __double2float_ru(edge(g, i));
+}
+
+// Exact ordering of non-negative doubles through their bit patterns.
+__device__ __forceinline__ long long dkey(double v) { return __double_as_longlong(v); }
+
+}  // namespace pr

@@ -1,0 +1,80 @@
+"""The C ABI library builds, loads and exports every entry point declared in
+include/pr.h; host-side argument validation rejects bad arguments before
+anything is launched (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1912_09240_gb300 import build as b
+    b.build()
+    from paper_1912_09240_gb300 import _lib
+    return _lib
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pr_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert len(names) >= 14
+    lib = L.lib()
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(L.EXPORTED) == set(names)
+
+
+def test_status_strings_and_version(L):
+    assert L.status_string(L.PR_OK) == "PR_OK"
+    assert L.status_string(L.PR_ERR_INVALID_ARG) == "PR_ERR_INVALID_ARG"
+    assert L.status_string(99) == "PR_ERR_UNKNOWN"
+    assert re.fullmatch(r"\d+\.\d+\.\d+", L.version())
+
+
+def test_invalid_arguments_rejected_on_host(L):
+    lib = L.lib()
+    m = L.Model(L.PR_MODEL_OU).c()
+    r = L.Rng().c()
+    g = L.Grid(16, -1.0, 1.0).c()
+    fake = ctypes.c_void_p(0x1000)
+    # NULL model / bad precision / n = 0 / bad dt / bad fast_dim for the OU family
+    assert lib.pr_fine_propagate(None, 0, ctypes.byref(r), fake, fake, 0, fake, fake, 10, 0, 1, 1, 1e-3,
+                                 None, None, None, None, None, None, None, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_fine_propagate(ctypes.byref(m), 7, ctypes.byref(r), fake, fake, 0, fake, fake, 10, 0, 1, 1,
+                                 1e-3, None, None, None, None, None, None, None, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_fine_propagate(ctypes.byref(m), 0, ctypes.byref(r), fake, fake, 0, fake, fake, 0, 0, 1, 1,
+                                 1e-3, None, None, None, None, None, None, None, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_fine_propagate(ctypes.byref(m), 0, ctypes.byref(r), fake, fake, 0, fake, fake, 10, 0, 1, 1,
+                                 -1.0, None, None, None, None, None, None, None, None) == L.PR_ERR_INVALID_ARG
+    m2 = L.Model(L.PR_MODEL_OU, fast_dim=3).c()
+    assert lib.pr_fine_propagate(ctypes.byref(m2), 0, ctypes.byref(r), fake, fake, 0, fake, fake, 10, 0, 1, 1,
+                                 1e-3, None, None, None, None, None, None, None, None) == L.PR_ERR_INVALID_ARG
+    # fused outputs without a grid; cdf without counts
+    assert lib.pr_fine_propagate(ctypes.byref(m), 0, ctypes.byref(r), fake, fake, 0, fake, fake, 10, 0, 1, 1,
+                                 1e-3, None, None, None, fake, None, None, None, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_fine_propagate(ctypes.byref(m), 0, ctypes.byref(r), fake, fake, 0, fake, fake, 10, 0, 1, 1,
+                                 1e-3, ctypes.byref(g), None, None, None, fake, None, None, None) == L.PR_ERR_INVALID_ARG
+    bad = L.Grid(0, -1.0, 1.0).c()
+    assert lib.pr_restrict(0, fake, 10, 1, ctypes.byref(bad), fake, None, None) == L.PR_ERR_INVALID_ARG
+    inv = L.Grid(4, 1.0, -1.0).c()
+    assert lib.pr_match(0, fake, fake, 10, 1, ctypes.byref(inv), fake, fake, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_parareal_update(None, 0, 0, 4, fake, fake, fake, fake, None, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_iterate(9, 0, ctypes.byref(g), 1, fake, fake, fake, fake, None, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_coarse_destroy(None) == L.PR_ERR_INVALID_ARG
+    # misaligned counters for the raw generator
+    assert lib.pr_rng_words(ctypes.byref(r), ctypes.c_void_p(0x1004), 1, fake, None) == L.PR_ERR_INVALID_ARG
+
+
+def test_python_binding_raises(L):
+    with pytest.raises(L.PrError) as e:
+        L._check("pr_x", L.PR_ERR_NUMERIC)
+    assert "PR_ERR_NUMERIC" in str(e.value)

@@ -1,0 +1,142 @@
+"""Whole micro-macro parareal runs on the GPU against the FP64 oracle, the
+exactness theorem on the GPU itself, and sampled per-particle parity at the
+full double-well size (2^20 particles, 50 slices of 1000 steps) in the same
+launch configuration as bench.py."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1912_09240_gb300 import build as b
+    b.build()
+    from paper_1912_09240_gb300 import _lib
+    return _lib
+
+
+def _solver(L, w, precision, iterator=0, qmode=0):
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    grid = L.Grid(w.bins, w.lo, w.hi)
+    s = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=precision,
+                       rng=L.Rng(w.seed, 0), iterator=iterator, qmode=qmode)
+    x0, y0 = workloads.initial_ensemble(w)
+    dt = torch.float32 if precision == L.PR_F32 else torch.float64
+    s.set_initial(torch.tensor(x0, dtype=dt, device="cuda"), torch.tensor(y0, dtype=dt, device="cuda"))
+    return s, x0, y0
+
+
+def _oracle_objs(orc, w):
+    return (orc.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x), orc.Grid(w.bins, w.lo, w.hi))
+
+
+def test_ou_fp64_full_workload_against_oracle(L, orc):
+    """The plain FP64 workload in full: N = 4096, K = 8, dt = 1e-3, 256 bins, 4 iterations."""
+    w = workloads.OU_SMALL
+    s, x0, y0 = _solver(L, w, L.PR_F64)
+    om, og = _oracle_objs(orc, w)
+    ref = orc.parareal(om, og, w.seed, x0, y0, w.K, w.steps, w.step_dt, iters=w.iters)
+    rho = [s.rho.cpu().numpy().copy()]
+    for _ in range(w.iters):
+        s.iterate()
+        rho.append(s.rho.cpu().numpy().copy())
+    worst = max(orc.w1(og, rho[k][n], ref.rho[k][n]) for k in range(w.iters + 1) for n in range(w.K + 1))
+    assert worst <= 1e-4, worst
+    # per-particle: the fine end states of the last iteration
+    xs_gpu = s.xa.cpu().numpy()
+    xbar_ref, _ = orc.fine_propagate(om, w.seed, ref.x[w.iters - 1][: w.K], ref.y[w.iters - 1][: w.K], 0,
+                                     w.steps, w.step_dt)
+    assert np.max(np.abs(xs_gpu - xbar_ref)) <= 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("qmode", [0])
+def test_exactness_theorem_on_gpu(L, orc, prec, qmode):
+    """Iterate k equals the serial fine solution on slices n <= k, bit for bit."""
+    w = workloads.DOUBLE_WELL.scaled(N=20_000, K=6, T=0.06, dt=1e-4, bins=256)
+    precision = L.PR_F64 if prec == "f64" else L.PR_F32
+    s, x0, y0 = _solver(L, w, precision, qmode=qmode)
+    xs, ys, rs = s.serial_reference()
+    for k in range(1, w.K + 1):
+        s.iterate()
+        torch.cuda.synchronize()
+        rho = s.rho.cpu().numpy()
+        rs_ = rs.cpu().numpy()
+        for n in range(k + 1):
+            np.testing.assert_array_equal(rho[n], rs_[n])
+        xa = s.xa.cpu().numpy()
+        xsn = xs.cpu().numpy()
+        for n in range(1, k + 1):
+            np.testing.assert_array_equal(xa[n - 1], xsn[n])
+    s.close()
+
+
+def test_double_well_fp32_small_against_oracle(L, orc):
+    """FP32 path against the FP64 oracle by W1 of the restricted densities."""
+    w = workloads.DOUBLE_WELL.scaled(N=1 << 14, K=5, T=0.05, dt=1e-4, bins=512, iters=3)
+    s, x0, y0 = _solver(L, w, L.PR_F32)
+    om, og = _oracle_objs(orc, w)
+    ref = orc.parareal(om, og, w.seed, x0.astype(np.float32).astype(np.float64),
+                       y0.astype(np.float32).astype(np.float64), w.K, w.steps, w.step_dt, iters=w.iters)
+    worst = 0.0
+    for k in range(1, w.iters + 1):
+        s.iterate()
+        rho = s.rho.cpu().numpy()
+        worst = max(worst, max(orc.w1(og, rho[n], ref.rho[k][n]) for n in range(w.K + 1)))
+    assert worst <= 1e-3, worst
+    s.close()
+
+
+@pytest.mark.parametrize("iterator", [1, 2, 3])
+def test_other_iterators_run_and_converge(L, orc, iterator):
+    w = workloads.OU_SMALL.scaled(N=2048, K=4, T=0.5, iters=4)
+    s, x0, y0 = _solver(L, w, L.PR_F64, iterator=iterator)
+    _, _, rs = s.serial_reference()
+    for _ in range(w.K):
+        s.iterate()
+    torch.cuda.synchronize()
+    w1 = s.w1_to(rs).cpu().numpy()
+    assert np.max(w1) < 1e-12
+    assert int(s.status.item()) == 0
+    s.close()
+
+
+def test_full_size_double_well_sampled_parity(L, orc):
+    """2^20 particles x 50 slices x 1000 steps, FP32, as bench.py runs it: one
+    parareal iteration from the zeroth (coarse sweep + matching against X_0);
+    sampled particles of several slices against the oracle run on those
+    particles only (their own Philox keys)."""
+    w = workloads.DOUBLE_WELL
+    s, x0, y0 = _solver(L, w, L.PR_F32)
+    s.iterate()
+    torch.cuda.synchronize()
+    xbar = s.xa.cpu().numpy()          # Xbar_0^{n+1} = F_n(X_0^n)
+    om, og = _oracle_objs(orc, w)
+    x0f = x0.astype(np.float32).astype(np.float64)
+    y0f = y0.astype(np.float32).astype(np.float64)
+    _, cdf0 = orc.restrict(x0f[None], og)
+    P = orc.coarse_propagator(om, og, w.slice_dt)
+    rho = [cdf0[0]]
+    for n in range(w.K):
+        rho.append(orc.coarse_apply(P, rho[-1])[0])
+    rng = np.random.default_rng(0)
+    ids = np.sort(rng.choice(w.N, 256, replace=False)).astype(np.uint32)
+    ids[0], ids[-1] = 0, w.N - 1
+    for n in (0, 1, 17, 49):
+        start = x0f[ids] if n == 0 else orc.match(x0f[ids][None], og, cdf0, rho[n][None])[0]
+        ox, _ = orc.fine_propagate(om, w.seed, start[None], y0f[:, ids][None], n, w.steps, w.step_dt, ids=ids)
+        got = xbar[n, ids].astype(np.float64)
+        assert np.all(np.abs(got - ox[0]) <= 2e-3 * np.maximum(np.abs(ox[0]), 1.0)), n
+    # coarse sweep of iteration 0 matches the oracle's
+    s2, _, _ = _solver(L, w, L.PR_F32)
+    r0 = s2.rho.cpu().numpy()
+    np.testing.assert_allclose(r0, np.stack(rho), rtol=0, atol=1e-11)
+    s.close()
+    s2.close()

@@ -1,0 +1,374 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances:
+  RNG words, restriction counts/CDFs, the FP64 matching and the quantile
+  iterator on identical inputs: bit-exact.
+  FP64 fine propagator, one slice from identical inputs: |dx| <= 1e-5 per
+  particle (observed ~1e-13: only libm vs CUDA log/sin/cos differ).
+  FP32 fine propagator, one slice: |dx| <= 2e-3 * max(|x|, 1) per particle.
+  Coarse propagator: 1e-12 absolute on P and on the propagated CDFs.
+  Whole parareal runs: W1 between restricted densities <= 1e-4 (FP64) and
+  <= 1e-3 (FP32) at every slice and iteration.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1912_09240_gb300 import build as b
+    b.build()
+    from paper_1912_09240_gb300 import _lib
+    return _lib
+
+
+DEV = "cuda"
+
+
+def _t(a, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV, dtype=dtype)
+
+
+def _models(L, orc):
+    return [
+        (L.Model(L.PR_MODEL_OU, 1, 1.0, 1.0, 0.1), orc.Model(0, 1, 1.0, 1.0, 0.1)),
+        (L.Model(L.PR_MODEL_DOUBLE_WELL, 1, 0.5, 3.0, 1e-2), orc.Model(1, 1, 0.5, 3.0, 1e-2)),
+        (L.Model(L.PR_MODEL_DW_MULTI, 16, 0.5, 3.0, 1e-2), orc.Model(2, 16, 0.5, 3.0, 1e-2)),
+        (L.Model(L.PR_MODEL_DW_MULTI, 3, 0.5, 3.0, 5e-2, 2.0), orc.Model(2, 3, 0.5, 3.0, 5e-2, 2.0)),
+    ]
+
+
+# ---------------------------------------------------------------------------
+# random numbers
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 0xDEADBEEFCAFEF00D])
+def test_rng_words_bit_exact(L, orc, seed):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2**32, size=(4099, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:3] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4]]
+    c = _t(ctr.view(np.int32))
+    out = torch.empty_like(c)
+    L.pr_rng_words(L.Rng(seed), c, ctr.shape[0], out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(got, orc.philox(ctr, seed))
+
+
+# ---------------------------------------------------------------------------
+# fine propagator, one slice from identical inputs
+# ---------------------------------------------------------------------------
+
+def _initial(n, d, seed=0):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(-0.3, 0.8, n)
+    y = x[None, :] + rng.normal(0.0, 0.5, (d, n))
+    return x, y
+
+
+@pytest.mark.parametrize("mi", range(4))
+@pytest.mark.parametrize("n,steps", [(1000, 125), (4096, 7), (1, 3), (257, 0)])
+def test_fine_f64_matches_oracle(L, orc, mi, n, steps):
+    gm, om = _models(L, orc)[mi]
+    d = gm.fast_dim
+    n_slices, slice_begin, dt = 3, 5, 1e-3 if gm.kind == 0 else 1e-4
+    xs, ys = [], []
+    for s in range(n_slices):
+        x, y = _initial(n, d, seed=s)
+        xs.append(x)
+        ys.append(y)
+    x0, y0 = np.stack(xs), np.stack(ys)
+    gx, gy = _t(x0), _t(y0)
+    L.pr_fine_propagate(gm, L.PR_F64, L.Rng(7, 3), gx, gy, False, gx, gy, n, slice_begin, n_slices, steps, dt)
+    torch.cuda.synchronize()
+    ox, oy = orc.fine_propagate(om, 7, x0, y0, slice_begin, steps, dt, problem=3)
+    np.testing.assert_allclose(gx.cpu().numpy(), ox, rtol=0, atol=1e-5)
+    np.testing.assert_allclose(gy.cpu().numpy(), oy, rtol=0, atol=1e-5)
+    assert np.max(np.abs(gx.cpu().numpy() - ox)) < 1e-10
+
+
+@pytest.mark.parametrize("mi", range(4))
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+def test_fine_f32_matches_oracle(L, orc, mi, ppt):
+    gm, om = _models(L, orc)[mi]
+    d = gm.fast_dim
+    n, n_slices, slice_begin, steps = 3000, 2, 11, 125
+    dt = 1e-3 if gm.kind == 0 else 1e-4
+    x0, y0 = _initial(n, d)
+    x0 = np.stack([x0, x0 + 0.5]).astype(np.float32)
+    y0 = np.stack([y0, y0 - 0.5]).astype(np.float32)
+    gx, gy = _t(x0), _t(y0)
+    ox_, oy_ = gx.clone(), gy.clone()
+    L.pr_set_particles_per_thread(ppt)
+    try:
+        L.pr_fine_propagate(gm, L.PR_F32, L.Rng(0), gx, gy, False, ox_, oy_, n, slice_begin, n_slices, steps, dt)
+        torch.cuda.synchronize()
+    finally:
+        L.pr_set_particles_per_thread(1)
+    ox, oy = orc.fine_propagate(om, 0, x0.astype(np.float64), y0.astype(np.float64), slice_begin, steps, dt)
+    gxn, gyn = ox_.cpu().numpy(), oy_.cpu().numpy()
+    assert np.all(np.abs(gxn - ox) <= 2e-3 * np.maximum(np.abs(ox), 1.0))
+    assert np.all(np.abs(gyn - oy) <= 2e-3 * np.maximum(np.abs(oy), 1.0))
+    # the inputs are untouched when out-of-place
+    np.testing.assert_array_equal(gx.cpu().numpy(), x0)
+
+
+def test_fine_broadcast_input(L, orc):
+    gm, om = _models(L, orc)[1]
+    n, K, steps, dt = 999, 4, 20, 1e-4
+    x0, y0 = _initial(n, 1)
+    gx, gy = _t(x0), _t(y0)
+    ox = torch.empty(K, n, dtype=torch.float64, device=DEV)
+    oy = torch.empty(K, 1, n, dtype=torch.float64, device=DEV)
+    L.pr_fine_propagate(gm, L.PR_F64, L.Rng(0), gx, gy, True, ox, oy, n, 2, K, steps, dt)
+    torch.cuda.synchronize()
+    ref, _ = orc.fine_propagate(om, 0, np.repeat(x0[None], K, 0), np.repeat(y0[None], K, 0), 2, steps, dt)
+    np.testing.assert_allclose(ox.cpu().numpy(), ref, rtol=0, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# restriction
+# ---------------------------------------------------------------------------
+
+def _awkward_x(n_slices, n, grid, rng):
+    e = grid.edges()
+    x = rng.normal(0.2, 1.3, (n_slices, n))
+    k = min(n, 64)
+    x[:, :k] = e[rng.integers(0, grid.bins + 1, (n_slices, k))]
+    if n > 70:
+        x[:, 64:70] = [grid.lo - 3.0, grid.hi + 3.0, grid.lo, grid.hi, np.nextafter(grid.hi, 0),
+                       np.nextafter(grid.lo, -10)]
+    return x
+
+
+@pytest.mark.parametrize("bins,lo,hi", [(256, -4.0, 4.0), (512, -3.0, 3.0), (37, -1.3, 2.9), (1, 0.0, 1.0),
+                                        (4096, -3.0, 3.0)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_restrict_bit_exact(L, orc, bins, lo, hi, prec):
+    og = orc.Grid(bins, lo, hi)
+    rng = np.random.default_rng(bins)
+    n, S = 50_001, 3
+    x = _awkward_x(S, n, og, rng)
+    if prec == 0:
+        x = x.astype(np.float32)
+    gx = _t(x)
+    counts = torch.empty(S, bins, dtype=torch.int32, device=DEV)
+    cdf = torch.empty(S, bins + 1, dtype=torch.float64, device=DEV)
+    L.pr_restrict(prec, gx, n, S, L.Grid(bins, lo, hi), counts, cdf)
+    torch.cuda.synchronize()
+    oc, ocdf = orc.restrict(x.astype(np.float64), og)
+    np.testing.assert_array_equal(counts.cpu().numpy().view(np.uint32), oc)
+    np.testing.assert_array_equal(cdf.cpu().numpy(), ocdf)
+
+
+# ---------------------------------------------------------------------------
+# matching
+# ---------------------------------------------------------------------------
+
+def _cdf_pair(orc, og, rng, n):
+    prior_x = rng.normal(-0.4, 0.9, n)
+    target_x = rng.gamma(3.0, 0.5, 4 * n) - 1.0
+    _, cp = orc.restrict(prior_x[None], og)
+    _, ct = orc.restrict(target_x[None], og)
+    return prior_x, cp[0], ct[0]
+
+
+@pytest.mark.parametrize("bins,lo,hi", [(64, -3.0, 3.0), (512, -3.0, 3.0), (37, -2.2, 4.1)])
+def test_match_f64_bit_exact(L, orc, bins, lo, hi):
+    og = orc.Grid(bins, lo, hi)
+    rng = np.random.default_rng(3)
+    n, S = 20_000, 3
+    xs, cps, cts = [], [], []
+    for s in range(S):
+        x, cp, ct = _cdf_pair(orc, og, rng, n)
+        x[:8] = [lo - 1, hi + 1, lo, hi, og.edges()[3], -1e9, 1e9, 0.0]
+        xs.append(x)
+        cps.append(cp)
+        cts.append(ct)
+    x, cp, ct = np.stack(xs), np.stack(cps), np.stack(cts)
+    out = torch.empty(S, n, dtype=torch.float64, device=DEV)
+    L.pr_match(L.PR_F64, _t(x), out, n, S, L.Grid(bins, lo, hi), _t(cp), _t(ct))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), orc.match(x, og, cp, ct))
+
+
+@pytest.mark.parametrize("bins,lo,hi", [(64, -3.0, 3.0), (512, -3.0, 3.0), (1024, -3.0, 3.0)])
+def test_match_f32_close(L, orc, bins, lo, hi):
+    og = orc.Grid(bins, lo, hi)
+    rng = np.random.default_rng(4)
+    n = 100_003
+    x, cp, ct = _cdf_pair(orc, og, rng, n)
+    x32 = x.astype(np.float32)
+    _, cp = orc.restrict(x32.astype(np.float64)[None], og)
+    out = torch.empty(1, n, dtype=torch.float32, device=DEV)
+    L.pr_match(L.PR_F32, _t(x32[None]), out, n, 1, L.Grid(bins, lo, hi), _t(cp), _t(ct[None]))
+    torch.cuda.synchronize()
+    ref = orc.match(x32.astype(np.float64)[None], og, cp, ct[None])
+    got = out.cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref)
+    assert np.all(err <= 2e-3 * np.maximum(np.abs(ref), 1.0))
+    assert np.median(err) < 1e-6
+    # matched ensembles restrict to the same histogram up to edge-straddlers
+    _, c_got = orc.restrict(got, og)
+    _, c_ref = orc.restrict(ref, og)
+    assert orc.w1(og, c_got[0], c_ref[0]) < 1e-5
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_match_strong_projection_exact(L, orc, prec):
+    og = orc.Grid(128, -3.0, 3.0)
+    rng = np.random.default_rng(9)
+    n = 30_000
+    x = np.concatenate([rng.normal(0.1, 0.8, n - 4), [-5.0, 5.0, -3.0, 3.0]])[None]
+    if prec == 0:
+        x = x.astype(np.float32)
+    _, cdf = orc.restrict(x.astype(np.float64), og)
+    gx = _t(x)
+    out = torch.empty_like(gx)
+    L.pr_match(prec, gx, out, n, 1, L.Grid(128, -3.0, 3.0), _t(cdf), _t(cdf))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), x)
+
+
+# ---------------------------------------------------------------------------
+# coarse propagator, iterators, W1
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,lam,beta,bins,lo,hi,dT", [(0, 1.0, 1.0, 256, -4.0, 4.0, 0.125),
+                                                        (1, 0.5, 3.0, 512, -3.0, 3.0, 0.1),
+                                                        (0, 0.3, 2.0, 100, -5.0, 5.0, 0.7)])
+def test_coarse_matches_oracle(L, orc, kind, lam, beta, bins, lo, hi, dT):
+    gm = L.Model(kind, 1, lam, beta, 0.1)
+    om = orc.Model(kind, 1, lam, beta, 0.1)
+    og = orc.Grid(bins, lo, hi)
+    h = L.pr_coarse_create(gm, L.Grid(bins, lo, hi), dT)
+    try:
+        P_ref = orc.coarse_propagator(om, og, dT)
+        Pg = torch.empty(bins, bins, dtype=torch.float64, device=DEV)
+        L.pr_coarse_matrix(h, Pg)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(Pg.cpu().numpy(), P_ref, rtol=0, atol=1e-12)
+        rng = np.random.default_rng(2)
+        cdfs = np.stack([np.concatenate([[0.0], np.cumsum(m)]) / m.sum() for m in rng.random((5, bins)) ** 3])
+        cdfs[:, -1] = 1.0
+        out = torch.empty(5, bins + 1, dtype=torch.float64, device=DEV)
+        L.pr_coarse_fp(h, _t(cdfs), out, 5)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(out.cpu().numpy(), orc.coarse_apply(P_ref, cdfs), rtol=0, atol=1e-12)
+    finally:
+        L.pr_coarse_destroy(h)
+
+
+def _rand_cdf(rng, bins, empty=0.3, n=4096):
+    m = rng.gamma(0.7, 1.0, bins)
+    m[rng.random(bins) < empty] = 0.0
+    m[rng.integers(0, bins)] += 0.5
+    c = np.round(m / m.sum() * n).astype(np.int64)
+    c[0] += max(0, 1 - c.sum())
+    cdf = np.concatenate([[0], np.cumsum(c)]) / c.sum()
+    cdf[-1] = 1.0
+    return cdf
+
+
+@pytest.mark.parametrize("qmode", [0, 1])
+@pytest.mark.parametrize("bins", [3, 64, 512, 1024])
+def test_quantile_iterator_bit_exact(L, orc, qmode, bins):
+    og = orc.Grid(bins, -3.0, 3.0)
+    rng = np.random.default_rng(bins + qmode)
+    V = 6
+    a = np.stack([_rand_cdf(rng, bins) for _ in range(V)])
+    b = np.stack([_rand_cdf(rng, bins) for _ in range(V)])
+    c = np.stack([_rand_cdf(rng, bins) for _ in range(V)])
+    c[0] = a[0]                       # J(a, b, a) = b
+    out = torch.empty(V, bins + 1, dtype=torch.float64, device=DEV)
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    L.pr_iterate(L.PR_ITER_QUANTILE, qmode, L.Grid(bins, -3.0, 3.0), V, _t(a), _t(b), _t(c), out, st)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert int(st.item()) == 0
+    for v in range(V):
+        np.testing.assert_array_equal(got[v], orc.iterate(og, a[v], b[v], c[v], 0, qmode))
+    if qmode == 0:
+        np.testing.assert_array_equal(got[0], b[0])
+
+
+@pytest.mark.parametrize("it", [1, 2, 3])
+def test_mass_iterators(L, orc, it):
+    bins = 200
+    og = orc.Grid(bins, 0.0, 1.0)
+    rng = np.random.default_rng(it)
+    lin = np.linspace(0, 1, bins + 1)
+    a = np.stack([0.5 * (_rand_cdf(rng, bins, 0.0) + lin) for _ in range(3)])
+    b = np.stack([_rand_cdf(rng, bins, 0.1) for _ in range(3)])
+    c = np.stack([0.5 * (_rand_cdf(rng, bins, 0.0) + lin) for _ in range(3)])
+    out = torch.empty(3, bins + 1, dtype=torch.float64, device=DEV)
+    L.pr_iterate(it, 0, L.Grid(bins, 0.0, 1.0), 3, _t(a), _t(b), _t(c), out)
+    torch.cuda.synchronize()
+    for v in range(3):
+        np.testing.assert_allclose(out.cpu().numpy()[v], orc.iterate(og, a[v], b[v], c[v], it), rtol=0, atol=1e-13)
+
+
+def test_iterator_flags_bad_input(L):
+    bins = 8
+    a = np.linspace(0, 1, bins + 1)
+    bad = a.copy()
+    bad[3], bad[4] = bad[4], bad[3]        # not monotone
+    out = torch.empty(1, bins + 1, dtype=torch.float64, device=DEV)
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    L.pr_iterate(L.PR_ITER_QUANTILE, 0, L.Grid(bins, 0.0, 1.0), 1, _t(a[None]), _t(bad[None]), _t(a[None]), out, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == L.PR_ERR_NUMERIC
+
+
+def test_w1_matches_oracle(L, orc):
+    bins = 300
+    og = orc.Grid(bins, -2.0, 3.0)
+    rng = np.random.default_rng(0)
+    c1 = np.stack([_rand_cdf(rng, bins) for _ in range(4)])
+    c2 = np.stack([_rand_cdf(rng, bins) for _ in range(4)])
+    w = torch.empty(4, dtype=torch.float64, device=DEV)
+    L.pr_w1(L.Grid(bins, -2.0, 3.0), 4, _t(c1), _t(c2), w)
+    torch.cuda.synchronize()
+    ref = [orc.w1(og, c1[v], c2[v]) for v in range(4)]
+    np.testing.assert_allclose(w.cpu().numpy(), ref, rtol=1e-13, atol=0)
+
+
+def test_parareal_update_matches_oracle(L, orc):
+    bins, K = 128, 6
+    gm, om = L.Model(1, 1, 0.5, 3.0, 0.01), orc.Model(1, 1, 0.5, 3.0, 0.01)
+    og = orc.Grid(bins, -3.0, 3.0)
+    rng = np.random.default_rng(5)
+    cdf0 = _rand_cdf(rng, bins, 0.5)
+    fs = np.stack([_rand_cdf(rng, bins, 0.3) for _ in range(K)])
+    cs = np.stack([_rand_cdf(rng, bins, 0.0) for _ in range(K)])
+    h = L.pr_coarse_create(gm, L.Grid(bins, -3.0, 3.0), 0.1)
+    try:
+        out = torch.empty(K + 1, bins + 1, dtype=torch.float64, device=DEV)
+        st = torch.zeros(1, dtype=torch.int32, device=DEV)
+        L.pr_parareal_update(h, L.PR_ITER_QUANTILE, 0, K, _t(cdf0), _t(fs), _t(cs), out, st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        P = orc.coarse_propagator(om, og, 0.1)
+        r = cdf0
+        got = out.cpu().numpy()
+        np.testing.assert_array_equal(got[0], cdf0)
+        for n in range(K):
+            # from the GPU's own previous state, so that rounding does not accumulate
+            a = orc.coarse_apply(P, got[n])[0]
+            ref = orc.iterate(og, a, fs[n], cs[n])
+            assert orc.w1(og, got[n + 1], ref) < 1e-12
+            r = ref
+        # iteration-0 sweep (no correction) equals repeated coarse steps
+        L.pr_parareal_update(h, L.PR_ITER_NONE, 0, K, _t(cdf0), None, None, out, st)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        r = cdf0
+        for n in range(K):
+            r = orc.coarse_apply(P, r)[0]
+            np.testing.assert_allclose(got[n + 1], r, rtol=0, atol=1e-12)
+    finally:
+        L.pr_coarse_destroy(h)

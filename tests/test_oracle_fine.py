@@ -106,3 +106,17 @@ def test_odd_step_count_uses_half_block(orc):
     x1, _ = orc.fine_propagate(model, 0, x0, y0, 0, 1, 1e-3)
     assert not np.array_equal(x3, x1)
     assert np.all(np.isfinite(x3))
+
+
+def test_sample_with_particle_ids(orc):
+    """A sample of columns advanced with its particle indices reproduces those
+    columns of the whole ensemble (used for sampled parity at full size)."""
+    model = orc.Model(kind=1, lam=0.5, beta=3.0, eps=0.01)
+    rng = np.random.default_rng(5)
+    x0 = rng.normal(-1, 0.2, (2, 300))
+    y0 = x0[:, None, :].copy()
+    full = orc.fine_propagate(model, 0, x0, y0, 3, 9, 1e-4)
+    ids = np.array([7, 0, 299, 150], dtype=np.uint32)
+    part = orc.fine_propagate(model, 0, x0[:, ids], y0[:, :, ids], 3, 9, 1e-4, ids=ids)
+    assert np.array_equal(part[0], full[0][:, ids])
+    assert np.array_equal(part[1], full[1][:, :, ids])
