@@ -143,10 +143,15 @@ pr_status pr_rng_words(const pr_rng* rng, const uint32_t* ctr, int64_t n, uint32
 
 /*
  * Tuning knob of the binary32 fine propagator with fast_dim = 1: particles
- * carried per thread (1, 2 or 4; other values select 1).  Process-wide; set
- * by the autotuner.  Results do not depend on it.
+ * carried per thread (1, 2 or 4; other values select 4, the default).
+ * Process-wide.  Results do not depend on it.
  */
 void pr_set_particles_per_thread(int32_t ppt);
+
+/* Tuning knob of the same kernel: the most consecutive particle tiles one CTA
+ * processes (1..64, default 8); the launch also keeps ~16 waves of CTAs.
+ * Process-wide; results do not depend on it. */
+void pr_set_tiles_per_cta(int32_t tiles);
 
 /*
  * Restriction R = R2 o R1 (Section 3.2.2, Eq. binning): drop Y, bin X.
@@ -200,7 +205,9 @@ pr_status pr_coarse_matrix(void* handle, double* out, void* stream);
 
 /*
  * Apply C_dT to n_vec macroscopic states: masses = diff(cdf_in), P @ masses
- * (negative round-off clipped to 0), cumulative sum normalised to unit mass.
+ * with masses <= 1e-10 set to 0 (below that level they are rounding noise of
+ * the matrix exponential, and negative round-off goes with them), cumulative
+ * sum normalised to unit mass.
  *   cdf_in, cdf_out (device) [n_vec][bins+1]; may not alias.
  */
 pr_status pr_coarse_fp(void* handle, const double* cdf_in, double* cdf_out, int32_t n_vec,

@@ -437,7 +437,9 @@ int or_quantile_update(int I, double lo, double hi, int mode,
     int nb = 0;
     for (int k = 0; k < nk; ++k) {
         bsum[nb] = kq[k]; bcnt[nb] = 1; ++nb;
-        while (nb >= 2 && bsum[nb - 2] / bcnt[nb - 2] > bsum[nb - 1] / bcnt[nb - 1]) {
+        /* mean of the left block > mean of the right block, compared as
+         * sum_l * n_r > sum_r * n_l (counts are positive) */
+        while (nb >= 2 && bsum[nb - 2] * (double)bcnt[nb - 1] > bsum[nb - 1] * (double)bcnt[nb - 2]) {
             bsum[nb - 2] += bsum[nb - 1];
             bcnt[nb - 2] += bcnt[nb - 1];
             --nb;

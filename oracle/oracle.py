@@ -278,15 +278,23 @@ def coarse_propagator(model: Model, grid: Grid, slice_dt: float) -> np.ndarray:
     return scipy.linalg.expm(coarse_generator(model, grid) * slice_dt)
 
 
+TAIL_MASS = 1e-10
+
+
 def coarse_apply(P: np.ndarray, cdf: np.ndarray) -> np.ndarray:
-    """C(rho) on a CDF: masses, P @ masses (clipped at 0), cumulative sum normalised to 1."""
+    """C(rho) on a CDF: masses, P @ masses (masses <= TAIL_MASS dropped),
+    cumulative sum normalised to 1."""
     cdf = np.atleast_2d(np.asarray(cdf, dtype=np.float64))
     out = np.empty_like(cdf)
     for r in range(cdf.shape[0]):
         m = cdf[r, 1:] - cdf[r, :-1]
-        # negative round-off of P @ m (entries of P are >= -1e-16) is clipped
-        # so that the CDF stays non-decreasing
-        mp = np.maximum(P @ m, 0.0)
+        # bin masses at or below TAIL_MASS are set to 0: below that level the
+        # entries of P @ m are rounding noise of the matrix exponential
+        # (absolute error ~1e-15), which would otherwise decide where the
+        # support of the result ends (and so the quantile iterator's q(0) and
+        # q(1)); this also clips negative round-off, keeping the CDF monotone
+        mp = P @ m
+        mp = np.where(mp > TAIL_MASS, mp, 0.0)
         s = np.cumsum(mp)
         out[r, 0] = 0.0
         out[r, 1:] = s / s[-1]

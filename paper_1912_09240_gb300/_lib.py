@@ -22,7 +22,7 @@ PR_QMODE_TWO_SIDED, PR_QMODE_MIDPOINT = 0, 1
 
 EXPORTED = (
     "pr_status_string", "pr_version", "pr_rng_words", "pr_fine_propagate", "pr_set_particles_per_thread",
-    "pr_restrict", "pr_counts_to_cdf", "pr_match", "pr_coarse_create", "pr_coarse_destroy",
+    "pr_set_tiles_per_cta", "pr_restrict", "pr_counts_to_cdf", "pr_match", "pr_coarse_create", "pr_coarse_destroy",
     "pr_coarse_matrix", "pr_coarse_fp", "pr_parareal_update", "pr_iterate", "pr_w1",
 )
 
@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
     L.pr_rng_words.argtypes = [P(_Rng), vp, i64, vp, vp]
     L.pr_set_particles_per_thread.argtypes = [i32]
     L.pr_set_particles_per_thread.restype = None
+    L.pr_set_tiles_per_cta.argtypes = [i32]
+    L.pr_set_tiles_per_cta.restype = None
     L.pr_restrict.argtypes = [i32, vp, i64, i32, P(_Grid), vp, vp, vp]
     L.pr_counts_to_cdf.argtypes = [vp, i64, i32, i32, vp, vp]
     L.pr_match.argtypes = [i32, vp, vp, i64, i32, P(_Grid), vp, vp, vp]
@@ -111,7 +113,8 @@ def lib() -> ctypes.CDLL:
     L.pr_iterate.argtypes = [i32, i32, P(_Grid), i32, vp, vp, vp, vp, vp, vp]
     L.pr_w1.argtypes = [P(_Grid), i32, vp, vp, vp, vp]
     for name in EXPORTED:
-        if name not in ("pr_status_string", "pr_version", "pr_set_particles_per_thread"):
+        if name not in ("pr_status_string", "pr_version", "pr_set_particles_per_thread",
+                        "pr_set_tiles_per_cta"):
             getattr(L, name).restype = i32
     _lib = L
     return L
@@ -164,6 +167,10 @@ def pr_rng_words(rng: Rng, ctr, n: int, out, stream=None):
 
 def pr_set_particles_per_thread(ppt: int):
     lib().pr_set_particles_per_thread(ppt)
+
+
+def pr_set_tiles_per_cta(tiles: int):
+    lib().pr_set_tiles_per_cta(tiles)
 
 
 def pr_restrict(precision: int, x, n: int, n_slices: int, grid: Grid, counts, cdf=None, stream=None):

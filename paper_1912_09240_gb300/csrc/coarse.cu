@@ -21,6 +21,11 @@ namespace pr {
 
 constexpr int kCoarseThreads = 512;   // every coarse apply uses this block size
 constexpr int kUpdateMaxBins = 1024;
+// Bin masses of a coarse result at or below this are dropped: below it the
+// entries of P @ m are rounding noise of the matrix exponential (absolute
+// error ~1e-15), which would otherwise decide where the support of the
+// result ends, and with it the quantile iterator's q(0) and q(1).
+constexpr double kTailMass = 1e-10;
 
 struct CoarseHandle {
     GridDev g;
@@ -64,10 +69,38 @@ __device__ void block_scan_f64(const double* v, double* out, int n, double* wsum
     // prefix of the previous lane
     const double prev = __shfl_up_sync(0xffffffffu, incl, 1);
     double run = lane > 0 ? __dadd_rn(wsum[warp], prev) : wsum[warp];
+    double lmax = -INFINITY;
     for (int i = b; i < e; ++i) {
         run = __dadd_rn(run, v[i]);
-        out[i] = run;
+        lmax = fmax(lmax, run);
+        out[i] = lmax;
     }
+    // The prefix of a thread's first element and the last prefix of the
+    // thread before it are rounded in different orders, so for non-negative
+    // inputs they can step back by an ulp.  A prefix maximum (exact in any
+    // order) makes the scan non-decreasing again.
+    double imax = lmax;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, imax, o);
+        if (lane >= o) imax = fmax(imax, t);
+    }
+    __syncthreads();   // everyone is done reading wsum
+    if (lane == 31) wsum[warp] = imax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = -INFINITY;
+        const int nw = T >> 5;
+        for (int w = 0; w < nw; ++w) {
+            const double t = wsum[w];
+            wsum[w] = m;
+            m = fmax(m, t);
+        }
+    }
+    __syncthreads();
+    const double pmax_lane = __shfl_up_sync(0xffffffffu, imax, 1);
+    const double before = lane > 0 ? fmax(wsum[warp], pmax_lane) : wsum[warp];
+    for (int i = b; i < e; ++i) out[i] = fmax(out[i], before);
     __syncthreads();
 }
 
@@ -91,7 +124,7 @@ __device__ double block_sum_f64(double v, double* wsum)
 }
 
 // ---------------------------------------------------------------------------
-// C_dT on one state: masses, P @ masses (negative round-off clipped), CDF of
+// C_dT on one state: masses, P @ masses (masses <= kTailMass dropped), CDF of
 // the result normalised to unit mass.  cdf_in, out: [I+1]; mass, mp: [I].
 // All in shared memory; every thread of a kCoarseThreads block calls it.
 // ---------------------------------------------------------------------------
@@ -108,7 +141,7 @@ __device__ void coarse_apply_block(const double* __restrict__ P, int I, const do
         for (int c = lane; c < I; c += 32) acc = fma(row[c], mass[c], acc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
-        if (lane == 0) mp[r] = acc > 0.0 ? acc : 0.0;
+        if (lane == 0) mp[r] = acc > kTailMass ? acc : 0.0;
     }
     __syncthreads();
     block_scan_f64(mp, mp, I, wsum);
@@ -168,31 +201,29 @@ __device__ __forceinline__ double inside(const GridDev& g, int b, double t)
     return q;
 }
 
-// q^-(p) = min{x : F(x) >= p}
-__device__ __forceinline__ double q_minus(const GridDev& g, const double* F, double p)
+// Both one-sided quantiles of a CDF F at level p:
+//   q^-(p) = min{x : F(x) >= p},  q^+(p) = max{x : F(x) <= p}.
+// They differ only where F is flat at p; otherwise one interpolation serves both.
+__device__ __forceinline__ void quantiles(const GridDev& g, const double* F, double p, double& qm, double& qp)
 {
     const int I = g.bins;
     const int a = count_lt(F, I + 1, p);   // lowest index with F[a] >= p (F[I] = 1 >= p)
-    if (a == 0 || F[a] == p) return edge(g, a);
+    if (a == 0 || F[a] == p) {
+        const int b = count_le(F, I + 1, p) - 1;   // highest index with F[b] <= p
+        qm = edge(g, a);
+        qp = edge(g, b);
+        return;
+    }
     const double t = __ddiv_rn(__dsub_rn(p, F[a - 1]), __dsub_rn(F[a], F[a - 1]));
-    return inside(g, a - 1, t);
-}
-
-// q^+(p) = max{x : F(x) <= p}
-__device__ __forceinline__ double q_plus(const GridDev& g, const double* F, double p)
-{
-    const int I = g.bins;
-    const int b = count_le(F, I + 1, p) - 1;   // highest index with F[b] <= p (F[0] = 0 <= p)
-    if (b == I || F[b] == p) return edge(g, b);
-    const double t = __ddiv_rn(__dsub_rn(p, F[b]), __dsub_rn(F[b + 1], F[b]));
-    return inside(g, b, t);
+    qm = qp = inside(g, a - 1, t);
 }
 
 struct JqSmem {
     double* levels;   // [3(I+1)]
     double* kq;       // [6(I+1)]  (merged values first, then knots)
-    double* bsum;     // [6(I+1)]
-    int* ibuf;        // [6(I+1)]  (ranks, then block counts)
+    double* bsum;     // [6(I+1)]  sums of pooled blocks
+    int* ibuf;        // [6(I+1)]  (distinct flags, then the descent list)
+    int* bpos;        // [6(I+1)]  pooled blocks: start | end << 16
     int* flag;        // [0]: level count, [1]: input not a CDF, [2]: knots need repair
     double* wsum;     // [40]
 };
@@ -200,7 +231,7 @@ struct JqSmem {
 __host__ __device__ inline size_t jq_smem_bytes(int bins)
 {
     const size_t M = 3 * (size_t)(bins + 1);
-    return (M + 2 * M + 2 * M + 40) * sizeof(double) + (2 * M + 4) * sizeof(int);
+    return (M + 2 * M + 2 * M + 40) * sizeof(double) + (4 * M + 4) * sizeof(int);
 }
 
 __device__ inline JqSmem carve_jq(unsigned char* base, int bins)
@@ -212,7 +243,8 @@ __device__ inline JqSmem carve_jq(unsigned char* base, int bins)
     j.bsum = j.kq + 2 * M;
     j.wsum = j.bsum + 2 * M;
     j.ibuf = reinterpret_cast<int*>(j.wsum + 40);
-    j.flag = j.ibuf + 2 * M;
+    j.bpos = j.ibuf + 2 * M;
+    j.flag = j.bpos + 2 * M;
     return j;
 }
 
@@ -284,52 +316,118 @@ __device__ void quantile_iterate_block(const GridDev& g, int qmode, const double
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
         const double p = s.levels[l];
         const bool first = l == 0, last = l == L - 1;
+        double am, ap, bm, bp, cm, cp;
+        quantiles(g, A, p, am, ap);
+        quantiles(g, B, p, bm, bp);
+        quantiles(g, C, p, cm, cp);
         if (two) {
-            if (!first) {
-                const double qa = q_minus(g, A, p), qb = q_minus(g, B, p), qc = q_minus(g, C, p);
-                s.kq[2 * l - 1] = __dadd_rn(__dadd_rn(qb, __dsub_rn(qa, qc)), 0.0);
-            }
-            if (!last) {
-                const double qa = q_plus(g, A, p), qb = q_plus(g, B, p), qc = q_plus(g, C, p);
-                s.kq[2 * l] = __dadd_rn(__dadd_rn(qb, __dsub_rn(qa, qc)), 0.0);
-            }
+            if (!first) s.kq[2 * l - 1] = __dadd_rn(__dadd_rn(bm, __dsub_rn(am, cm)), 0.0);
+            if (!last) s.kq[2 * l] = __dadd_rn(__dadd_rn(bp, __dsub_rn(ap, cp)), 0.0);
         } else {
             double qa, qb, qc;
-            if (first) { qa = q_plus(g, A, p); qb = q_plus(g, B, p); qc = q_plus(g, C, p); }
-            else if (last) { qa = q_minus(g, A, p); qb = q_minus(g, B, p); qc = q_minus(g, C, p); }
+            if (first) { qa = ap; qb = bp; qc = cp; }
+            else if (last) { qa = am; qb = bm; qc = cm; }
             else {
-                qa = __dmul_rn(0.5, __dadd_rn(q_minus(g, A, p), q_plus(g, A, p)));
-                qb = __dmul_rn(0.5, __dadd_rn(q_minus(g, B, p), q_plus(g, B, p)));
-                qc = __dmul_rn(0.5, __dadd_rn(q_minus(g, C, p), q_plus(g, C, p)));
+                qa = __dmul_rn(0.5, __dadd_rn(am, ap));
+                qb = __dmul_rn(0.5, __dadd_rn(bm, bp));
+                qc = __dmul_rn(0.5, __dadd_rn(cm, cp));
             }
             s.kq[l] = __dadd_rn(__dadd_rn(qb, __dsub_rn(qa, qc)), 0.0);
         }
     }
     __syncthreads();
-    // 4. monotone repair: pool adjacent violators (equal weights), only if needed
-    for (int k = threadIdx.x; k + 1 < nk; k += blockDim.x)
-        if (s.kq[k + 1] < s.kq[k]) s.flag[2] = 1;
+    // 4. monotone repair: pool adjacent violators with equal weights.  The
+    //    descents q[k+1] < q[k] are listed in parallel; one thread then runs
+    //    the pooling from descent to descent, visiting only the knots that
+    //    pool (stretches between descents are singleton blocks that pool with
+    //    nothing).  The merges, and the order of the additions, are those of
+    //    the plain left-to-right algorithm.
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) s.ibuf[k] = (k + 1 < nk && s.kq[k + 1] < s.kq[k]) ? 1 : 0;
     __syncthreads();
-    if (s.flag[2] && threadIdx.x == 0) {
-        double* bsum = s.bsum;
-        int* bcnt = s.ibuf;
-        int nb = 0;
-        for (int k = 0; k < nk; ++k) {
-            bsum[nb] = s.kq[k];
-            bcnt[nb] = 1;
-            ++nb;
-            while (nb >= 2 && __ddiv_rn(bsum[nb - 2], (double)bcnt[nb - 2]) >
-                                  __ddiv_rn(bsum[nb - 1], (double)bcnt[nb - 1])) {
-                bsum[nb - 2] = __dadd_rn(bsum[nb - 2], bsum[nb - 1]);
-                bcnt[nb - 2] += bcnt[nb - 1];
-                --nb;
-            }
+    {
+        // compact the descent flags into a sorted list (deterministic scan)
+        const int T = blockDim.x;
+        const int chunk = (nk + T - 1) / T;
+        const int b = threadIdx.x * chunk, e = min(nk, b + chunk);
+        int loc = 0;
+        for (int i = b; i < e; ++i) loc += s.ibuf[i];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int incl = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
         }
-        int k = 0;
-        for (int b = 0; b < nb; ++b) {
-            if (bcnt[b] == 1) { ++k; continue; }
-            const double mean = __dadd_rn(__ddiv_rn(bsum[b], (double)bcnt[b]), 0.0);
-            for (int c = 0; c < bcnt[b]; ++c) s.kq[k++] = mean;
+        int* wtot = reinterpret_cast<int*>(s.wsum);
+        if (lane == 31) wtot[warp] = incl;
+        __syncthreads();
+        int off = 0;
+        for (int w = 0; w < warp; ++w) off += wtot[w];
+        int run = off + incl - loc;
+        // flags are read into the compacted positions of bpos (not ibuf, which is being read)
+        for (int i = b; i < e; ++i) {
+            if (s.ibuf[i]) s.bpos[run] = i;
+            run += s.ibuf[i];
+        }
+        if (threadIdx.x == T - 1) s.flag[2] = run;   // number of descents
+    }
+    __syncthreads();
+    const int nd = s.flag[2];
+    if (nd > 0) {
+        for (int k = threadIdx.x; k < nd; k += blockDim.x) s.ibuf[k] = s.bpos[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double* bsum = s.bsum;
+            int* bpos = s.bpos;   // start | end << 16 of the pooled blocks on the stack
+            int nb = 0, pos = 0;
+            for (int q = 0; q < nd; ++q) {
+                const int d = s.ibuf[q];
+                if (d + 1 < pos) continue;   // inside a block already pooled
+                int cs = d + 1, ce = d + 2, cn = 1;
+                double csum = s.kq[d + 1];
+                for (;;) {
+                    // pool with the block on the left while its mean is larger
+                    for (;;) {
+                        if (cs == 0) break;
+                        double lsum;
+                        int ls, ln;
+                        const bool top = nb > 0 && (bpos[nb - 1] >> 16) == cs;
+                        if (top) {
+                            ls = bpos[nb - 1] & 0xFFFF;
+                            ln = cs - ls;
+                            lsum = bsum[nb - 1];
+                        } else {
+                            ls = cs - 1;
+                            ln = 1;
+                            lsum = s.kq[cs - 1];
+                        }
+                        // mean(left) > mean(cur) as lsum * cn > csum * ln
+                        if (!(__dmul_rn(lsum, (double)cn) > __dmul_rn(csum, (double)ln))) break;
+                        csum = __dadd_rn(lsum, csum);
+                        cn += ln;
+                        cs = ls;
+                        if (top) --nb;
+                    }
+                    // take in the next knot while it lies below the block's mean
+                    if (ce < nk && __dmul_rn(csum, 1.0) > __dmul_rn(s.kq[ce], (double)cn)) {
+                        csum = __dadd_rn(csum, s.kq[ce]);
+                        ++cn;
+                        ++ce;
+                        continue;
+                    }
+                    break;
+                }
+                bsum[nb] = csum;
+                bpos[nb] = cs | (ce << 16);
+                ++nb;
+                pos = ce;
+            }
+            for (int bi = 0; bi < nb; ++bi) {
+                const int bs = bpos[bi] & 0xFFFF, be = bpos[bi] >> 16;
+                if (be - bs < 2) continue;      // a knot that pooled with nothing keeps its bits
+                const double mean = __dadd_rn(__ddiv_rn(bsum[bi], (double)(be - bs)), 0.0);
+                for (int k = bs; k < be; ++k) s.kq[k] = mean;
+            }
         }
     }
     __syncthreads();

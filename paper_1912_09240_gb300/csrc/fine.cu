@@ -56,6 +56,9 @@ struct FineArgs {
     double relax;      // dt / eps
     double sx;         // sqrt(2 D / tau_x) sqrt(dt), D = 1/beta
     double sy;         // sqrt(2 E / eps) sqrt(dt), E = 1
+    float lam_f, drift_dt_f, relax_f, sx_f, sy_f;   // the same, rounded once on the host
+    float sxk_f, syk_f;                             // sx, sy times sqrt(2 ln 2)
+    int tiles_per_cta;  // binary32 d = 1 kernel: consecutive tiles handled by one CTA
     // random numbers
     uint32_t k0, k1, ctr_hi;   // key words; (problem_id << 8)
     // fused restriction / matching
@@ -144,72 +147,74 @@ fine_f32_d1_kernel(FineArgs a, FineSmemOffsets so, int flags)
     float* __restrict__ xout = static_cast<float*>(a.x_out) + (int64_t)s * N;
     float* __restrict__ yout = static_cast<float*>(a.y_out) + (int64_t)s * N;
 
-    const float lam = (float)a.lam, ddt = (float)a.drift_dt, rel = (float)a.relax;
-    const float sx = (float)a.sx, sy = (float)a.sy;
-
-    float x[PPT], y[PPT];
-    uint32_t pid[PPT];
-    bool ok[PPT];
-    const int64_t base = (int64_t)blockIdx.x * blockDim.x * PPT + threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int64_t p = base + (int64_t)k * blockDim.x;
-        ok[k] = p < N;
-        pid[k] = (uint32_t)p;
-        x[k] = ok[k] ? xin[p] : 0.0f;
-        y[k] = ok[k] ? yin[p] : 0.0f;
-    }
-    if (do_match) {
-#pragma unroll
-        for (int k = 0; k < PPT; ++k)
-            if (ok[k]) x[k] = match_one_f32(ms, thr, bins, a.lo_f, a.inv_h_f, x[k]);
-    }
-    if (do_hs) {
-#pragma unroll
-        for (int k = 0; k < PPT; ++k)
-            if (ok[k]) atomicAdd(&hist_s[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x[k])], 1u);
-    }
-
+    const float lam = a.lam_f, ddt = a.drift_dt_f, rel = a.relax_f;
+    const float sxk = a.sxk_f, syk = a.syk_f;   // noise amplitudes times sqrt(2 ln 2)
     const uint32_t k0 = a.k0, k1 = a.k1, chi = a.ctr_hi;
     const int pairs = a.steps >> 1;
-    for (int mp = 0; mp < pairs; ++mp) {
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)mp, pid[k], slice, chi), k0, k1);
-            float z0, z1, z2, z3;
-            box_muller_f32(w.x, w.y, z0, z1);
-            box_muller_f32(w.z, w.w, z2, z3);
-            float xv = x[k], yv = y[k];
-            // step 2 mp
-            float f = slow_force<KIND>(xv, yv, lam);
-            float xn = fmaf(sx, z0, fmaf(-f, ddt, xv));
-            float yn = fmaf(sy, z1, fmaf(xv - yv, rel, yv));
-            // step 2 mp + 1
-            f = slow_force<KIND>(xn, yn, lam);
-            x[k] = fmaf(sx, z2, fmaf(-f, ddt, xn));
-            y[k] = fmaf(sy, z3, fmaf(xn - yn, rel, yn));
-        }
-    }
-    if (a.steps & 1) {
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)pairs, pid[k], slice, chi), k0, k1);
-            float z0, z1;
-            box_muller_f32(w.x, w.y, z0, z1);
-            const float xv = x[k], yv = y[k];
-            const float f = slow_force<KIND>(xv, yv, lam);
-            x[k] = fmaf(sx, z0, fmaf(-f, ddt, xv));
-            y[k] = fmaf(sy, z1, fmaf(xv - yv, rel, yv));
-        }
-    }
+    const int64_t tile = (int64_t)blockDim.x * PPT;
 
+    for (int t = 0; t < a.tiles_per_cta; ++t) {
+        const int64_t base = ((int64_t)blockIdx.x * a.tiles_per_cta + t) * tile + threadIdx.x;
+        if (base - threadIdx.x >= N) break;   // uniform across the block
+        float x[PPT], y[PPT];
+        uint32_t pid[PPT];
+        bool ok[PPT];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        if (!ok[k]) continue;
-        const int64_t p = base + (int64_t)k * blockDim.x;
-        xout[p] = x[k];
-        yout[p] = y[k];
-        if (do_he) atomicAdd(&hist_e[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x[k])], 1u);
+        for (int k = 0; k < PPT; ++k) {
+            const int64_t p = base + (int64_t)k * blockDim.x;
+            ok[k] = p < N;
+            pid[k] = (uint32_t)p;
+            x[k] = ok[k] ? xin[p] : 0.0f;
+            y[k] = ok[k] ? yin[p] : 0.0f;
+        }
+        if (do_match) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                if (ok[k]) x[k] = match_one_f32(ms, thr, bins, a.lo_f, a.inv_h_f, x[k]);
+        }
+        if (do_hs) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                if (ok[k]) atomicAdd(&hist_s[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x[k])], 1u);
+        }
+        for (int mp = 0; mp < pairs; ++mp) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)mp, pid[k], slice, chi), k0, k1);
+                float q0, c0, s0, q1, c1, s1;
+                box_muller_qcs(w.x, w.y, q0, c0, s0);
+                box_muller_qcs(w.z, w.w, q1, c1, s1);
+                float xv = x[k], yv = y[k];
+                // step 2 mp: sx z0 = (q0 sxk) c0, sy z1 = (q0 syk) s0
+                float f = slow_force<KIND>(xv, yv, lam);
+                float xn = fmaf(q0 * sxk, c0, fmaf(-f, ddt, xv));
+                float yn = fmaf(q0 * syk, s0, fmaf(xv - yv, rel, yv));
+                // step 2 mp + 1
+                f = slow_force<KIND>(xn, yn, lam);
+                x[k] = fmaf(q1 * sxk, c1, fmaf(-f, ddt, xn));
+                y[k] = fmaf(q1 * syk, s1, fmaf(xn - yn, rel, yn));
+            }
+        }
+        if (a.steps & 1) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)pairs, pid[k], slice, chi), k0, k1);
+                float q0, c0, s0;
+                box_muller_qcs(w.x, w.y, q0, c0, s0);
+                const float xv = x[k], yv = y[k];
+                const float f = slow_force<KIND>(xv, yv, lam);
+                x[k] = fmaf(q0 * sxk, c0, fmaf(-f, ddt, xv));
+                y[k] = fmaf(q0 * syk, s0, fmaf(xv - yv, rel, yv));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (!ok[k]) continue;
+            const int64_t p = base + (int64_t)k * blockDim.x;
+            xout[p] = x[k];
+            yout[p] = y[k];
+            if (do_he) atomicAdd(&hist_e[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x[k])], 1u);
+        }
     }
     if (do_hs || do_he) {
         __syncthreads();
@@ -266,8 +271,8 @@ fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
     if (do_match && ok) x = match_one_f32(ms, thr, bins, a.lo_f, a.inv_h_f, x);
     if (do_hs && ok) atomicAdd(&hist_s[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x)], 1u);
 
-    const float lam = (float)a.lam, ddt = (float)a.drift_dt, rel = (float)a.relax;
-    const float sx = (float)a.sx, sy = (float)a.sy;
+    const float lam = a.lam_f, ddt = a.drift_dt_f, rel = a.relax_f;
+    const float sx = a.sx_f, sy = a.sy_f;
     const float invD = 1.0f / (float)D;
     constexpr int Q = 1 + D;
     constexpr int PAIRS = (Q + 1) / 2;
@@ -529,16 +534,26 @@ static cudaError_t set_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+static int g_tiles_max = 8;   // upper bound of tiles per CTA (binary32 d = 1 kernel)
+
 template <int KIND, int PPT>
 static pr_status launch_f32_d1(const FineArgs& a, FineSmemOffsets so, int flags, size_t smem,
                                int n_slices, cudaStream_t st)
 {
     const int threads = a.n >= 4096 ? 256 : 64;
     const int64_t per = (int64_t)threads * PPT;
-    dim3 grid((unsigned)((a.n + per - 1) / per), (unsigned)n_slices);
+    const int64_t tiles = (a.n + per - 1) / per;
+    // Several consecutive tiles per CTA amortise the per-CTA prologue (edge
+    // thresholds, matching table), while keeping >= ~16 waves of CTAs so the
+    // last wave costs little.
+    FineArgs b = a;
+    const int64_t target_ctas = (int64_t)num_sms() * 6 * 16;
+    int64_t tpc = (tiles * n_slices) / std::max<int64_t>(1, target_ctas);
+    b.tiles_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(tpc, g_tiles_max));
+    dim3 grid((unsigned)((tiles + b.tiles_per_cta - 1) / b.tiles_per_cta), (unsigned)n_slices);
     auto k = fine_f32_d1_kernel<KIND, PPT>;
     PR_TRY_CUDA(set_smem(k, smem));
-    k<<<grid, threads, smem, st>>>(a, so, flags);
+    k<<<grid, threads, smem, st>>>(b, so, flags);
     PR_CHECK_LAUNCH();
     return PR_OK;
 }
@@ -570,13 +585,15 @@ static pr_status launch_f32_multi(int D, const FineArgs& a, FineSmemOffsets so, 
     }
 }
 
-static int g_ppt = 1;   // particles per thread of the binary32 d = 1 kernel
+static int g_ppt = 4;   // particles per thread of the binary32 d = 1 kernel
 
 }  // namespace pr
 
 using namespace pr;
 
-extern "C" void pr_set_particles_per_thread(int32_t ppt) { g_ppt = (ppt == 2 || ppt == 4) ? ppt : 1; }
+extern "C" void pr_set_particles_per_thread(int32_t ppt) { g_ppt = (ppt == 1 || ppt == 2) ? ppt : 4; }
+
+extern "C" void pr_set_tiles_per_cta(int32_t tiles) { g_tiles_max = tiles < 1 ? 1 : (tiles > 64 ? 64 : tiles); }
 
 extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision precision, const pr_rng* rng,
                                        const void* x_in, const void* y_in, int32_t broadcast_input,
@@ -620,6 +637,14 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
     a.relax = dt / model->eps;
     a.sx = sqrt(2.0 * (1.0 / model->beta) / model->tau_x) * sqrt(dt);
     a.sy = sqrt(2.0 * 1.0 / model->eps) * sqrt(dt);
+    a.lam_f = (float)a.lam;
+    a.drift_dt_f = (float)a.drift_dt;
+    a.relax_f = (float)a.relax;
+    a.sx_f = (float)a.sx;
+    a.sy_f = (float)a.sy;
+    a.sxk_f = (float)(a.sx * 1.1774100225154746910);
+    a.syk_f = (float)(a.sy * 1.1774100225154746910);
+    a.tiles_per_cta = 1;
     a.k0 = (uint32_t)(rng->seed & 0xFFFFFFFFull);
     a.k1 = (uint32_t)(rng->seed >> 32);
     a.ctr_hi = rng->problem_id << 8;

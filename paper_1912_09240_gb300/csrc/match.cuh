@@ -25,6 +25,7 @@ namespace pr {
 //   jfirst      : int    [I]       first piece's target bin of prior bin i
 //   pstart      : int    [I+1]     first piece of prior bin i (pstart[i] == pstart[i+1]: identity)
 //   fend, alpha, beta : float [2I+1]
+//   jp          : int    [2I+1]    target bin of each piece (the result is clamped into it)
 struct MatchSmem {
     double* Cp;
     double* Ct;
@@ -35,6 +36,7 @@ struct MatchSmem {
     float* fend;
     float* alpha;
     float* beta;
+    int* jp;
     int* scratch;   // [blockDim.x / 32 + 1] for scans
 };
 
@@ -44,6 +46,7 @@ __host__ __device__ inline size_t match_smem_bytes(int bins)
     size_t b = 2 * (I + 1) * sizeof(double);
     b += (I + 1 + I + I + I + 1) * sizeof(int);
     b += 3 * (2 * I + 1) * sizeof(float);
+    b += (2 * I + 1) * sizeof(int);
     b += 64 * sizeof(int);
     return (b + 15) & ~(size_t)15;
 }
@@ -63,7 +66,8 @@ __device__ inline MatchSmem carve_match_smem(unsigned char* base, int bins)
     m.fend = fp;
     m.alpha = m.fend + (2 * I + 1);
     m.beta = m.alpha + (2 * I + 1);
-    m.scratch = reinterpret_cast<int*>(m.beta + (2 * I + 1));
+    m.jp = reinterpret_cast<int*>(m.beta + (2 * I + 1));
+    m.scratch = m.jp + (2 * I + 1);
     return m;
 }
 
@@ -197,8 +201,11 @@ __device__ inline void build_match_table(const GridDev& g, const double* __restr
         if (k + 1 < m.pstart[i + 1] && rho_bar > 0.0)
             fe = (float)__ddiv_rn(__dsub_rn(m.Ct[j + 1], m.Cp[i]), rho_bar);
         m.fend[k] = fe;
-        m.alpha[k] = (float)a;
-        m.beta[k] = (float)b;
+        // a target bin of negligible mass makes the slope huge; saturate so
+        // that the clamp into the bin below never sees inf - inf
+        m.alpha[k] = (float)fmax(fmin(a, 1e30), -1e30);
+        m.beta[k] = (float)fmin(b, 1e30);
+        m.jp[k] = j;
     }
     __syncthreads();
 }
@@ -218,7 +225,8 @@ __device__ __forceinline__ float match_one_f32(const MatchSmem& m, const float* 
     if (above) f = 1.0f;
     int k = k0;
     while (k < k1 - 1 && f > m.fend[k]) ++k;
-    const float xn = fmaf(m.beta[k], f, m.alpha[k]);
+    const int j = m.jp[k];
+    const float xn = fminf(fmaxf(fmaf(m.beta[k], f, m.alpha[k]), thr[j]), thr[j + 1]);
     if (below) return x + (xn - thr[0]);
     if (above) return x + (xn - thr[bins]);
     return xn;

@@ -47,15 +47,21 @@ constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u;
 constexpr uint32_t kPhiloxWeylB = 0xBB67AE85u;
 
+// One Philox4x32 round keyed by (k0, k1); each 32 x 32 -> 64-bit product
+// gives both its high and low words.
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1)
+{
+    const unsigned long long pa = (unsigned long long)kPhiloxMulA * c.x;
+    const unsigned long long pb = (unsigned long long)kPhiloxMulB * c.z;
+    return make_uint4((uint32_t)(pb >> 32) ^ c.y ^ k0, (uint32_t)pb, (uint32_t)(pa >> 32) ^ c.w ^ k1,
+                      (uint32_t)pa);
+}
+
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi_a = __umulhi(kPhiloxMulA, c.x);
-        const uint32_t lo_a = kPhiloxMulA * c.x;
-        const uint32_t hi_b = __umulhi(kPhiloxMulB, c.z);
-        const uint32_t lo_b = kPhiloxMulB * c.z;
-        c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+        c = philox_round(c, k0, k1);
         k0 += kPhiloxWeylA;
         k1 += kPhiloxWeylB;
     }
@@ -94,6 +100,22 @@ __device__ __forceinline__ void box_muller_f32(uint32_t w0, uint32_t w1, float& 
     __sincosf(th, &s, &c);
     z0 = r * c;
     z1 = r * s;
+}
+
+// Box-Muller split for the EM kernels: with L = log2(u0), the normals are
+// z0 = K q cos(theta), z1 = K q sin(theta), q = sqrt(-L), K = sqrt(2 ln 2);
+// K is folded into the noise amplitudes on the host.  The angle is built with
+// one FMA from the float 1 + (w1 >> 9) 2^-23: theta = 2 pi (u1) with
+// u1 = that float - (1 - 2^-24).
+constexpr float kSqrt2Ln2 = 1.17741002251547469101f;   // sqrt(2 ln 2)
+
+__device__ __forceinline__ void box_muller_qcs(uint32_t w0, uint32_t w1, float& q, float& c, float& s)
+{
+    const float u0 = uniform_f32(w0);
+    const float f1 = __uint_as_float(0x3F800000u | (w1 >> 9));
+    const float th = fmaf(6.28318530717958647693f, f1, -6.283185107518108f);   // 2 pi_f (1 - 2^-24)
+    q = sqrt_approx(-__log2f(u0));
+    __sincosf(th, &s, &c);
 }
 
 __device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, double& z0, double& z1)

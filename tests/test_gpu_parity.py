@@ -108,7 +108,7 @@ def test_fine_f32_matches_oracle(L, orc, mi, ppt):
         L.pr_fine_propagate(gm, L.PR_F32, L.Rng(0), gx, gy, False, ox_, oy_, n, slice_begin, n_slices, steps, dt)
         torch.cuda.synchronize()
     finally:
-        L.pr_set_particles_per_thread(1)
+        L.pr_set_particles_per_thread(4)
     ox, oy = orc.fine_propagate(om, 0, x0.astype(np.float64), y0.astype(np.float64), slice_begin, steps, dt)
     gxn, gyn = ox_.cpu().numpy(), oy_.cpu().numpy()
     assert np.all(np.abs(gxn - ox) <= 2e-3 * np.maximum(np.abs(ox), 1.0))
