@@ -33,10 +33,16 @@ import workloads  # noqa: E402
 METRIC = "fine-propagator particle-steps/s (FP32 vs FP64 GPU) and parareal iter time at W1≤1e-3"
 UNIT = "particle-steps/s"
 WORKLOAD = workloads.DOUBLE_WELL
-# Thread-instructions per particle-step of the binary32 fine kernel (d = 1),
-# from ncu sm__inst_executed on the double-well workload (profiles/); None
-# until measured.
-INST_PER_PARTICLE_STEP = None
+# Thread-instructions issued per particle-step by the binary32 fine kernel
+# (d = 1, 4 particles per thread): ncu smsp__inst_issued.sum x 32 over the
+# particle-steps of the launch, double-well workload at 2^16 particles x 9
+# slices x 1000 steps (profiles/fine_f32_d1_double_well.md).
+INST_PER_PARTICLE_STEP = 41.70
+# DRAM bytes per particle per slice of that kernel, read + write (ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of a full-size 49-slice launch
+# after iteration 0, profiles/launches_double_well_full.md); the algorithmic
+# figure is 16 B (x and y read once and written once, binary32).
+TRAFFIC_BYTES_PER_PARTICLE_SLICE = 15.32
 SMS = 152
 ISSUE_LANES_PER_SM_CLK = 4 * 32       # 4 sub-partitions x one 32-wide warp instruction per clock
 
@@ -279,11 +285,15 @@ def run_ours(args):
         launch_ps = (w.K - 1) * w.N * w.steps
         achieved = INST_PER_PARTICLE_STEP * launch_ps / (fine_ms / 1e3) / 1e12
         peak = SMS * ISSUE_LANES_PER_SM_CLK * sm_max * 1e6 / 1e12
+        traffic = (TRAFFIC_BYTES_PER_PARTICLE_SLICE * (w.K - 1) * w.N
+                   if TRAFFIC_BYTES_PER_PARTICLE_SLICE else None)
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": traffic,
                     "kernel": "fine_f32_d1_kernel (slices 1..49)",
                     "fine_ms_per_launch": fine_ms,
-                    "peak_basis": f"152 SMs x 4 warp-instr/clk x 32 lanes x {sm_max:.0f} MHz (max SM clock)"}
+                    "peak_basis": f"152 SMs x 4 warp-instr/clk x 32 lanes x {sm_max:.0f} MHz (max SM clock)",
+                    "algorithmic": f"{INST_PER_PARTICLE_STEP} thread-instructions per particle-step x "
+                                   f"{launch_ps:.3e} particle-steps per launch"}
     cpu = None if args.no_cpu else _cpu_sample()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

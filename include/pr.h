@@ -243,6 +243,45 @@ pr_status pr_iterate(pr_iterator iterator, pr_quantile_mode qmode, const pr_grid
                      double* out, int32_t* status, void* stream);
 
 /*
+ * Pathwise adjoint of the binary32 fine propagator with fixed noise (not in
+ * the paper; the EM recursion of Section 2.1.3 differentiated backwards).
+ * fast_dim = 1, families PR_MODEL_OU and PR_MODEL_DOUBLE_WELL.  The forward
+ * pass takes exactly the steps and random numbers of pr_fine_propagate over
+ * slices slice_begin .. slice_begin + n_slices - 1 in sequence (slice s + 1
+ * starting where slice s ended), storing (x, y) every ckpt_every steps in
+ * the workspace; the backward pass replays each checkpoint segment and runs
+ * the adjoint recursion, accumulating in FP64.
+ *   x0, y0      (device) [n] float start states
+ *   x_T, y_T    (device) [n] float end states, or NULL
+ *   xbar_T      (device) [n] double dL/dX_T per particle, or NULL
+ *   ybar_T      (device) [n] double dL/dY_T per particle, or NULL (= 0; needs xbar_T)
+ *   grad        (device) with xbar_T: [3] = dL/d(lambda, beta, eps), summed over
+ *               particles in a fixed order; without: [n][3] = dX_T^p/d(lambda, beta, eps)
+ *   xbar_0, ybar_0 (device) [n] double dL/dX_0, dL/dY_0 (per particle: dX_T/dX_0, dX_T/dY_0
+ *               without seeds), or NULL
+ *   workspace   (device) >= pr_fine_adjoint_workspace(...) bytes, 256-byte aligned,
+ *               caller-owned scratch (checkpoints and partial sums)
+ */
+size_t pr_fine_adjoint_workspace(int64_t n, int32_t n_slices, int32_t steps, int32_t ckpt_every);
+pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, const float* x0, const float* y0,
+                          int64_t n, int32_t slice_begin, int32_t n_slices, int32_t steps, double dt,
+                          int32_t ckpt_every, float* x_T, float* y_T, const double* xbar_T,
+                          const double* ybar_T, double* grad, double* xbar_0, double* ybar_0,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Order statistics of n floats: index_out[r] = the index of the particle of
+ * rank ranks[r] (0-based, ascending; ties broken by particle index), -1 for a
+ * rank outside [0, n).  Used for the pathwise derivative of the empirical
+ * quantile function, Q(p) = X_(ceil(p n)).
+ *   x (device) [n]; ranks (device) [n_ranks] int64; index_out (device) [n_ranks] int64
+ *   workspace (device) >= pr_order_statistics_workspace(n) bytes, 8-byte aligned.
+ */
+size_t pr_order_statistics_workspace(int64_t n);
+pr_status pr_order_statistics(const float* x, int64_t n, const int64_t* ranks, int32_t n_ranks,
+                              int64_t* index_out, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * W1 distance between pairs of macroscopic states on the same grid, each read
  * as its piecewise-linear CDF: integral of |C1 - C2| over [x_lo, x_hi].
  *   c1, c2 (device) [n_vec][bins+1]; w1 (device) [n_vec] doubles.

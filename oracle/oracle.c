@@ -232,6 +232,70 @@ void or_fine_propagate(int kind, int d, double lambda, double beta, double eps, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Tangent-linear (forward-mode) derivatives of the EM recursion with fixed   */
+/* noise (pathwise sensitivities; the paper has no adjoint, this checks one). */
+/* One particle per column, one slow and one fast variable (d = 1), drift     */
+/* families 0 (OU) and 1 (double well).  Tangent directions, in order:        */
+/* theta = (lambda, beta, eps), then the initial state x0 and y0.  ids as in  */
+/* or_fine_propagate_ids (NULL: column p is particle p).                      */
+/*   x_out, y_out   : [N]  states after n_slices * S steps                    */
+/*   dx_out, dy_out : [N][5] d(X_T, Y_T)/d(lambda, beta, eps, x0, y0)         */
+/* ------------------------------------------------------------------------ */
+
+void or_fine_tangent(int kind, double lambda, double beta, double eps, double tau_x,
+                     uint64_t seed, uint32_t problem, const double* x0, const double* y0,
+                     int64_t N, const uint32_t* ids, int slice_begin, int n_slices, int S, double dt,
+                     double* x_out, double* y_out, double* dx_out, double* dy_out)
+{
+    const double D = 1.0 / beta, E = 1.0;
+    const double sqrt_dt = sqrt(dt);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < N; ++p) {
+        double X = x0[p], Y = y0[p];
+        double dX[5] = {0, 0, 0, 1, 0}, dY[5] = {0, 0, 0, 0, 1};
+        double z[2];
+        for (int s = 0; s < n_slices; ++s) {
+            const uint32_t n = (uint32_t)(slice_begin + s);
+            for (int m = 0; m < S; ++m) {
+                or_step_normals(seed, problem, ids ? ids[p] : (uint32_t)p, n, (uint32_t)m, 2, z);
+                const double dU = sqrt_dt * z[0], dV = sqrt_dt * z[1];
+                const double sX = sqrt(2.0 * D / tau_x), sY = sqrt(2.0 * E / eps);
+                /* d_x F and its partial derivatives */
+                double F, Fx, Fy, Fl;
+                if (kind == OR_MODEL_OU) { F = X - lambda * Y; Fx = 1.0; Fy = -lambda; Fl = -Y; }
+                else { F = X * X * X - X + lambda * Y; Fx = 3.0 * X * X - 1.0; Fy = lambda; Fl = Y; }
+                const double Xn = X - (1.0 / tau_x) * F * dt + sX * dU;
+                const double Yn = Y - (1.0 / eps) * (Y - X) * dt + sY * dV;
+                /* Jacobian of the step */
+                const double Jxx = 1.0 - Fx * dt / tau_x, Jxy = -Fy * dt / tau_x;
+                const double Jyx = dt / eps, Jyy = 1.0 - dt / eps;
+                /* explicit parameter derivatives of the step */
+                double px[5] = { -Fl * dt / tau_x,                       /* lambda */
+                                 -0.5 * sX / beta * dU,                  /* beta: d sqrt(2/(beta tau))/d beta */
+                                 0.0, 0.0, 0.0 };
+                double py[5] = { 0.0, 0.0,
+                                 (Y - X) * dt / (eps * eps) - 0.5 * sY / eps * dV,   /* eps */
+                                 0.0, 0.0 };
+                for (int k = 0; k < 5; ++k) {
+                    const double a = Jxx * dX[k] + Jxy * dY[k] + px[k];
+                    const double b = Jyx * dX[k] + Jyy * dY[k] + py[k];
+                    dX[k] = a;
+                    dY[k] = b;
+                }
+                X = Xn;
+                Y = Yn;
+            }
+        }
+        x_out[p] = X;
+        y_out[p] = Y;
+        for (int k = 0; k < 5; ++k) {
+            dx_out[p * 5 + k] = dX[k];
+            dy_out[p * 5 + k] = dY[k];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Uniform grid x_lo = e_0 < e_1 < ... < e_I = x_hi (Section 2.2.2).         */
 /* ------------------------------------------------------------------------ */
 

@@ -62,6 +62,8 @@ def lib():
                                            i32, i32, i32, d]
         _lib.or_fine_propagate_ids.argtypes = [i32, i32, d, d, d, d, u64, u32, vp, vp, i64, vp,
                                                i32, i32, i32, d]
+        _lib.or_fine_tangent.argtypes = [i32, d, d, d, d, u64, u32, vp, vp, i64, vp, i32, i32, i32, d,
+                                          vp, vp, vp, vp]
         _lib.or_edge.argtypes = [i32, i32, d, d]
         _lib.or_edge.restype = d
         _lib.or_bin.argtypes = [d, i32, d, d]
@@ -172,6 +174,28 @@ def fine_propagate(model: Model, seed: int, x: np.ndarray, y: np.ndarray, slice_
                                     model.tau_x, seed, problem, _p(x), _p(y), N, _p(ids),
                                     slice_begin, n_slices, steps, dt)
     return x, y
+
+
+def fine_tangent(model: Model, seed: int, x0: np.ndarray, y0: np.ndarray, slice_begin: int,
+                 n_slices: int, steps: int, dt: float, problem: int = 0, ids: np.ndarray | None = None):
+    """Forward-mode pathwise derivatives with fixed noise (d = 1 families).
+
+    Returns X_T, Y_T [N] and dX_T, dY_T [N][5] with respect to
+    (lambda, beta, eps, x0, y0)."""
+    assert model.fast_dim == 1 and model.kind in (MODEL_OU, MODEL_DOUBLE_WELL)
+    x0 = np.ascontiguousarray(x0, dtype=np.float64).reshape(-1)
+    y0 = np.ascontiguousarray(y0, dtype=np.float64).reshape(-1)
+    N = x0.shape[0]
+    xo, yo = np.empty(N), np.empty(N)
+    dx, dy = np.empty((N, 5)), np.empty((N, 5))
+    idp = None
+    if ids is not None:
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        assert ids.shape == (N,)
+        idp = _p(ids)
+    lib().or_fine_tangent(model.kind, model.lam, model.beta, model.eps, model.tau_x, seed, problem,
+                          _p(x0), _p(y0), N, idp, slice_begin, n_slices, steps, dt, _p(xo), _p(yo), _p(dx), _p(dy))
+    return xo, yo, dx, dy
 
 
 # --------------------------------------------------------------------------

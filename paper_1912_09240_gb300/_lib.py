@@ -24,6 +24,7 @@ EXPORTED = (
     "pr_status_string", "pr_version", "pr_rng_words", "pr_fine_propagate", "pr_set_particles_per_thread",
     "pr_set_tiles_per_cta", "pr_restrict", "pr_counts_to_cdf", "pr_match", "pr_coarse_create", "pr_coarse_destroy",
     "pr_coarse_matrix", "pr_coarse_fp", "pr_parareal_update", "pr_iterate", "pr_w1",
+    "pr_fine_adjoint_workspace", "pr_fine_adjoint", "pr_order_statistics_workspace", "pr_order_statistics",
 )
 
 
@@ -112,9 +113,17 @@ def lib() -> ctypes.CDLL:
     L.pr_parareal_update.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp]
     L.pr_iterate.argtypes = [i32, i32, P(_Grid), i32, vp, vp, vp, vp, vp, vp]
     L.pr_w1.argtypes = [P(_Grid), i32, vp, vp, vp, vp]
+    L.pr_fine_adjoint_workspace.argtypes = [i64, i32, i32, i32]
+    L.pr_fine_adjoint_workspace.restype = ctypes.c_size_t
+    L.pr_fine_adjoint.argtypes = [P(_Model), P(_Rng), vp, vp, i64, i32, i32, i32, d, i32, vp, vp, vp, vp, vp,
+                                  vp, vp, vp, ctypes.c_size_t, vp]
+    L.pr_order_statistics_workspace.argtypes = [i64]
+    L.pr_order_statistics_workspace.restype = ctypes.c_size_t
+    L.pr_order_statistics.argtypes = [vp, i64, vp, i32, vp, vp, ctypes.c_size_t, vp]
     for name in EXPORTED:
         if name not in ("pr_status_string", "pr_version", "pr_set_particles_per_thread",
-                        "pr_set_tiles_per_cta"):
+                        "pr_set_tiles_per_cta", "pr_fine_adjoint_workspace",
+                        "pr_order_statistics_workspace"):
             getattr(L, name).restype = i32
     _lib = L
     return L
@@ -227,3 +236,29 @@ def pr_iterate(iterator: int, qmode: int, grid: Grid, n_vec: int, a, b, c, out, 
 def pr_w1(grid: Grid, n_vec: int, c1, c2, w1, stream=None):
     g = grid.c()
     _check("pr_w1", lib().pr_w1(ctypes.byref(g), n_vec, _ptr(c1), _ptr(c2), _ptr(w1), _stream(stream)))
+
+
+def pr_fine_adjoint_workspace(n: int, n_slices: int, steps: int, ckpt_every: int) -> int:
+    return lib().pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every)
+
+
+def pr_fine_adjoint(model: Model, rng: Rng, x0, y0, n: int, slice_begin: int, n_slices: int, steps: int,
+                    dt: float, ckpt_every: int, x_T, y_T, xbar_T, ybar_T, grad, xbar_0, ybar_0, workspace,
+                    stream=None):
+    m, r = model.c(), rng.c()
+    wbytes = workspace.numel() * workspace.element_size()
+    _check("pr_fine_adjoint", lib().pr_fine_adjoint(ctypes.byref(m), ctypes.byref(r), _ptr(x0), _ptr(y0), n,
+                                                    slice_begin, n_slices, steps, dt, ckpt_every, _ptr(x_T),
+                                                    _ptr(y_T), _ptr(xbar_T), _ptr(ybar_T), _ptr(grad),
+                                                    _ptr(xbar_0), _ptr(ybar_0), _ptr(workspace), wbytes,
+                                                    _stream(stream)))
+
+
+def pr_order_statistics_workspace(n: int) -> int:
+    return lib().pr_order_statistics_workspace(n)
+
+
+def pr_order_statistics(x, n: int, ranks, n_ranks: int, index_out, workspace, stream=None):
+    wbytes = workspace.numel() * workspace.element_size()
+    _check("pr_order_statistics", lib().pr_order_statistics(_ptr(x), n, _ptr(ranks), n_ranks, _ptr(index_out),
+                                                            _ptr(workspace), wbytes, _stream(stream)))

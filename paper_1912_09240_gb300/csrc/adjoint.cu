@@ -1,0 +1,397 @@
+// adjoint.cu -- pathwise adjoint of the binary32 Euler-Maruyama propagator
+// with fixed noise (the EM recursion of Section 2.1.3, Eqs. EMx/EMy, run
+// backwards), for gradients of ensemble observables with respect to
+// theta = (lambda, beta, eps) and to the initial state; and order statistics
+// (sorting) for the derivative of the quantile function.
+//
+// Forward: each thread advances one particle over the whole horizon
+// (n_slices x steps), drawing exactly the random numbers pr_fine_propagate
+// draws and taking exactly its steps (em_step_f32), and stores (x, y) every
+// `ckpt_every` steps in the caller's workspace.
+// Backward, for each checkpoint segment from the last: the segment is
+// replayed once from its checkpoint to leave sub-checkpoints every 16 steps in
+// shared memory; each 16-step block is then replayed once more, keeping its
+// states and noise increments in shared memory, and the adjoint recursion
+//   lbar_t = J_t^T lbar_{t+1},  g += lbar_{t+1} . d(step_t)/d theta
+// runs backwards over the block.  Per-block partial sums are binary32; they
+// are added into binary64 accumulators per particle, and the ensemble sum is
+// reduced in a fixed order (deterministic).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "pr_common.cuh"
+
+namespace pr {
+
+constexpr int kAdjThreads = 128;
+constexpr int kSub = 16;   // steps per replay block
+
+struct AdjArgs {
+    const float* x0;
+    const float* y0;
+    int64_t n;
+    int slice_begin;
+    int steps;        // per slice
+    int64_t total;    // n_slices * steps
+    int ckpt;         // checkpoint interval
+    int64_t n_ckpt;
+    float lam, ddt, rel, sxk, syk;               // forward constants, as pr_fine_propagate
+    float inv2beta, inv2eps, rel_over_eps;       // derivative factors: 1/(2 beta), 1/(2 eps), dt/eps^2
+    uint32_t k0, k1, chi;
+    float* ckpt_buf;          // [n_ckpt][2][n]
+    double* partial;          // [gridDim.x][3] (ensemble-sum mode)
+    float* xT;
+    float* yT;
+    const double* xbar;       // seeds dL/dX_T (NULL: per-particle mode with seed 1)
+    const double* ybar;       // seeds dL/dY_T or NULL
+    double* grad_pp;          // [n][3] in per-particle mode
+    double* xbar0;
+    double* ybar0;
+};
+
+// Walks the steps in order; step m of slice s uses words 2(m&1), 2(m&1)+1 of
+// the Philox block (m >> 1, p, slice_begin + s, problem << 8).
+struct NoiseWalker {
+    int slice, m, cached_mp, cached_slice;
+    uint4 w;
+
+    __device__ void seek(int64_t t, int S)
+    {
+        slice = (int)(t / S);
+        m = (int)(t - (int64_t)slice * S);
+        cached_mp = -1;
+        cached_slice = -1;
+    }
+
+    __device__ __forceinline__ void draw(const AdjArgs& a, uint32_t pid, float& q, float& c, float& s)
+    {
+        const int mp = m >> 1;
+        if (mp != cached_mp || slice != cached_slice) {
+            w = philox4x32_10(make_uint4((uint32_t)mp, pid, (uint32_t)(a.slice_begin + slice), a.chi), a.k0, a.k1);
+            cached_mp = mp;
+            cached_slice = slice;
+        }
+        if (m & 1) box_muller_qcs(w.z, w.w, q, c, s);
+        else box_muller_qcs(w.x, w.y, q, c, s);
+    }
+
+    __device__ __forceinline__ void advance(int S)
+    {
+        if (++m == S) {
+            m = 0;
+            ++slice;
+        }
+    }
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(kAdjThreads)
+adjoint_kernel(AdjArgs a)
+{
+    extern __shared__ float asm_[];
+    const int T = blockDim.x, tid = threadIdx.x;
+    float* subx = asm_;
+    float* suby = subx + kSub * T;
+    float* bx = suby + kSub * T;
+    float* by = bx + kSub * T;
+    float* bnx = by + kSub * T;
+    float* bny = bnx + kSub * T;
+    const int64_t p = (int64_t)blockIdx.x * T + tid;
+    const bool ok = p < a.n;
+    const uint32_t pid = (uint32_t)p;
+    const int S = a.steps;
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    float lx = 0.0f, ly = 0.0f;
+
+    if (ok) {
+        // ---- forward with checkpoints ----
+        float x = a.x0[p], y = a.y0[p];
+        NoiseWalker nw;
+        nw.seek(0, S);
+        int64_t next_ck = 0, ck = 0;
+        for (int64_t t = 0; t < a.total; ++t) {
+            if (t == next_ck) {
+                a.ckpt_buf[(ck * 2) * a.n + p] = x;
+                a.ckpt_buf[(ck * 2 + 1) * a.n + p] = y;
+                ++ck;
+                next_ck += a.ckpt;
+            }
+            float q, c, s;
+            nw.draw(a, pid, q, c, s);
+            em_step_f32<KIND>(x, y, q * a.sxk, c, q * a.syk, s, a.lam, a.ddt, a.rel);
+            nw.advance(S);
+        }
+        if (a.xT) a.xT[p] = x;
+        if (a.yT) a.yT[p] = y;
+
+        // ---- backward ----
+        lx = a.xbar ? (float)a.xbar[p] : 1.0f;
+        ly = a.ybar ? (float)a.ybar[p] : 0.0f;
+        for (int64_t c = a.n_ckpt - 1; c >= 0; --c) {
+            const int64_t t0 = c * a.ckpt;
+            const int L = (int)min((int64_t)a.ckpt, a.total - t0);
+            const int nsub = (L + kSub - 1) / kSub;
+            x = a.ckpt_buf[(c * 2) * a.n + p];
+            y = a.ckpt_buf[(c * 2 + 1) * a.n + p];
+            nw.seek(t0, S);
+            for (int j = 0; j < nsub; ++j) {
+                subx[j * T + tid] = x;
+                suby[j * T + tid] = y;
+                const int len = min(kSub, L - j * kSub);
+                for (int i = 0; i < len; ++i) {
+                    float q, cc, s;
+                    nw.draw(a, pid, q, cc, s);
+                    em_step_f32<KIND>(x, y, q * a.sxk, cc, q * a.syk, s, a.lam, a.ddt, a.rel);
+                    nw.advance(S);
+                }
+            }
+            for (int j = nsub - 1; j >= 0; --j) {
+                const int len = min(kSub, L - j * kSub);
+                x = subx[j * T + tid];
+                y = suby[j * T + tid];
+                nw.seek(t0 + (int64_t)j * kSub, S);
+                for (int i = 0; i < len; ++i) {
+                    float q, cc, s;
+                    nw.draw(a, pid, q, cc, s);
+                    const float ax = q * a.sxk, ay = q * a.syk;
+                    bx[i * T + tid] = x;
+                    by[i * T + tid] = y;
+                    bnx[i * T + tid] = ax * cc;
+                    bny[i * T + tid] = ay * s;
+                    em_step_f32<KIND>(x, y, ax, cc, ay, s, a.lam, a.ddt, a.rel);
+                    nw.advance(S);
+                }
+                float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
+                for (int i = len - 1; i >= 0; --i) {
+                    const float xi = bx[i * T + tid], yi = by[i * T + tid];
+                    const float nx = bnx[i * T + tid], ny = bny[i * T + tid];
+                    float jxx, jxy, dxdl;
+                    if (KIND == PR_MODEL_OU) {          // d_x F = x - lam y
+                        jxx = 1.0f - a.ddt;
+                        jxy = a.lam * a.ddt;
+                        dxdl = a.ddt * yi;
+                    } else {                            // d_x F = x^3 - x + lam y
+                        jxx = 1.0f - a.ddt * (3.0f * xi * xi - 1.0f);
+                        jxy = -a.lam * a.ddt;
+                        dxdl = -a.ddt * yi;
+                    }
+                    const float jyx = a.rel, jyy = 1.0f - a.rel;
+                    p0 = fmaf(lx, dxdl, p0);                                   // d/d lambda
+                    p1 = fmaf(lx, -nx * a.inv2beta, p1);                       // d/d beta (noise amplitude)
+                    p2 = fmaf(ly, -a.rel_over_eps * (xi - yi) - ny * a.inv2eps, p2);   // d/d eps
+                    const float nlx = lx * jxx + ly * jyx;
+                    const float nly = lx * jxy + ly * jyy;
+                    lx = nlx;
+                    ly = nly;
+                }
+                g0 += (double)p0;
+                g1 += (double)p1;
+                g2 += (double)p2;
+            }
+        }
+        if (a.xbar0) a.xbar0[p] = (double)lx;
+        if (a.ybar0) a.ybar0[p] = (double)ly;
+        if (a.grad_pp) {
+            a.grad_pp[p * 3 + 0] = g0;
+            a.grad_pp[p * 3 + 1] = g1;
+            a.grad_pp[p * 3 + 2] = g2;
+        }
+    }
+    if (a.partial) {
+        // fixed-order block reduction of the three sums
+        __shared__ double red[3][kAdjThreads / 32];
+        double v[3] = {g0, g1, g2};
+        const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+            if (lane == 0) red[k][warp] = v[k];
+        }
+        __syncthreads();
+        if (tid < 3) {
+            double s = 0.0;
+            for (int w = 0; w < T / 32; ++w) s += red[tid][w];
+            a.partial[(size_t)blockIdx.x * 3 + tid] = s;
+        }
+    }
+}
+
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int64_t blocks, double* __restrict__ grad)
+{
+    __shared__ double red[3][256];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int64_t b = threadIdx.x; b < blocks; b += blockDim.x) {
+        s0 += partial[b * 3 + 0];
+        s1 += partial[b * 3 + 1];
+        s2 += partial[b * 3 + 2];
+    }
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    red[2][threadIdx.x] = s2;
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int i = 0; i < (int)blockDim.x; ++i) s += red[threadIdx.x][i];
+        grad[threadIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Order statistics: bitonic sort of (orderable float bits << 32 | index)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t float_order_bits(float v)
+{
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__global__ void make_keys_kernel(const float* __restrict__ x, int64_t n, int64_t padded, unsigned long long* keys)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < padded; i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = i < n ? (((unsigned long long)float_order_bits(x[i]) << 32) | (unsigned long long)i)
+                        : ~0ull;
+}
+
+__global__ void bitonic_step_kernel(unsigned long long* keys, int64_t padded, int64_t j, int64_t k)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < padded; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = i ^ j;
+        if (l > i) {
+            const unsigned long long a = keys[i], b = keys[l];
+            const bool up = (i & k) == 0;
+            if ((a > b) == up) {
+                keys[i] = b;
+                keys[l] = a;
+            }
+        }
+    }
+}
+
+__global__ void gather_ranks_kernel(const unsigned long long* __restrict__ keys, const int64_t* __restrict__ ranks,
+                                    int n_ranks, int64_t n, int64_t* __restrict__ idx)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_ranks) return;
+    const int64_t rk = ranks[r];
+    idx[r] = (rk >= 0 && rk < n) ? (int64_t)(keys[rk] & 0xFFFFFFFFull) : -1;   // -1: rank out of range
+}
+
+inline int64_t next_pow2(int64_t v)
+{
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace pr
+
+using namespace pr;
+
+extern "C" size_t pr_fine_adjoint_workspace(int64_t n, int32_t n_slices, int32_t steps, int32_t ckpt_every)
+{
+    if (n < 1 || n_slices < 1 || steps < 0 || ckpt_every < 1) return 0;
+    const int64_t total = (int64_t)n_slices * steps;
+    const int64_t n_ckpt = std::max<int64_t>(1, (total + ckpt_every - 1) / ckpt_every);
+    const int64_t blocks = (n + kAdjThreads - 1) / kAdjThreads;
+    return align256((size_t)n_ckpt * 2 * n * sizeof(float)) + align256((size_t)blocks * 3 * sizeof(double));
+}
+
+extern "C" pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, const float* x0, const float* y0,
+                                     int64_t n, int32_t slice_begin, int32_t n_slices, int32_t steps, double dt,
+                                     int32_t ckpt_every, float* x_T, float* y_T, const double* xbar_T,
+                                     const double* ybar_T, double* grad, double* xbar_0, double* ybar_0,
+                                     void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!model || !rng || !x0 || !y0 || !grad || !workspace) return PR_ERR_INVALID_ARG;
+    if (model->kind != PR_MODEL_OU && model->kind != PR_MODEL_DOUBLE_WELL) return PR_ERR_UNSUPPORTED;
+    if (model->fast_dim != 1) return PR_ERR_UNSUPPORTED;
+    if (!(model->beta > 0.0) || !(model->eps > 0.0) || !(model->tau_x > 0.0)) return PR_ERR_INVALID_ARG;
+    if (n < 1 || n > 0xFFFFFFFFll || n_slices < 1 || slice_begin < 0 || steps < 0 || ckpt_every < 1) return PR_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !isfinite(dt) || rng->problem_id >= (1u << 24)) return PR_ERR_INVALID_ARG;
+    if (ybar_T && !xbar_T) return PR_ERR_INVALID_ARG;
+    const size_t need = pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every);
+    if (workspace_bytes < need || ((uintptr_t)workspace & 255)) return PR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    AdjArgs a{};
+    a.x0 = x0;
+    a.y0 = y0;
+    a.n = n;
+    a.slice_begin = slice_begin;
+    a.steps = steps;
+    a.total = (int64_t)n_slices * steps;
+    a.ckpt = ckpt_every;
+    a.n_ckpt = std::max<int64_t>(1, (a.total + ckpt_every - 1) / ckpt_every);
+    const double drift_dt = dt / model->tau_x, relax = dt / model->eps;
+    const double sx = sqrt(2.0 * (1.0 / model->beta) / model->tau_x) * sqrt(dt);
+    const double sy = sqrt(2.0 / model->eps) * sqrt(dt);
+    a.lam = (float)model->lambda;
+    a.ddt = (float)drift_dt;
+    a.rel = (float)relax;
+    a.sxk = (float)(sx * 1.1774100225154746910);
+    a.syk = (float)(sy * 1.1774100225154746910);
+    a.inv2beta = (float)(0.5 / model->beta);
+    a.inv2eps = (float)(0.5 / model->eps);
+    a.rel_over_eps = (float)(dt / (model->eps * model->eps));
+    a.k0 = (uint32_t)(rng->seed & 0xFFFFFFFFull);
+    a.k1 = (uint32_t)(rng->seed >> 32);
+    a.chi = rng->problem_id << 8;
+    const int64_t blocks = (n + kAdjThreads - 1) / kAdjThreads;
+    a.ckpt_buf = static_cast<float*>(workspace);
+    const bool sum_mode = xbar_T != nullptr;
+    a.partial = sum_mode ? reinterpret_cast<double*>(static_cast<char*>(workspace) +
+                                                     align256((size_t)a.n_ckpt * 2 * n * sizeof(float)))
+                         : nullptr;
+    a.xT = x_T;
+    a.yT = y_T;
+    a.xbar = xbar_T;
+    a.ybar = ybar_T;
+    a.grad_pp = sum_mode ? nullptr : grad;
+    a.xbar0 = xbar_0;
+    a.ybar0 = ybar_0;
+    const size_t smem = (size_t)6 * kSub * kAdjThreads * sizeof(float);
+    if (model->kind == PR_MODEL_OU) {
+        PR_TRY_CUDA(cudaFuncSetAttribute(adjoint_kernel<PR_MODEL_OU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        adjoint_kernel<PR_MODEL_OU><<<(unsigned)blocks, kAdjThreads, smem, st>>>(a);
+    } else {
+        PR_TRY_CUDA(cudaFuncSetAttribute(adjoint_kernel<PR_MODEL_DOUBLE_WELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        adjoint_kernel<PR_MODEL_DOUBLE_WELL><<<(unsigned)blocks, kAdjThreads, smem, st>>>(a);
+    }
+    PR_CHECK_LAUNCH();
+    if (sum_mode) {
+        reduce_partials_kernel<<<1, 256, 0, st>>>(a.partial, blocks, grad);
+        PR_CHECK_LAUNCH();
+    }
+    return PR_OK;
+}
+
+extern "C" size_t pr_order_statistics_workspace(int64_t n)
+{
+    return n < 1 ? 0 : align256((size_t)next_pow2(n) * sizeof(unsigned long long));
+}
+
+extern "C" pr_status pr_order_statistics(const float* x, int64_t n, const int64_t* ranks, int32_t n_ranks,
+                                         int64_t* index_out, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (!x || !ranks || !index_out || !workspace || n < 1 || n > 0xFFFFFFFFll || n_ranks < 1) return PR_ERR_INVALID_ARG;
+    if (workspace_bytes < pr_order_statistics_workspace(n) || ((uintptr_t)workspace & 7)) return PR_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t padded = next_pow2(n);
+    auto* keys = static_cast<unsigned long long*>(workspace);
+    const int blocks = (int)std::min<int64_t>((padded + 255) / 256, 16 * (int64_t)num_sms());
+    make_keys_kernel<<<blocks, 256, 0, st>>>(x, n, padded, keys);
+    for (int64_t k = 2; k <= padded; k <<= 1)
+        for (int64_t j = k >> 1; j > 0; j >>= 1)
+            bitonic_step_kernel<<<blocks, 256, 0, st>>>(keys, padded, j, k);
+    gather_ranks_kernel<<<(n_ranks + 255) / 256, 256, 0, st>>>(keys, ranks, n_ranks, n, index_out);
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}

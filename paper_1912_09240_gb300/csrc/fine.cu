@@ -184,15 +184,9 @@ fine_f32_d1_kernel(FineArgs a, FineSmemOffsets so, int flags)
                 float q0, c0, s0, q1, c1, s1;
                 box_muller_qcs(w.x, w.y, q0, c0, s0);
                 box_muller_qcs(w.z, w.w, q1, c1, s1);
-                float xv = x[k], yv = y[k];
-                // step 2 mp: sx z0 = (q0 sxk) c0, sy z1 = (q0 syk) s0
-                float f = slow_force<KIND>(xv, yv, lam);
-                float xn = fmaf(q0 * sxk, c0, fmaf(-f, ddt, xv));
-                float yn = fmaf(q0 * syk, s0, fmaf(xv - yv, rel, yv));
-                // step 2 mp + 1
-                f = slow_force<KIND>(xn, yn, lam);
-                x[k] = fmaf(q1 * sxk, c1, fmaf(-f, ddt, xn));
-                y[k] = fmaf(q1 * syk, s1, fmaf(xn - yn, rel, yn));
+                // steps 2 mp and 2 mp + 1: sx z0 = (q sxk) cos, sy z1 = (q syk) sin
+                em_step_f32<KIND>(x[k], y[k], q0 * sxk, c0, q0 * syk, s0, lam, ddt, rel);
+                em_step_f32<KIND>(x[k], y[k], q1 * sxk, c1, q1 * syk, s1, lam, ddt, rel);
             }
         }
         if (a.steps & 1) {
@@ -201,10 +195,7 @@ fine_f32_d1_kernel(FineArgs a, FineSmemOffsets so, int flags)
                 const uint4 w = philox4x32_10(make_uint4((uint32_t)pairs, pid[k], slice, chi), k0, k1);
                 float q0, c0, s0;
                 box_muller_qcs(w.x, w.y, q0, c0, s0);
-                const float xv = x[k], yv = y[k];
-                const float f = slow_force<KIND>(xv, yv, lam);
-                x[k] = fmaf(q0 * sxk, c0, fmaf(-f, ddt, xv));
-                y[k] = fmaf(q0 * syk, s0, fmaf(xv - yv, rel, yv));
+                em_step_f32<KIND>(x[k], y[k], q0 * sxk, c0, q0 * syk, s0, lam, ddt, rel);
             }
         }
 #pragma unroll

@@ -118,6 +118,30 @@ __device__ __forceinline__ void box_muller_qcs(uint32_t w0, uint32_t w1, float& 
     __sincosf(th, &s, &c);
 }
 
+// One binary32 Euler-Maruyama step of the d = 1 families (Eqs. EMx/EMy with
+// tau_x folded into ddt = dt/tau_x, rel = dt/eps), the noise increments given
+// as products: sx dU = ax * cx, sy dV = ay * cy.  Written with explicit FMAs so
+// that every kernel taking this step produces the same bits.
+//   OU:          d_x F = x - lam y
+//   double well: d_x F = x^3 - x + lam y
+template <int KIND>
+__device__ __forceinline__ float slow_force_f32(float x, float y, float lam)
+{
+    if (KIND == PR_MODEL_OU) return fmaf(-lam, y, x);
+    return fmaf(lam, y, fmaf(x * x, x, -x));
+}
+
+template <int KIND>
+__device__ __forceinline__ void em_step_f32(float& x, float& y, float ax, float cx, float ay, float cy, float lam,
+                                            float ddt, float rel)
+{
+    const float f = slow_force_f32<KIND>(x, y, lam);
+    const float xn = fmaf(ax, cx, fmaf(-f, ddt, x));
+    const float yn = fmaf(ay, cy, fmaf(x - y, rel, y));
+    x = xn;
+    y = yn;
+}
+
 __device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, double& z0, double& z1)
 {
     const double u0 = uniform_f64(w0);

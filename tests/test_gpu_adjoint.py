@@ -1,0 +1,196 @@
+"""The pathwise adjoint (pr_fine_adjoint) and order statistics on the GPU
+against the FP64 oracle's tangent-linear derivatives and against central
+finite differences with common random numbers.
+
+Tolerances: per-particle sensitivities <= 2e-3 relative (binary32 state
+against FP64) to max(|value|, ensemble scale), ensemble gradients <= 5e-3
+relative against central differences (h = 1e-4, FP64 propagation on the
+GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1912_09240_gb300 import build as b
+    b.build()
+    from paper_1912_09240_gb300 import _lib
+    return _lib
+
+
+def _close(a, b, rel, abs_=0.0):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    scale = np.maximum(np.abs(b), np.max(np.abs(b)) * 1e-3)
+    return np.all(np.abs(a - b) <= rel * scale + abs_)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("slices,steps,ckpt", [(3, 40, 32), (2, 125, 256), (1, 1, 256), (4, 7, 5)])
+def test_per_particle_against_tangent(L, orc, kind, slices, steps, ckpt):
+    rng = np.random.default_rng(kind + steps)
+    n, dt = 1000, 1e-3
+    lam, beta, eps, tau = (1.0, 1.0, 0.1, 1.0) if kind == 0 else (0.5, 3.0, 0.05, 1.0)
+    x0 = rng.normal(1.0 if kind == 0 else -1.0, 0.3, n).astype(np.float32)
+    y0 = rng.normal(0.0, 1.0, n).astype(np.float32)
+    gm = L.Model(kind, 1, lam, beta, eps, tau)
+    om = orc.Model(kind, 1, lam, beta, eps, tau)
+    gx0 = torch.tensor(x0, device="cuda")
+    gy0 = torch.tensor(y0, device="cuda")
+    xT = torch.empty(n, dtype=torch.float32, device="cuda")
+    grads = torch.empty(n, 3, dtype=torch.float64, device="cuda")
+    xb0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    yb0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    ws = torch.empty(L.pr_fine_adjoint_workspace(n, slices, steps, ckpt), dtype=torch.uint8, device="cuda")
+    L.pr_fine_adjoint(gm, L.Rng(9, 2), gx0, gy0, n, 3, slices, steps, dt, ckpt, xT, None, None, None, grads,
+                      xb0, yb0, ws)
+    torch.cuda.synchronize()
+    X, Y, dX, dY = orc.fine_tangent(om, 9, x0.astype(np.float64), y0.astype(np.float64), 3, slices, steps, dt,
+                                    problem=2)
+    assert np.all(np.abs(xT.cpu().numpy() - X) <= 2e-3 * np.maximum(np.abs(X), 1.0))
+    g = grads.cpu().numpy()
+    for k in range(3):
+        assert _close(g[:, k], dX[:, k], 2e-3, 1e-7), k
+    assert _close(xb0.cpu().numpy(), dX[:, 3], 2e-3, 1e-7)
+    assert _close(yb0.cpu().numpy(), dX[:, 4], 2e-3, 1e-7)
+    # the adjoint's forward pass takes exactly pr_fine_propagate's steps
+    x = gx0.reshape(1, n).clone()
+    y = gy0.reshape(1, 1, n).clone()
+    for s in range(slices):
+        L.pr_fine_propagate(gm, L.PR_F32, L.Rng(9, 2), x, y, False, x, y, n, 3 + s, 1, steps, dt)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(x.reshape(n).cpu().numpy(), xT.cpu().numpy())
+
+
+def test_seeded_sum_equals_contracted_per_particle(L):
+    n, slices, steps, dt = 5000, 2, 100, 1e-3
+    gm = L.Model(0, 1, 0.8, 1.5, 0.1, 1.0)
+    rng = np.random.default_rng(1)
+    x0 = torch.tensor(rng.normal(1, 0.2, n), dtype=torch.float32, device="cuda")
+    y0 = torch.tensor(rng.normal(0, 1, n), dtype=torch.float32, device="cuda")
+    seeds = torch.tensor(rng.normal(0, 1, n), dtype=torch.float64, device="cuda")
+    ws = torch.empty(L.pr_fine_adjoint_workspace(n, slices, steps, 256), dtype=torch.uint8, device="cuda")
+    per = torch.empty(n, 3, dtype=torch.float64, device="cuda")
+    L.pr_fine_adjoint(gm, L.Rng(0), x0, y0, n, 0, slices, steps, dt, 256, None, None, None, None, per, None, None, ws)
+    tot = torch.zeros(3, dtype=torch.float64, device="cuda")
+    L.pr_fine_adjoint(gm, L.Rng(0), x0, y0, n, 0, slices, steps, dt, 256, None, None, seeds, None, tot, None, None, ws)
+    tot2 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    L.pr_fine_adjoint(gm, L.Rng(0), x0, y0, n, 0, slices, steps, dt, 256, None, None, seeds, None, tot2, None, None, ws)
+    torch.cuda.synchronize()
+    ref = (seeds[:, None] * per).sum(0).cpu().numpy()
+    np.testing.assert_allclose(tot.cpu().numpy(), ref, rtol=1e-5)
+    np.testing.assert_array_equal(tot.cpu().numpy(), tot2.cpu().numpy())   # deterministic reduction
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_second_moment_gradient_against_central_differences(L, kind):
+    """Central differences (h = 1e-4) of E[X_T^2] with common random numbers,
+    propagated in FP64 on the GPU, against the binary32 adjoint."""
+    from paper_1912_09240_gb300.adjoint import second_moment_gradient
+    n, slices, steps, dt = 1 << 16, 2, 1000, 1e-4
+    lam, beta, eps = (1.0, 1.0, 0.1) if kind == 0 else (0.5, 3.0, 0.01)
+    rng = np.random.default_rng(3)
+    x0n = rng.normal(1.0 if kind == 0 else -1.0, 0.1, n)
+    y0n = rng.normal(0.0, 1.0, n) if kind == 0 else x0n.copy()
+    x0 = torch.tensor(x0n, dtype=torch.float32, device="cuda")
+    y0 = torch.tensor(y0n, dtype=torch.float32, device="cuda")
+    val, grad = second_moment_gradient(L.Model(kind, 1, lam, beta, eps), L.Rng(0), x0, y0, 0, slices, steps, dt)
+    torch.cuda.synchronize()
+
+    def second_moment(l_, b_, e_):
+        x = x0.double().reshape(1, n).clone()
+        y = y0.double().reshape(1, 1, n).clone()
+        for s in range(slices):
+            L.pr_fine_propagate(L.Model(kind, 1, l_, b_, e_), L.PR_F64, L.Rng(0), x, y, False, x, y, n, s, 1,
+                                steps, dt)
+        return float((x ** 2).mean().item())
+
+    h = 1e-4
+    fd = [(second_moment(lam + h, beta, eps) - second_moment(lam - h, beta, eps)) / (2 * h),
+          (second_moment(lam, beta + h, eps) - second_moment(lam, beta - h, eps)) / (2 * h),
+          (second_moment(lam, beta, eps + h * eps) - second_moment(lam, beta, eps - h * eps)) / (2 * h * eps)]
+    g = grad.cpu().numpy()
+    for k in range(3):
+        assert abs(g[k] - fd[k]) <= 5e-3 * max(abs(fd[k]), 1e-3 * max(abs(v) for v in fd)), (k, g[k], fd[k])
+    assert abs(val.item() - second_moment(lam, beta, eps)) < 1e-4
+
+
+def test_autograd_function_matches_adjoint(L):
+    from paper_1912_09240_gb300.adjoint import fine_em
+    n, slices, steps, dt = 4096, 2, 50, 1e-3
+    rng = np.random.default_rng(4)
+    x0 = torch.tensor(rng.normal(1, 0.2, n), dtype=torch.float32, device="cuda", requires_grad=True)
+    y0 = torch.tensor(rng.normal(0, 1, n), dtype=torch.float32, device="cuda", requires_grad=True)
+    theta = torch.tensor([0.9, 1.2, 0.1], dtype=torch.float64, device="cuda", requires_grad=True)
+    xT, yT = fine_em(theta, x0, y0, 0, 1.0, L.Rng(5), 0, slices, steps, dt)
+    loss = (xT.double() ** 2).mean() + 0.5 * (xT.double() * yT.double()).mean()
+    loss.backward()
+    torch.cuda.synchronize()
+    # reference: the same loss through the oracle's tangent-linear
+    from oracle import oracle as orc
+    om = orc.Model(0, 1, 0.9, 1.2, 0.1)
+    X, Y, dX, dY = orc.fine_tangent(om, 5, x0.detach().cpu().numpy().astype(np.float64),
+                                    y0.detach().cpu().numpy().astype(np.float64), 0, slices, steps, dt)
+    dl = ((2 * X + 0.5 * Y)[:, None] * dX + (0.5 * X)[:, None] * dY) / n
+    np.testing.assert_allclose(theta.grad.cpu().numpy(), dl[:, :3].sum(0), rtol=3e-3)
+    np.testing.assert_allclose(x0.grad.double().cpu().numpy(), dl[:, 3], rtol=3e-3, atol=1e-9)
+    np.testing.assert_allclose(y0.grad.double().cpu().numpy(), dl[:, 4], rtol=3e-3, atol=1e-9)
+
+
+def test_order_statistics(L):
+    rng = np.random.default_rng(6)
+    for n in (1, 7, 1000, 1 << 16, 100_003):
+        x = rng.normal(0, 1, n).astype(np.float32)
+        if n > 10:
+            x[:10] = x[10]                      # ties are broken by particle index
+        ranks = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 50)]))
+        gx = torch.tensor(x, device="cuda")
+        gr = torch.tensor(np.concatenate([ranks, [n, -1]]), dtype=torch.int64, device="cuda")
+        idx = torch.empty(gr.numel(), dtype=torch.int64, device="cuda")
+        ws = torch.empty(L.pr_order_statistics_workspace(n), dtype=torch.uint8, device="cuda")
+        L.pr_order_statistics(gx, n, gr, gr.numel(), idx, ws)
+        torch.cuda.synchronize()
+        order = np.lexsort((np.arange(n), x))
+        got = idx.cpu().numpy()
+        np.testing.assert_array_equal(got[:-2], order[ranks])
+        assert got[-2] == -1 and got[-1] == -1
+
+
+def test_adjoint_workload_sampled_at_full_size(L, orc):
+    """The adjoint workload at full size (2^20 particles, 20 slices x 1000
+    steps, checkpoints every 256 steps): sampled particles' sensitivities
+    against the oracle's tangent-linear on those particles (their own keys),
+    and the 512-point quantile function's gradient at the ranked particles."""
+    import workloads
+    from paper_1912_09240_gb300.adjoint import quantile_gradient
+    w = workloads.ADJOINT
+    x0, y0 = workloads.initial_ensemble(w)
+    gx0 = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    gy0 = torch.tensor(y0[0], dtype=torch.float32, device="cuda")
+    model = L.Model(w.kind, 1, w.lam, w.beta, w.eps, w.tau_x)
+    Q, dQ, idx = quantile_gradient(model, L.Rng(w.seed), gx0, gy0, 0, w.K, w.steps, w.step_dt)
+    torch.cuda.synchronize()
+    idx = idx.cpu().numpy()
+    Q = Q.cpu().numpy()
+    assert np.all(np.diff(Q) >= 0)
+    sample = np.unique(np.concatenate([idx[::32], [idx[0], idx[-1]]])).astype(np.uint32)
+    om = orc.Model(w.kind, 1, w.lam, w.beta, w.eps, w.tau_x)
+    x0f = x0.astype(np.float32).astype(np.float64)
+    y0f = y0[0].astype(np.float32).astype(np.float64)
+    X, Y, dX, dY = orc.fine_tangent(om, w.seed, x0f[sample], y0f[sample], 0, w.K, w.steps, w.step_dt, ids=sample)
+    pos = {int(p): i for i, p in enumerate(sample)}
+    dq = dQ.cpu().numpy()
+    # relative to max(|value|, RMS over the sampled particles): a sensitivity
+    # that crosses zero is compared on the scale of the ensemble's sensitivities
+    rms = np.sqrt((dX[:, :3] ** 2).mean(axis=0))
+    for j, p in enumerate(idx):
+        if int(p) in pos:
+            i = pos[int(p)]
+            assert abs(Q[j] - X[i]) <= 2e-3 * max(abs(X[i]), 1.0)
+            for k in range(3):
+                assert abs(dq[j, k] - dX[i, k]) <= 2e-3 * max(abs(dX[i, k]), rms[k]), (j, k, dq[j, k], dX[i, k])
