@@ -24,7 +24,9 @@
  *    x_lo = e_0 < ... < e_I = x_hi, Section 2.2.2) is passed as its
  *    piecewise-linear CDF sampled at the I+1 edges (Eq. discr_cdf), double,
  *    C_0 = 0, C_I = 1, bin masses rho_i = C_{i+1} - C_i.
- *  - No call allocates device memory except pr_coarse_create.
+ *  - No call allocates device memory except pr_coarse_create; calls that need
+ *    scratch take it from the caller (workspace arguments), except
+ *    pr_fine_adjoint_noalloc, which uses a fixed array inside the library.
  *  - Calls on distinct handles are thread-safe.
  */
 #ifndef PR_H
@@ -268,6 +270,33 @@ pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, const float*
                           int32_t ckpt_every, float* x_T, float* y_T, const double* xbar_T,
                           const double* ybar_T, double* grad, double* xbar_0, double* ybar_0,
                           void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * pr_fine_adjoint without any device allocation by the library or the
+ * caller.  The paper has no counterpart: this serves callers that cannot
+ * allocate device memory while they run -- a real-time control loop that
+ * forbids cudaMalloc/cudaFree after start-up because they can block and
+ * synchronise the device, or a host whose device memory belongs to another
+ * allocator.  Arguments and results are those of pr_fine_adjoint; the
+ * checkpoints and partial sums live instead in a fixed 32 MiB device array
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits (pr_fine_adjoint_noalloc_capacity() gives its size).
+ *  - A problem whose pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every)
+ *    exceeds the capacity is rejected with PR_ERR_NOMEM before anything runs.
+ *  - The first call on a device looks up the array's device address there
+ *    (the device must be current); make that first call before any stream
+ *    capture.
+ *  - All calls share the one array and it keeps the last call's contents.
+ *    Every word a call reads it has written first, so nothing needs clearing;
+ *    calls that overlap on the GPU (other streams, other threads) race on the
+ *    array and must be serialised by the caller.
+ */
+size_t pr_fine_adjoint_noalloc_capacity(void);
+pr_status pr_fine_adjoint_noalloc(const pr_model* model, const pr_rng* rng, const float* x0, const float* y0,
+                                  int64_t n, int32_t slice_begin, int32_t n_slices, int32_t steps, double dt,
+                                  int32_t ckpt_every, float* x_T, float* y_T, const double* xbar_T,
+                                  const double* ybar_T, double* grad, double* xbar_0, double* ybar_0,
+                                  void* stream);
 
 /*
  * Order statistics of n floats: index_out[r] = the index of the particle of

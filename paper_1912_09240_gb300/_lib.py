@@ -25,6 +25,7 @@ EXPORTED = (
     "pr_set_tiles_per_cta", "pr_restrict", "pr_counts_to_cdf", "pr_match", "pr_coarse_create", "pr_coarse_destroy",
     "pr_coarse_matrix", "pr_coarse_fp", "pr_parareal_update", "pr_iterate", "pr_w1",
     "pr_fine_adjoint_workspace", "pr_fine_adjoint", "pr_order_statistics_workspace", "pr_order_statistics",
+    "pr_fine_adjoint_noalloc_capacity", "pr_fine_adjoint_noalloc",
 )
 
 
@@ -120,10 +121,14 @@ def lib() -> ctypes.CDLL:
     L.pr_order_statistics_workspace.argtypes = [i64]
     L.pr_order_statistics_workspace.restype = ctypes.c_size_t
     L.pr_order_statistics.argtypes = [vp, i64, vp, i32, vp, vp, ctypes.c_size_t, vp]
+    L.pr_fine_adjoint_noalloc_capacity.argtypes = []
+    L.pr_fine_adjoint_noalloc_capacity.restype = ctypes.c_size_t
+    L.pr_fine_adjoint_noalloc.argtypes = [P(_Model), P(_Rng), vp, vp, i64, i32, i32, i32, d, i32, vp, vp, vp, vp,
+                                          vp, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("pr_status_string", "pr_version", "pr_set_particles_per_thread",
                         "pr_set_tiles_per_cta", "pr_fine_adjoint_workspace",
-                        "pr_order_statistics_workspace"):
+                        "pr_order_statistics_workspace", "pr_fine_adjoint_noalloc_capacity"):
             getattr(L, name).restype = i32
     _lib = L
     return L
@@ -262,3 +267,19 @@ def pr_order_statistics(x, n: int, ranks, n_ranks: int, index_out, workspace, st
     wbytes = workspace.numel() * workspace.element_size()
     _check("pr_order_statistics", lib().pr_order_statistics(_ptr(x), n, _ptr(ranks), n_ranks, _ptr(index_out),
                                                             _ptr(workspace), wbytes, _stream(stream)))
+
+
+def pr_fine_adjoint_noalloc_capacity() -> int:
+    return lib().pr_fine_adjoint_noalloc_capacity()
+
+
+def pr_fine_adjoint_noalloc(model: Model, rng: Rng, x0, y0, n: int, slice_begin: int, n_slices: int, steps: int,
+                            dt: float, ckpt_every: int, x_T, y_T, xbar_T, ybar_T, grad, xbar_0, ybar_0,
+                            stream=None):
+    """pr_fine_adjoint with its scratch in the library's fixed device array
+    (for callers that must not allocate device memory while they run)."""
+    m, r = model.c(), rng.c()
+    _check("pr_fine_adjoint_noalloc",
+           lib().pr_fine_adjoint_noalloc(ctypes.byref(m), ctypes.byref(r), _ptr(x0), _ptr(y0), n, slice_begin,
+                                         n_slices, steps, dt, ckpt_every, _ptr(x_T), _ptr(y_T), _ptr(xbar_T),
+                                         _ptr(ybar_T), _ptr(grad), _ptr(xbar_0), _ptr(ybar_0), _stream(stream)))

@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "pr_common.cuh"
 
@@ -393,5 +394,119 @@ extern "C" pr_status pr_order_statistics(const float* x, int64_t n, const int64_
             bitonic_step_kernel<<<blocks, 256, 0, st>>>(keys, padded, j, k);
     gather_ranks_kernel<<<(n_ranks + 255) / 256, 256, 0, st>>>(keys, ranks, n_ranks, n, index_out);
     PR_CHECK_LAUNCH();
+    return PR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint without any device allocation.
+//
+// Some callers cannot allocate device memory once they are running: a
+// real-time control loop (the paper's motivating setting of model-predictive
+// control) that forbids cudaMalloc/cudaFree after start-up because they can
+// block and synchronise the device, or a host application whose device memory
+// is owned by another allocator.  pr_fine_adjoint_noalloc serves them: its
+// checkpoints and partial sums live in the fixed array below, which every GPU
+// that loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace pr {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_adjoint_scratch[kNoAllocScratchBytes];
+
+// The array's device address on the current device.  Looked up once per
+// device (with that device current) and kept.
+static pr_status adjoint_scratch_address(void** out)
+{
+    static std::mutex mu;
+    static void* addr[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return PR_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_adjoint_scratch) != cudaSuccess || !p) return PR_ERR_CUDA;
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return PR_OK;
+}
+
+}  // namespace pr
+
+extern "C" size_t pr_fine_adjoint_noalloc_capacity(void) { return kNoAllocScratchBytes; }
+
+extern "C" pr_status pr_fine_adjoint_noalloc(const pr_model* model, const pr_rng* rng, const float* x0,
+                                             const float* y0, int64_t n, int32_t slice_begin, int32_t n_slices,
+                                             int32_t steps, double dt, int32_t ckpt_every, float* x_T, float* y_T,
+                                             const double* xbar_T, const double* ybar_T, double* grad,
+                                             double* xbar_0, double* ybar_0, void* stream)
+{
+    if (!model || !rng || !x0 || !y0 || !grad) return PR_ERR_INVALID_ARG;
+    if (model->kind != PR_MODEL_OU && model->kind != PR_MODEL_DOUBLE_WELL) return PR_ERR_UNSUPPORTED;
+    if (model->fast_dim != 1) return PR_ERR_UNSUPPORTED;
+    if (!(model->beta > 0.0) || !(model->eps > 0.0) || !(model->tau_x > 0.0)) return PR_ERR_INVALID_ARG;
+    if (n < 1 || n > 0xFFFFFFFFll || n_slices < 1 || slice_begin < 0 || steps < 0 || ckpt_every < 1) return PR_ERR_INVALID_ARG;
+    if (!(dt > 0.0) || !isfinite(dt) || rng->problem_id >= (1u << 24)) return PR_ERR_INVALID_ARG;
+    if (ybar_T && !xbar_T) return PR_ERR_INVALID_ARG;
+    // the problem must fit the fixed array (checked before anything else runs)
+    if (pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every) > kNoAllocScratchBytes) return PR_ERR_NOMEM;
+    void* scratch = nullptr;
+    const pr_status got = adjoint_scratch_address(&scratch);
+    if (got != PR_OK) return got;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    AdjArgs a{};
+    a.x0 = x0;
+    a.y0 = y0;
+    a.n = n;
+    a.slice_begin = slice_begin;
+    a.steps = steps;
+    a.total = (int64_t)n_slices * steps;
+    a.ckpt = ckpt_every;
+    a.n_ckpt = std::max<int64_t>(1, (a.total + ckpt_every - 1) / ckpt_every);
+    const double drift_dt = dt / model->tau_x, relax = dt / model->eps;
+    const double sx = sqrt(2.0 * (1.0 / model->beta) / model->tau_x) * sqrt(dt);
+    const double sy = sqrt(2.0 / model->eps) * sqrt(dt);
+    a.lam = (float)model->lambda;
+    a.ddt = (float)drift_dt;
+    a.rel = (float)relax;
+    a.sxk = (float)(sx * 1.1774100225154746910);
+    a.syk = (float)(sy * 1.1774100225154746910);
+    a.inv2beta = (float)(0.5 / model->beta);
+    a.inv2eps = (float)(0.5 / model->eps);
+    a.rel_over_eps = (float)(dt / (model->eps * model->eps));
+    a.k0 = (uint32_t)(rng->seed & 0xFFFFFFFFull);
+    a.k1 = (uint32_t)(rng->seed >> 32);
+    a.chi = rng->problem_id << 8;
+    const int64_t blocks = (n + kAdjThreads - 1) / kAdjThreads;
+    // checkpoints first, then the per-block partial sums; every word is
+    // written before it is read in the same call, so nothing is cleared
+    a.ckpt_buf = static_cast<float*>(scratch);
+    const bool sum_mode = xbar_T != nullptr;
+    a.partial = sum_mode ? reinterpret_cast<double*>(static_cast<char*>(scratch) +
+                                                     align256((size_t)a.n_ckpt * 2 * n * sizeof(float)))
+                         : nullptr;
+    a.xT = x_T;
+    a.yT = y_T;
+    a.xbar = xbar_T;
+    a.ybar = ybar_T;
+    a.grad_pp = sum_mode ? nullptr : grad;
+    a.xbar0 = xbar_0;
+    a.ybar0 = ybar_0;
+    const size_t smem = (size_t)6 * kSub * kAdjThreads * sizeof(float);
+    if (model->kind == PR_MODEL_OU) {
+        PR_TRY_CUDA(cudaFuncSetAttribute(adjoint_kernel<PR_MODEL_OU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        adjoint_kernel<PR_MODEL_OU><<<(unsigned)blocks, kAdjThreads, smem, st>>>(a);
+    } else {
+        PR_TRY_CUDA(cudaFuncSetAttribute(adjoint_kernel<PR_MODEL_DOUBLE_WELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        adjoint_kernel<PR_MODEL_DOUBLE_WELL><<<(unsigned)blocks, kAdjThreads, smem, st>>>(a);
+    }
+    PR_CHECK_LAUNCH();
+    if (sum_mode) {
+        reduce_partials_kernel<<<1, 256, 0, st>>>(a.partial, blocks, grad);
+        PR_CHECK_LAUNCH();
+    }
     return PR_OK;
 }
