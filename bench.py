@@ -270,6 +270,88 @@ def run_ours(args):
                 "fp32_over_fp64": (fine_rate / fp64_rate) if fine_rate else None,
                 "sample": f"FP64 fine kernel, {w.N} particles x 2 slices x {w.steps} steps"}
 
+    # convergence: iterations until max_n W1(rho_k^n, R X_serial^n) <= 1e-3,
+    # against the serial fine solution with the same random numbers
+    conv = None
+    if not args.no_conv:
+        _, _, rho_ser = solver.serial_reference()
+        solver.set_initial(x0t, y0t)
+        w1_hist, k_star = [], None
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for k in range(1, w.iters + 1):
+            solver.iterate()
+            w1k = float(solver.w1_to(rho_ser).max().item())
+            w1_hist.append(w1k)
+            if k_star is None and w1k <= 1e-3:
+                k_star = k
+                c1.record(stream)
+        torch.cuda.synchronize()
+        conv = {"w1_target": 1e-3, "iterations_to_target": k_star, "max_w1_per_iteration": w1_hist,
+                "iteration_ms": ms,
+                "time_to_target_ms": (c0.elapsed_time(c1) if k_star else None),
+                "note": "W1 between the parareal macroscopic states and the restriction of the serial fine "
+                        "solution with the same random numbers, max over slices; time includes the per-"
+                        "iteration W1 reduction"}
+        # FP32 against the plain FP64 path on a paired smaller run (2^16 particles, 10 slices, 3 iterations)
+        ws_ = w.scaled(N=1 << 16, K=10, T=w.slice_dt * 10, iters=3)
+        x0s, y0s = workloads.initial_ensemble(ws_)
+        rhos = {}
+        for prec in (L.PR_F32, L.PR_F64):
+            dty = torch.float32 if prec == L.PR_F32 else torch.float64
+            sv = PararealSolver(model, grid, ws_.N, ws_.K, ws_.steps, ws_.step_dt, precision=prec,
+                                rng=L.Rng(w.seed, rank), device=str(dev))
+            sv.set_initial(torch.tensor(x0s, dtype=dty, device=dev), torch.tensor(y0s, dtype=dty, device=dev))
+            for _ in range(ws_.iters):
+                sv.iterate()
+            rhos[prec] = sv.rho.clone()
+            sv.close()
+        wv = torch.empty(ws_.K + 1, dtype=torch.float64, device=dev)
+        L.pr_w1(grid, ws_.K + 1, rhos[L.PR_F32], rhos[L.PR_F64], wv)
+        conv["fp32_vs_fp64_max_w1"] = float(wv.max().item())
+        conv["fp32_vs_fp64_case"] = "2^16 particles, 10 slices x 1000 steps, 3 iterations"
+
+    # batched serving: 64 independent OU problems with uneven eps, lambda and
+    # particle counts, one persistent launch per iteration, graph-replayed,
+    # scheduling picked by the autotuner
+    batched = None
+    if not args.no_batch:
+        from paper_1912_09240_gb300.batch import BatchSolver
+        bw = workloads.batched_problems()
+        probs, bx, by = [], [], []
+        for pw in bw.problems:
+            probs.append(L.Problem(L.Model(pw.kind, 1, pw.lam, pw.beta, pw.eps), L.Grid(pw.bins, pw.lo, pw.hi),
+                                   pw.N, pw.K, pw.steps, pw.step_dt, pw.seed))
+            xx, yy = workloads.initial_ensemble(pw)
+            bx.append(xx.astype(np.float32))
+            by.append(yy[0].astype(np.float32))
+        bs = BatchSolver(probs, device=str(dev))
+        bs.set_initial(bx, by)
+        t_tune0 = time.perf_counter()
+        tuned_ms = bs.tune(steps_div=8)
+        tune_s = time.perf_counter() - t_tune0
+        bs.set_initial(bx, by)
+        bs.iterate()   # zeroth -> first iteration (eager)
+        bs.iterate()   # first graph replay (captures)
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nb = 3
+        b0.record(stream)
+        for _ in range(nb):
+            bs.iterate()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bms = b0.elapsed_time(b1) / nb
+        ppt, work, items = bs.config()
+        batched = {"workload": bw.name, "problems": len(probs),
+                   "particle_steps_per_iteration": bs.particle_steps,
+                   "iteration_ms": bms, "particle_steps_per_s": bs.particle_steps / (bms / 1e3),
+                   "graph_replayed": True, "tuned": {"particles_per_thread": ppt, "item_particle_steps": work,
+                                                      "items": items, "tune_s": tune_s,
+                                                      "trial_ms": tuned_ms},
+                   "status": bs.status()}
+        bs.close()
+
     if rank != 0:
         if dist:
             dist.barrier()
@@ -308,6 +390,8 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "fp64_vs_fp32": fp64,
+        "convergence": conv,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
     solver.close()
@@ -325,6 +409,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU sample")
+    ap.add_argument("--no-conv", action="store_true", help="skip the convergence study")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-serving leg")
     ap.add_argument("--n", type=int, default=None, help="particles (smaller case for profiling)")
     ap.add_argument("--k", type=int, default=None, help="slices (smaller case for profiling)")
     args = ap.parse_args()

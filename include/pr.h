@@ -311,6 +311,66 @@ pr_status pr_order_statistics(const float* x, int64_t n, const int64_t* ranks, i
                               int64_t* index_out, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Batched serving: many independent micro-macro parareal problems advanced
+ * together, one parareal iteration of the whole batch per pr_batch_iterate.
+ * Problem p draws its random numbers with problem_id = p (so a batch run of
+ * problem p equals a single-problem run with pr_rng{seed, p}, bit for bit).
+ * FP32 state, fast_dim = 1, families PR_MODEL_OU and PR_MODEL_DOUBLE_WELL,
+ * bins <= 1024.  The plan owns every buffer (allocated by pr_batch_create):
+ * ensembles, CDFs, one coarse propagator per problem, the work list.
+ *
+ * One iteration = a persistent fine kernel whose CTAs take work items
+ * (problem, slice, particle range of about `item_work` particle-steps) from
+ * an atomic counter, largest first; counts -> CDFs; the coarse step on every
+ * start state; the serial update, one CTA per problem.  From the second
+ * iteration on it is replayed as a CUDA graph.  Calls on one plan must not
+ * overlap.
+ */
+typedef struct {
+    pr_model model;
+    pr_grid grid;
+    int64_t n;          /* particles */
+    int32_t n_slices;   /* K */
+    int32_t steps;      /* EM steps per slice */
+    double dt;          /* EM step */
+    uint64_t seed;      /* Philox key */
+} pr_problem;
+
+/* Creates the plan (synchronises `stream`). */
+pr_status pr_batch_create(const pr_problem* problems, int32_t n_problems, pr_iterator iterator,
+                          pr_quantile_mode qmode, void** plan, void* stream);
+pr_status pr_batch_destroy(void* plan);
+
+/* Particle-steps of one iteration of the whole batch. */
+int64_t pr_batch_particle_steps(void* plan);
+
+/* Initial ensembles, packed: problem p occupies [off_p, off_p + n_p) of x0 and
+ * y0 (device, float), off_p = n_0 + ... + n_{p-1}.  Runs the restriction of
+ * X_0 and the zeroth iteration (serial coarse sweep). */
+pr_status pr_batch_set_initial(void* plan, const float* x0, const float* y0, void* stream);
+
+/* One parareal iteration of every problem. */
+pr_status pr_batch_iterate(void* plan, void* stream);
+
+/* Copies of a problem's state: rho_k^n as CDFs [K+1][bins+1] (device double);
+ * the latest fine end states Xbar^{n+1}, n = 0..K-1, [K][n] each (device float). */
+pr_status pr_batch_rho(void* plan, int32_t problem, double* out, void* stream);
+pr_status pr_batch_fine_state(void* plan, int32_t problem, float* x_out, float* y_out, void* stream);
+
+/* Largest status word over the problems (0 = PR_OK, else PR_ERR_NUMERIC);
+ * synchronises `stream`. */
+pr_status pr_batch_status(void* plan, int32_t* worst, void* stream);
+
+/* Scheduling knobs: particles per thread (1, 2, 4) and the work per item in
+ * particle-steps.  pr_batch_tune times the fine kernel for a grid of both
+ * (each trial at ceil(steps / steps_div) steps per item, after
+ * pr_batch_set_initial; trials do not disturb the iteration state), keeps
+ * the fastest, and reports its time.  Results do not depend on the knobs. */
+pr_status pr_batch_set_config(void* plan, int32_t ppt, double item_work);
+pr_status pr_batch_get_config(void* plan, int32_t* ppt, double* item_work, int32_t* n_items);
+pr_status pr_batch_tune(void* plan, int32_t steps_div, double* best_ms, void* stream);
+
+/*
  * W1 distance between pairs of macroscopic states on the same grid, each read
  * as its piecewise-linear CDF: integral of |C1 - C2| over [x_lo, x_hi].
  *   c1, c2 (device) [n_vec][bins+1]; w1 (device) [n_vec] doubles.

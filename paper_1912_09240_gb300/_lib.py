@@ -26,6 +26,9 @@ EXPORTED = (
     "pr_coarse_matrix", "pr_coarse_fp", "pr_parareal_update", "pr_iterate", "pr_w1",
     "pr_fine_adjoint_workspace", "pr_fine_adjoint", "pr_order_statistics_workspace", "pr_order_statistics",
     "pr_fine_adjoint_noalloc_capacity", "pr_fine_adjoint_noalloc",
+    "pr_batch_create", "pr_batch_destroy", "pr_batch_particle_steps", "pr_batch_set_initial", "pr_batch_iterate",
+    "pr_batch_rho", "pr_batch_fine_state", "pr_batch_status", "pr_batch_set_config", "pr_batch_get_config",
+    "pr_batch_tune",
 )
 
 
@@ -46,6 +49,11 @@ class _Grid(ctypes.Structure):
 
 class _Rng(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("problem_id", ctypes.c_uint32)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("model", _Model), ("grid", _Grid), ("n", ctypes.c_int64), ("n_slices", ctypes.c_int32),
+                ("steps", ctypes.c_int32), ("dt", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
 @dataclass(frozen=True)
@@ -78,6 +86,21 @@ class Rng:
 
     def c(self) -> _Rng:
         return _Rng(self.seed, self.problem_id)
+
+
+@dataclass(frozen=True)
+class Problem:
+    """One problem of a batch (include/pr.h, pr_problem)."""
+    model: Model
+    grid: Grid
+    n: int
+    n_slices: int
+    steps: int
+    dt: float
+    seed: int = 0
+
+    def c(self) -> _Problem:
+        return _Problem(self.model.c(), self.grid.c(), self.n, self.n_slices, self.steps, self.dt, self.seed)
 
 
 _lib = None
@@ -125,10 +148,23 @@ def lib() -> ctypes.CDLL:
     L.pr_fine_adjoint_noalloc_capacity.restype = ctypes.c_size_t
     L.pr_fine_adjoint_noalloc.argtypes = [P(_Model), P(_Rng), vp, vp, i64, i32, i32, i32, d, i32, vp, vp, vp, vp,
                                           vp, vp, vp, vp]
+    L.pr_batch_create.argtypes = [P(_Problem), i32, i32, i32, P(vp), vp]
+    L.pr_batch_destroy.argtypes = [vp]
+    L.pr_batch_particle_steps.argtypes = [vp]
+    L.pr_batch_particle_steps.restype = i64
+    L.pr_batch_set_initial.argtypes = [vp, vp, vp, vp]
+    L.pr_batch_iterate.argtypes = [vp, vp]
+    L.pr_batch_rho.argtypes = [vp, i32, vp, vp]
+    L.pr_batch_fine_state.argtypes = [vp, i32, vp, vp, vp]
+    L.pr_batch_status.argtypes = [vp, P(i32), vp]
+    L.pr_batch_set_config.argtypes = [vp, i32, d]
+    L.pr_batch_get_config.argtypes = [vp, P(i32), P(d), P(i32)]
+    L.pr_batch_tune.argtypes = [vp, i32, P(d), vp]
     for name in EXPORTED:
         if name not in ("pr_status_string", "pr_version", "pr_set_particles_per_thread",
                         "pr_set_tiles_per_cta", "pr_fine_adjoint_workspace",
-                        "pr_order_statistics_workspace", "pr_fine_adjoint_noalloc_capacity"):
+                        "pr_order_statistics_workspace", "pr_fine_adjoint_noalloc_capacity",
+                        "pr_batch_particle_steps"):
             getattr(L, name).restype = i32
     _lib = L
     return L
@@ -283,3 +319,60 @@ def pr_fine_adjoint_noalloc(model: Model, rng: Rng, x0, y0, n: int, slice_begin:
            lib().pr_fine_adjoint_noalloc(ctypes.byref(m), ctypes.byref(r), _ptr(x0), _ptr(y0), n, slice_begin,
                                          n_slices, steps, dt, ckpt_every, _ptr(x_T), _ptr(y_T), _ptr(xbar_T),
                                          _ptr(ybar_T), _ptr(grad), _ptr(xbar_0), _ptr(ybar_0), _stream(stream)))
+
+
+def pr_batch_create(problems, iterator: int = PR_ITER_QUANTILE, qmode: int = PR_QMODE_TWO_SIDED,
+                    stream=None) -> int:
+    arr = (_Problem * len(problems))(*[p.c() for p in problems])
+    h = ctypes.c_void_p()
+    _check("pr_batch_create", lib().pr_batch_create(arr, len(problems), iterator, qmode, ctypes.byref(h),
+                                                    _stream(stream)))
+    return h.value
+
+
+def pr_batch_destroy(plan: int):
+    _check("pr_batch_destroy", lib().pr_batch_destroy(plan))
+
+
+def pr_batch_particle_steps(plan: int) -> int:
+    return lib().pr_batch_particle_steps(plan)
+
+
+def pr_batch_set_initial(plan: int, x0, y0, stream=None):
+    _check("pr_batch_set_initial", lib().pr_batch_set_initial(plan, _ptr(x0), _ptr(y0), _stream(stream)))
+
+
+def pr_batch_iterate(plan: int, stream=None):
+    _check("pr_batch_iterate", lib().pr_batch_iterate(plan, _stream(stream)))
+
+
+def pr_batch_rho(plan: int, problem: int, out, stream=None):
+    _check("pr_batch_rho", lib().pr_batch_rho(plan, problem, _ptr(out), _stream(stream)))
+
+
+def pr_batch_fine_state(plan: int, problem: int, x_out, y_out, stream=None):
+    _check("pr_batch_fine_state", lib().pr_batch_fine_state(plan, problem, _ptr(x_out), _ptr(y_out),
+                                                            _stream(stream)))
+
+
+def pr_batch_status(plan: int, stream=None) -> int:
+    w = ctypes.c_int32()
+    _check("pr_batch_status", lib().pr_batch_status(plan, ctypes.byref(w), _stream(stream)))
+    return w.value
+
+
+def pr_batch_set_config(plan: int, ppt: int, item_work: float):
+    _check("pr_batch_set_config", lib().pr_batch_set_config(plan, ppt, item_work))
+
+
+def pr_batch_get_config(plan: int):
+    ppt, work, items = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()
+    _check("pr_batch_get_config", lib().pr_batch_get_config(plan, ctypes.byref(ppt), ctypes.byref(work),
+                                                            ctypes.byref(items)))
+    return ppt.value, work.value, items.value
+
+
+def pr_batch_tune(plan: int, steps_div: int = 8, stream=None) -> float:
+    best = ctypes.c_double()
+    _check("pr_batch_tune", lib().pr_batch_tune(plan, steps_div, ctypes.byref(best), _stream(stream)))
+    return best.value

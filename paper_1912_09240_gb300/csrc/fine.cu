@@ -18,6 +18,7 @@
 #include <mutex>
 #include <vector>
 
+#include "fine_dev.cuh"
 #include "match.cuh"
 #include "pr_common.cuh"
 
@@ -146,67 +147,11 @@ fine_f32_d1_kernel(FineArgs a, FineSmemOffsets so, int flags)
     const float* __restrict__ yin = static_cast<const float*>(a.y_in) + (int64_t)s * a.in_slice_stride;
     float* __restrict__ xout = static_cast<float*>(a.x_out) + (int64_t)s * N;
     float* __restrict__ yout = static_cast<float*>(a.y_out) + (int64_t)s * N;
-
-    const float lam = a.lam_f, ddt = a.drift_dt_f, rel = a.relax_f;
-    const float sxk = a.sxk_f, syk = a.syk_f;   // noise amplitudes times sqrt(2 ln 2)
-    const uint32_t k0 = a.k0, k1 = a.k1, chi = a.ctr_hi;
-    const int pairs = a.steps >> 1;
-    const int64_t tile = (int64_t)blockDim.x * PPT;
-
-    for (int t = 0; t < a.tiles_per_cta; ++t) {
-        const int64_t base = ((int64_t)blockIdx.x * a.tiles_per_cta + t) * tile + threadIdx.x;
-        if (base - threadIdx.x >= N) break;   // uniform across the block
-        float x[PPT], y[PPT];
-        uint32_t pid[PPT];
-        bool ok[PPT];
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            const int64_t p = base + (int64_t)k * blockDim.x;
-            ok[k] = p < N;
-            pid[k] = (uint32_t)p;
-            x[k] = ok[k] ? xin[p] : 0.0f;
-            y[k] = ok[k] ? yin[p] : 0.0f;
-        }
-        if (do_match) {
-#pragma unroll
-            for (int k = 0; k < PPT; ++k)
-                if (ok[k]) x[k] = match_one_f32(ms, thr, bins, a.lo_f, a.inv_h_f, x[k]);
-        }
-        if (do_hs) {
-#pragma unroll
-            for (int k = 0; k < PPT; ++k)
-                if (ok[k]) atomicAdd(&hist_s[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x[k])], 1u);
-        }
-        for (int mp = 0; mp < pairs; ++mp) {
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)mp, pid[k], slice, chi), k0, k1);
-                float q0, c0, s0, q1, c1, s1;
-                box_muller_qcs(w.x, w.y, q0, c0, s0);
-                box_muller_qcs(w.z, w.w, q1, c1, s1);
-                // steps 2 mp and 2 mp + 1: sx z0 = (q sxk) cos, sy z1 = (q syk) sin
-                em_step_f32<KIND>(x[k], y[k], q0 * sxk, c0, q0 * syk, s0, lam, ddt, rel);
-                em_step_f32<KIND>(x[k], y[k], q1 * sxk, c1, q1 * syk, s1, lam, ddt, rel);
-            }
-        }
-        if (a.steps & 1) {
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)pairs, pid[k], slice, chi), k0, k1);
-                float q0, c0, s0;
-                box_muller_qcs(w.x, w.y, q0, c0, s0);
-                em_step_f32<KIND>(x[k], y[k], q0 * sxk, c0, q0 * syk, s0, lam, ddt, rel);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-            if (!ok[k]) continue;
-            const int64_t p = base + (int64_t)k * blockDim.x;
-            xout[p] = x[k];
-            yout[p] = y[k];
-            if (do_he) atomicAdd(&hist_e[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x[k])], 1u);
-        }
-    }
+    D1Consts cst{a.lam_f, a.drift_dt_f, a.relax_f, a.sxk_f, a.syk_f, a.k0, a.k1, a.ctr_hi};
+    D1Smem sm{thr, hist_s, hist_e, &ms, bins, a.lo_f, a.inv_h_f, do_match, do_hs, do_he};
+    const int64_t span = (int64_t)a.tiles_per_cta * blockDim.x * PPT;
+    const int64_t p_begin = (int64_t)blockIdx.x * span;
+    fine_d1_range<KIND, PPT>(xin, yin, xout, yout, p_begin, min(N, p_begin + span), slice, a.steps, cst, sm);
     if (do_hs || do_he) {
         __syncthreads();
         for (int i = threadIdx.x; i < bins; i += blockDim.x) {
