@@ -2,12 +2,12 @@
 
 The driver owns the device buffers (torch tensors: memory only) and sequences
 the library's kernels; it performs no arithmetic of its own.  One parareal
-iteration k -> k+1 is, in order:
+iteration k -> k+1 is:
 
-1. fine propagation of all slices at once (``pr_fine_propagate``), slice 0
-   from X_0 and slice n >= 1 from the matched state
-   X_k^n = M(rho_k^n, Xbar_{k-1}^n), with the matching fused into the kernel's
-   prologue and the restrictions R X_k^n and R Xbar_k^{n+1} into it;
+1. fine propagation of all slices (``pr_fine_propagate``), slice 0 from X_0
+   and slice n >= 1 from the matched state X_k^n = M(rho_k^n, Xbar_{k-1}^n),
+   the matching fused into the kernel's prologue and the restrictions
+   R X_k^n and R Xbar_k^{n+1} into it;
 2. the coarse propagator on every start state, rho_c* = C(R X_k^n)
    (``pr_coarse_fp``);
 3. the serial update rho_{k+1}^{n+1} = J(C(rho_{k+1}^n), rho_f*, rho_c*)
@@ -15,6 +15,17 @@ iteration k -> k+1 is, in order:
 
 Iteration 0 is the serial coarse sweep from R X_0 (``PR_ITER_NONE``); its
 matching against X_0 happens in the prologue of the first fine launch.
+
+Pipelined mode (``chunk > 0``): the slices are cut into chunks; the fine
+launches of chunk c run on two alternating streams and the coarse step and
+serial sweep of chunk c on a high-priority stream as soon as that chunk's
+fine results exist.  Slice n of iteration k+1 only needs the sweep of
+iteration k up to slice n, so the serial sweep hides behind the fine work.
+The macroscopic states are double-buffered; every cross-stream hazard is
+ordered by an event (fine(k+1, c) waits for the sweep of chunk c and for
+fine(k, c+1), which reads the slice fine(k+1, c) overwrites).  Results are
+bit for bit those of the sequential mode.  ``join()`` (called by every
+accessor) makes the caller's stream wait for the outstanding work.
 """
 from __future__ import annotations
 
@@ -26,7 +37,7 @@ from . import _lib as L
 class PararealSolver:
     def __init__(self, model: L.Model, grid: L.Grid, n: int, K: int, steps: int, dt: float,
                  precision: int = L.PR_F32, rng: L.Rng = L.Rng(), iterator: int = L.PR_ITER_QUANTILE,
-                 qmode: int = L.PR_QMODE_TWO_SIDED, device: str = "cuda", stream=None):
+                 qmode: int = L.PR_QMODE_TWO_SIDED, device: str = "cuda", stream=None, chunk: int = 0):
         self.model, self.grid, self.n, self.K, self.steps, self.dt = model, grid, n, K, steps, dt
         self.precision, self.rng, self.iterator, self.qmode = precision, rng, iterator, qmode
         self.device = torch.device(device)
@@ -40,7 +51,8 @@ class PararealSolver:
         f64 = torch.float64
         self.cdf0 = z(I + 1, dtype=f64)
         self.counts0 = z(I, dtype=torch.int32)
-        self.rho = z(K + 1, I + 1, dtype=f64)
+        self._rho = z(K + 1, I + 1, dtype=f64)       # rho_k (read by the fine launches)
+        self._rho_next = z(K + 1, I + 1, dtype=f64)  # rho_{k+1} (written by the sweep)
         self.prior0 = z(K, I + 1, dtype=f64)
         self.f_star = z(K, I + 1, dtype=f64)        # R Xbar_k^{n+1} of this iteration
         self.f_star_prev = z(K, I + 1, dtype=f64)   # ... of the previous iteration
@@ -48,18 +60,28 @@ class PararealSolver:
         self.c_star = z(K, I + 1, dtype=f64)
         self.counts_s = z(K, I, dtype=torch.int32)
         self.counts_e = z(K, I, dtype=torch.int32)
-        self.status = z(1, dtype=torch.int32)
+        self.chunk = int(chunk) if chunk and chunk < K else 0
+        nch = (K + self.chunk - 1) // self.chunk if self.chunk else 1
+        self._status = z(nch, dtype=torch.int32)
         self.coarse = L.pr_coarse_create(model, grid, steps * dt, stream=self._s())
         self.k = 0
         # when a list, (start, end) CUDA events around the main fine launch of
-        # every iteration are appended to it
+        # every sequential iteration are appended to it
         self.fine_events = None
+        if self.chunk:
+            self._sf = [torch.cuda.Stream(self.device), torch.cuda.Stream(self.device)]
+            self._su = torch.cuda.Stream(self.device, priority=-1)
+            self._ev_fine = [None] * nch     # fine(k, c) of the latest enqueued iteration
+            self._ev_upd = [None] * nch      # sweep(k, c) of the latest enqueued iteration
+        self._pending = False
 
+    # -- plumbing ----------------------------------------------------------------
     def _s(self):
         return self.stream if self.stream is not None else torch.cuda.current_stream(self.device)
 
     def close(self):
         if getattr(self, "coarse", None):
+            self.join()
             L.pr_coarse_destroy(self.coarse)
             self.coarse = None
 
@@ -69,54 +91,119 @@ class PararealSolver:
         except Exception:
             pass
 
+    def join(self):
+        """Make the caller's stream wait for every enqueued kernel of the solver."""
+        if self.chunk and self._pending:
+            s = self._s()
+            for ev in self._ev_upd + self._ev_fine:
+                if ev is not None:
+                    s.wait_event(ev)
+            self._pending = False
+
+    @property
+    def rho(self) -> torch.Tensor:
+        """rho_k^n, n = 0..K, as CDFs at the edges (after the latest iteration)."""
+        self.join()
+        return self._rho
+
+    @property
+    def status(self) -> torch.Tensor:
+        self.join()
+        return self._status.max().reshape(1)
+
     # -- setup and iteration 0 -------------------------------------------------
     def set_initial(self, x0: torch.Tensor, y0: torch.Tensor):
+        self.join()
+        s = self._s()
         self.x0.copy_(x0.reshape(self.n))
         self.y0.copy_(y0.reshape(self.model.fast_dim, self.n))
-        s = self._s()
         L.pr_restrict(self.precision, self.x0, self.n, 1, self.grid, self.counts0, self.cdf0, stream=s)
         self.prior0.copy_(self.cdf0.expand(self.K, -1))
         L.pr_parareal_update(self.coarse, L.PR_ITER_NONE, self.qmode, self.K, self.cdf0, None, None,
-                             self.rho, self.status, stream=s)
+                             self._rho, self._status[0], stream=s)
         self.k = 0
+        if self.chunk:
+            self._ev_fine = [None] * len(self._ev_fine)
+            self._ev_upd = [None] * len(self._ev_upd)
 
     # -- one generic iteration ---------------------------------------------------
+    def _fine(self, a: int, b: int, first: bool, stream):
+        """Fine launches for slices [a, b) of this iteration on `stream`."""
+        n = self.n
+        if a == 0:
+            L.pr_fine_propagate(self.model, self.precision, self.rng, self.x0, self.y0, True,
+                                self.xb[0], self.yb[0], n, 0, 1, self.steps, self.dt, self.grid,
+                                None, None, self.counts_s[0], self.start[0], self.counts_e[0],
+                                self.f_star[0], stream=stream)
+            a = 1
+        if b <= a:
+            return
+        if first:   # X_0^n = M(rho_0^n, X_0)
+            src_x, src_y, bcast, prior = self.x0, self.y0, True, self.prior0[a - 1:b - 1]
+        else:       # X_k^n = M(rho_k^n, Xbar_{k-1}^n)
+            src_x, src_y, bcast = self.xa[a - 1:b - 1], self.ya[a - 1:b - 1], False
+            prior = self.f_star_prev[a - 1:b - 1]
+        ev = None
+        if self.fine_events is not None and not self.chunk:
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record(stream)
+        L.pr_fine_propagate(self.model, self.precision, self.rng, src_x, src_y, bcast,
+                            self.xb[a:b], self.yb[a:b], n, a, b - a, self.steps, self.dt, self.grid,
+                            prior, self._rho[a:b], self.counts_s[a:b], self.start[a:b], self.counts_e[a:b],
+                            self.f_star[a:b], stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+            self.fine_events.append(ev)
+
     def iterate(self):
-        K, n, s = self.K, self.n, self._s()
+        K = self.K
         first = self.k == 0
-        # slice 0 starts from X_0 (no matching)
-        L.pr_fine_propagate(self.model, self.precision, self.rng, self.x0, self.y0, True,
-                            self.xb[0], self.yb[0], n, 0, 1, self.steps, self.dt, self.grid,
-                            None, None, self.counts_s[0], self.start[0], self.counts_e[0],
-                            self.f_star[0], stream=s)
-        if K > 1:
-            if first:   # X_0^n = M(rho_0^n, X_0)
-                src_x, src_y, bcast, prior = self.x0, self.y0, True, self.prior0[: K - 1]
-            else:       # X_k^n = M(rho_k^n, Xbar_{k-1}^n)
-                src_x, src_y, bcast, prior = self.xa[: K - 1], self.ya[: K - 1], False, self.f_star_prev[: K - 1]
-            ev = None
-            if self.fine_events is not None:
-                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                ev[0].record(s)
-            L.pr_fine_propagate(self.model, self.precision, self.rng, src_x, src_y, bcast,
-                                self.xb[1:], self.yb[1:], n, 1, K - 1, self.steps, self.dt, self.grid,
-                                prior, self.rho[1:K], self.counts_s[1:], self.start[1:], self.counts_e[1:],
-                                self.f_star[1:], stream=s)
-            if ev is not None:
-                ev[1].record(s)
-                self.fine_events.append(ev)
-        L.pr_coarse_fp(self.coarse, self.start, self.c_star, K, stream=s)
-        L.pr_parareal_update(self.coarse, self.iterator, self.qmode, K, self.cdf0, self.f_star, self.c_star,
-                             self.rho, self.status, stream=s)
+        if not self.chunk:
+            s = self._s()
+            self._fine(0, K, first, s)
+            L.pr_coarse_fp(self.coarse, self.start, self.c_star, K, stream=s)
+            L.pr_parareal_update(self.coarse, self.iterator, self.qmode, K, self.cdf0, self.f_star, self.c_star,
+                                 self._rho_next, self._status[0], stream=s)
+        else:
+            C = self.chunk
+            nch = len(self._ev_upd)
+            fork = torch.cuda.Event()
+            fork.record(self._s())
+            for st in (*self._sf, self._su):
+                st.wait_event(fork)
+            new_fine, new_upd = [None] * nch, [None] * nch
+            for c in range(nch):
+                a, b = c * C, min(K, (c + 1) * C)
+                sf = self._sf[c % 2]
+                for ev in (self._ev_upd[c], self._ev_fine[c + 1] if c + 1 < nch else None):
+                    if ev is not None:
+                        sf.wait_event(ev)
+                self._fine(a, b, first, sf)
+                ef = torch.cuda.Event()
+                ef.record(sf)
+                new_fine[c] = ef
+                su = self._su
+                su.wait_event(ef)
+                L.pr_coarse_fp(self.coarse, self.start[a:b], self.c_star[a:b], b - a, stream=su)
+                state = self.cdf0 if a == 0 else self._rho_next[a]
+                L.pr_parareal_update(self.coarse, self.iterator, self.qmode, b - a, state, self.f_star[a:b],
+                                     self.c_star[a:b], self._rho_next[a:b + 1], self._status[c], stream=su)
+                eu = torch.cuda.Event()
+                eu.record(su)
+                new_upd[c] = eu
+            self._ev_fine, self._ev_upd = new_fine, new_upd
+            self._pending = True
         # the fine results become the priors of the next matching
         self.xa, self.xb = self.xb, self.xa
         self.ya, self.yb = self.yb, self.ya
         self.f_star, self.f_star_prev = self.f_star_prev, self.f_star
+        self._rho, self._rho_next = self._rho_next, self._rho
         self.k += 1
 
     # -- the serial fine solution with the same random numbers -----------------
     def serial_reference(self):
         """x[K+1][n], y[K+1][d][n] and their restrictions rho[K+1][I+1]."""
+        self.join()
         K, n, s = self.K, self.n, self._s()
         d = self.model.fast_dim
         xs = torch.empty(K + 1, n, dtype=self.x0.dtype, device=self.device)
@@ -137,6 +224,7 @@ class PararealSolver:
         return out
 
     def state(self):
-        """Current iterate X_k^n for n = 1..K is held implicitly (Xbar + matching);
-        this returns the fine end states Xbar_{k-1}^{n} and rho_k."""
-        return self.xa, self.ya, self.rho
+        """The fine end states Xbar_{k-1}^{n}, n = 1..K, and rho_k (the iterate
+        X_k^n is their matching against rho_k)."""
+        self.join()
+        return self.xa, self.ya, self._rho
