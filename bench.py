@@ -113,30 +113,64 @@ class ClockSampler:
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1912_09240_gb300.replicas import rank_env
+    return rank_env()
 
 
 def _cpu_sample(seconds_target: float = 12.0):
-    """Time the oracle's fine propagator on a bounded sample of the workload."""
+    """Time the oracle on bounded samples of the workloads (host cores of this
+    machine): the double-well fine propagator at all cores and at one core,
+    one slice of the 16-dimensional fast space at 2^16 particles, and the
+    plain FP64 workload's whole parareal run."""
     from oracle import oracle as orc
+    orc.build()
     w = WORKLOAD
     om = orc.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
     x0, y0 = workloads.initial_ensemble(w)
-    # calibrate on a small sample, then size the timed sample to ~seconds_target
-    n_cal, s_cal = 1 << 14, 100
+    cores = orc.num_threads()
+
+    def rate_of(n_max, target):
+        # calibrate on a small sample, then size the timed sample to ~target seconds
+        n_cal, s_cal = 1 << 12, 100
+        t0 = time.perf_counter()
+        orc.fine_propagate(om, w.seed, x0[None, :n_cal], y0[None, :, :n_cal], 1, s_cal, w.step_dt)
+        rate = n_cal * s_cal / max(time.perf_counter() - t0, 1e-6)
+        n = int(min(n_max, max(1 << 12, rate * target / w.steps)))
+        t0 = time.perf_counter()
+        orc.fine_propagate(om, w.seed, x0[None, :n], y0[None, :, :n], 1, w.steps, w.step_dt)
+        el = time.perf_counter() - t0
+        return n * w.steps / el, n, el
+
+    value, n, el = rate_of(w.N, seconds_target)
+    orc.set_num_threads(1)
+    try:
+        v1, n1, el1 = rate_of(w.N, seconds_target / 3)
+    finally:
+        orc.set_num_threads(cores)
+    # one slice of the 16-dimensional fast space, 2^16 particles
+    lw = workloads.LARGE_FAST
+    nl = 1 << 16
+    lm = orc.Model(lw.kind, lw.fast_dim, lw.lam, lw.beta, lw.eps, lw.tau_x)
+    lx, ly = workloads.initial_ensemble(lw.scaled(N=nl))
     t0 = time.perf_counter()
-    orc.fine_propagate(om, w.seed, x0[None, :n_cal], y0[None, :, :n_cal], 1, s_cal, w.step_dt)
-    rate = n_cal * s_cal / max(time.perf_counter() - t0, 1e-6)
-    n = int(min(w.N, max(1 << 14, rate * seconds_target / w.steps)))
+    orc.fine_propagate(lm, lw.seed, lx[None], ly[None], 1, lw.steps, lw.step_dt)
+    el_l = time.perf_counter() - t0
+    # the plain FP64 workload in full (4096 particles, 8 slices, 4 iterations)
+    ow = workloads.OU_SMALL
+    ox, oy = workloads.initial_ensemble(ow)
     t0 = time.perf_counter()
-    orc.fine_propagate(om, w.seed, x0[None, :n], y0[None, :, :n], 1, w.steps, w.step_dt)
-    el = time.perf_counter() - t0
-    return {"value": n * w.steps / el, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+    orc.parareal(orc.Model(ow.kind, ow.fast_dim, ow.lam, ow.beta, ow.eps, ow.tau_x), orc.Grid(ow.bins, ow.lo, ow.hi),
+                 ow.seed, ox, oy, ow.K, ow.steps, ow.step_dt, iters=ow.iters)
+    el_o = time.perf_counter() - t0
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} particles x 1 slice x {w.steps} EM steps of the double-well workload "
-                      f"(FP64 C oracle, OpenMP), {el:.1f} s"}
+                      f"(FP64 C oracle, OpenMP), {el:.1f} s",
+            "single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": f"{n1} particles x 1 slice x {w.steps} steps, {el1:.1f} s"},
+            "fast16": {"value": nl * lw.steps / el_l, "unit": UNIT, "cores": cores,
+                       "sample": f"{nl} particles x 1 slice x {lw.steps} steps of the 16-dimensional "
+                                 f"fast-space workload, {el_l:.1f} s"},
+            "ou_fp64_full_parareal_s": el_o}
 
 
 def run_reference(args):
@@ -171,6 +205,192 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _ev_time(fn, stream, reps: int) -> float:
+    """Mean milliseconds of `fn` over `reps` calls, CUDA events on `stream`, after one warm call."""
+    import torch
+    fn(0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for r in range(reps):
+        fn(r + 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _unfused_leg(L, solver, w, stream, hbm_peak):
+    """Restriction and matching as standalone passes over the 49 non-initial
+    slices of the double-well state (4 B and 8 B per particle), alternating
+    between the two ensemble buffers so the working set (412 MB) exceeds L2;
+    the coarse propagator on 50 states and the serial sweep over 50 slices."""
+    n, K = w.N, w.K
+    bufs = [solver.xa[1:], solver.xb[1:]]
+    S = K - 1
+    t_r = _ev_time(lambda r: L.pr_restrict(L.PR_F32, bufs[r % 2], n, S, solver.grid, solver.counts_s[1:],
+                                           solver.start[1:], stream=stream), stream, 10)
+    prior, target = solver.f_star_prev[:S], solver.rho[1:K]
+    t_m = _ev_time(lambda r: L.pr_match(L.PR_F32, bufs[r % 2], bufs[(r + 1) % 2], n, S, solver.grid, prior,
+                                        target, stream=stream), stream, 10)
+    t_c = _ev_time(lambda r: L.pr_coarse_fp(solver.coarse, solver.start, solver.c_star, K, stream=stream),
+                   stream, 20)
+    t_u = _ev_time(lambda r: L.pr_parareal_update(solver.coarse, L.PR_ITER_QUANTILE, L.PR_QMODE_TWO_SIDED, K,
+                                                  solver.cdf0, solver.f_star, solver.c_star, solver._rho_next,
+                                                  solver._status[0], stream=stream), stream, 20)
+    rb, mb = 4.0 * n * S, 8.0 * n * S
+    out = {"restrict": {"ms": t_r, "algorithmic_bytes": rb, "gbs": rb / t_r / 1e6},
+           "match": {"ms": t_m, "algorithmic_bytes": mb, "gbs": mb / t_m / 1e6},
+           "coarse_fp_us": 1e3 * t_c, "serial_sweep_us": 1e3 * t_u,
+           "note": f"{S} slices x {n} binary32 particles; coarse step on {K} states of {w.bins} bins; "
+                   f"sweep over {K} slices"}
+    if hbm_peak:
+        out["restrict"]["frac_of_measured_hbm"] = out["restrict"]["gbs"] / hbm_peak
+        out["match"]["frac_of_measured_hbm"] = out["match"]["gbs"] / hbm_peak
+    return out
+
+
+def _plain_leg(L, dev, stream, rank):
+    """The plain FP64 workload in full (4096 particles, 8 slices x 125 steps,
+    256 bins): iteration time eager and graph-replayed, iterations to
+    W1 <= 1e-3 against the serial fine solution; and the same OU system at
+    2^20 particles in binary32 and FP64 (time per iteration, W1 between them)."""
+    import torch
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    out = {}
+    for wname, w, precs in (("ou_fp64_full", workloads.OU_SMALL, (L.PR_F64,)),
+                            ("ou_n2^20", workloads.OU_SMALL.scaled(N=1 << 20, name="ou_n2^20_k8"),
+                             (L.PR_F32, L.PR_F64))):
+        model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+        grid = L.Grid(w.bins, w.lo, w.hi)
+        x0, y0 = workloads.initial_ensemble(w)
+        res, rhos = {}, {}
+        for prec in precs:
+            dty = torch.float32 if prec == L.PR_F32 else torch.float64
+            x0t = torch.tensor(x0, dtype=dty, device=dev)
+            y0t = torch.tensor(y0, dtype=dty, device=dev)
+            r = {}
+            for graph in (False, True):
+                sv = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=prec,
+                                    rng=L.Rng(w.seed, rank), device=str(dev), graph=graph)
+                sv.set_initial(x0t, y0t)
+                _, _, rser = sv.serial_reference()
+                sv.set_initial(x0t, y0t)
+                for _ in range(3):
+                    sv.iterate()
+                torch.cuda.synchronize()
+                reps = 20 if w.N < 100000 else 5
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    sv.iterate()
+                sv.join()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                r["graph_ms" if graph else "eager_ms"] = e0.elapsed_time(e1) / reps
+                if not graph:
+                    sv.set_initial(x0t, y0t)
+                    kstar = None
+                    for k in range(1, w.K + 1):
+                        sv.iterate()
+                        if kstar is None and float(sv.w1_to(rser).max().item()) <= 1e-3:
+                            kstar = k
+                    r["iterations_to_w1_1e-3"] = kstar
+                    rhos[prec] = sv.rho.clone()
+                sv.close()
+            ps = w.particle_steps_per_iteration
+            r["particle_steps_per_s"] = ps / (min(r["eager_ms"], r["graph_ms"]) / 1e3)
+            res["f32" if prec == L.PR_F32 else "f64"] = r
+        if len(rhos) == 2:
+            wv = torch.empty(w.K + 1, dtype=torch.float64, device=dev)
+            L.pr_w1(grid, w.K + 1, rhos[L.PR_F32], rhos[L.PR_F64], wv)
+            res["fp32_vs_fp64_max_w1_at_k_iterations"] = float(wv.max().item())
+            res["f64_over_f32_time"] = (min(res["f64"]["eager_ms"], res["f64"]["graph_ms"]) /
+                                        min(res["f32"]["eager_ms"], res["f32"]["graph_ms"]))
+        res.update({"N": w.N, "K": w.K, "steps_per_slice": w.steps})
+        out[wname] = res
+    return out
+
+
+def _adjoint_leg(L, dev, stream, rank, n=None):
+    """Pathwise gradients of the adjoint workload (2^20 particles, 20 slices x
+    1000 steps, checkpoints every 256 steps): the forward alone, the gradient
+    of E[X_T^2] (forward + adjoint), and the gradient of the 512-point
+    quantile function (per-particle adjoint + order statistics)."""
+    import torch
+    from paper_1912_09240_gb300.adjoint import quantile_gradient, second_moment_gradient
+    w = workloads.ADJOINT
+    if n:
+        w = w.scaled(N=n, name=w.name + f"_n{n}")
+    x0, y0 = workloads.initial_ensemble(w)
+    gx0 = torch.tensor(x0, dtype=torch.float32, device=dev)
+    gy0 = torch.tensor(y0[0], dtype=torch.float32, device=dev)
+    model = L.Model(w.kind, 1, w.lam, w.beta, w.eps, w.tau_x)
+    rng = L.Rng(w.seed, rank)
+    x = gx0.reshape(1, -1).clone()
+    y = gy0.reshape(1, 1, -1).clone()
+
+    def forward():
+        x.copy_(gx0.reshape(1, -1))
+        y.copy_(gy0.reshape(1, 1, -1))
+        for n in range(w.K):
+            L.pr_fine_propagate(model, L.PR_F32, rng, x, y, False, x, y, w.N, n, 1, w.steps, w.step_dt)
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    t_f, _ = timed(forward)
+    t_g, (val, grad) = timed(lambda: second_moment_gradient(model, rng, gx0, gy0, 0, w.K, w.steps, w.step_dt))
+    t_q, _ = timed(lambda: quantile_gradient(model, rng, gx0, gy0, 0, w.K, w.steps, w.step_dt))
+    ps = w.N * w.K * w.steps
+    return {"workload": w.name, "particle_steps": ps,
+            "forward_ms": t_f, "second_moment_grad_ms": t_g, "quantile_grad_ms": t_q,
+            "forward_particle_steps_per_s": ps / (t_f / 1e3),
+            "second_moment_grad_particle_steps_per_s": ps / (t_g / 1e3),
+            "grad_over_forward": t_g / t_f,
+            "second_moment": float(val.item()), "grad_lambda_beta_eps": [float(v) for v in grad.cpu()]}
+
+
+def _large_leg(L, dev, stream, rank, chunk, n=None, k=None, iters=1):
+    """One parareal iteration of the 16-dimensional fast-space workload
+    (4e6 particles, 100 slices x 1000 steps, 1024 bins), after a warm-up
+    iteration."""
+    import torch
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    w = workloads.LARGE_FAST
+    if n or k:
+        w = w.scaled(N=n or w.N, K=k or w.K, T=w.slice_dt * (k or w.K))
+    model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    grid = L.Grid(w.bins, w.lo, w.hi)
+    x0t = torch.tensor(workloads.initial_slow(w), dtype=torch.float32, device=dev)   # Y_0 = X_0 (1, ..., 1)
+    solver = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                            rng=L.Rng(w.seed, rank), device=str(dev), chunk=chunk)
+    solver.set_initial(x0t, x0t.expand(w.fast_dim, w.N).contiguous())
+    solver.iterate()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(iters):
+        solver.iterate()
+    solver.join()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    status = int(solver.status.item())
+    solver.close()
+    ps = w.particle_steps_per_iteration
+    return {"workload": w.name, "N": w.N, "K": w.K, "steps_per_slice": w.steps, "fast_dim": w.fast_dim,
+            "bins": w.bins, "particle_steps_per_iteration": ps, "iteration_ms": ms,
+            "particle_steps_per_s": ps / (ms / 1e3), "status": status}
 
 
 def run_ours(args):
@@ -215,11 +435,13 @@ def run_ours(args):
             dist.barrier()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        launches0 = solver.launches
         t0.record(stream)
         for _ in range(args.steps):
             solver.iterate()
         solver.join()
         t1.record(stream)
+        launches = solver.launches - launches0
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -234,10 +456,8 @@ def run_ours(args):
     fine_times = solver.fine_events
     solver.fine_events = None
     solver.chunk = chunk_saved
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    from paper_1912_09240_gb300.replicas import max_over_ranks, shard, sum_over_ranks
+    ms = max_over_ranks(ms, dist, dev)
     ps_per_step = w.particle_steps_per_iteration
     value = ws * ps_per_step / (ms / 1e3)
     fine_ms = statistics.mean(a.elapsed_time(b_) for a, b_ in fine_times) if fine_times else None
@@ -279,6 +499,24 @@ def run_ours(args):
                 "fp32_fine_particle_steps_per_s": fine_rate,
                 "fp32_over_fp64": (fine_rate / fp64_rate) if fine_rate else None,
                 "sample": f"FP64 fine kernel, {w.N} particles x 2 slices x {w.steps} steps"}
+        del xs, ys
+        # one whole parareal iteration of the workload on the plain FP64 path
+        # (pipelined driver as above), after one warm-up iteration
+        sv = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F64,
+                            rng=L.Rng(w.seed, rank), device=str(dev), chunk=args.chunk)
+        sv.set_initial(torch.tensor(x0, dtype=torch.float64, device=dev),
+                       torch.tensor(y0, dtype=torch.float64, device=dev))
+        sv.iterate()
+        torch.cuda.synchronize()
+        f0.record(stream)
+        sv.iterate()
+        sv.join()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fp64["fp64_iteration_ms"] = f0.elapsed_time(f1)
+        fp64["fp64_over_fp32_iteration_time"] = fp64["fp64_iteration_ms"] / ms
+        sv.close()
+        del sv
 
     # convergence: iterations until max_n W1(rho_k^n, R X_serial^n) <= 1e-3,
     # against the serial fine solution with the same random numbers
@@ -329,7 +567,9 @@ def run_ours(args):
         from paper_1912_09240_gb300.batch import BatchSolver
         bw = workloads.batched_problems()
         probs, bx, by = [], [], []
-        for pw in bw.problems:
+        # independent problems: each rank serves its share, no collective
+        mine = shard([float(pw.N * pw.K * pw.steps) for pw in bw.problems], rank, ws)
+        for pw in (bw.problems[i] for i in mine):
             probs.append(L.Problem(L.Model(pw.kind, 1, pw.lam, pw.beta, pw.eps), L.Grid(pw.bins, pw.lo, pw.hi),
                                    pw.N, pw.K, pw.steps, pw.step_dt, pw.seed))
             xx, yy = workloads.initial_ensemble(pw)
@@ -351,16 +591,28 @@ def run_ours(args):
             bs.iterate()
         b1.record(stream)
         torch.cuda.synchronize()
-        bms = b0.elapsed_time(b1) / nb
+        bms = max_over_ranks(b0.elapsed_time(b1) / nb, dist, dev)
+        b_ps = sum_over_ranks(bs.particle_steps, dist, dev)
         ppt, work, items = bs.config()
-        batched = {"workload": bw.name, "problems": len(probs),
-                   "particle_steps_per_iteration": bs.particle_steps,
-                   "iteration_ms": bms, "particle_steps_per_s": bs.particle_steps / (bms / 1e3),
+        batched = {"workload": bw.name, "problems": len(bw.problems), "problems_per_rank": len(probs),
+                   "particle_steps_per_iteration": b_ps,
+                   "iteration_ms": bms, "particle_steps_per_s": b_ps / (bms / 1e3),
                    "graph_replayed": True, "tuned": {"particles_per_thread": ppt, "item_particle_steps": work,
                                                       "items": items, "tune_s": tune_s,
                                                       "trial_ms": tuned_ms},
                    "status": bs.status()}
         bs.close()
+
+    unfused = None if args.no_unfused else _unfused_leg(L, solver, w, stream, _peaks().get("hbm_gbs"))
+    plain = None if args.no_plain else _plain_leg(L, dev, stream, rank)
+    adjoint = None if args.no_adjoint else _adjoint_leg(L, dev, stream, rank, n=args.adjoint_n)
+    large = None
+    if not args.no_large:
+        solver.close()
+        large = _large_leg(L, dev, stream, rank, args.chunk, n=args.large_n, k=args.large_k)
+        if dist:
+            large["particle_steps_per_s"] = sum_over_ranks(large["particle_steps_per_iteration"], dist, dev) / (
+                max_over_ranks(large["iteration_ms"], dist, dev) / 1e3)
 
     if rank != 0:
         if dist:
@@ -383,6 +635,7 @@ def run_ours(args):
                     "frac": achieved / peak, "traffic": traffic,
                     "kernel": "fine_f32_d1_kernel (slices 1..49)",
                     "fine_ms_per_launch": fine_ms,
+                    "achieved_in_step": INST_PER_PARTICLE_STEP * ps_per_step / (ms / 1e3) / 1e12,
                     "peak_basis": f"152 SMs x 4 warp-instr/clk x 32 lanes x {sm_max:.0f} MHz (max SM clock)",
                     "algorithmic": f"{INST_PER_PARTICLE_STEP} thread-instructions per particle-step x "
                                    f"{launch_ps:.3e} particle-steps per launch"}
@@ -395,7 +648,7 @@ def run_ours(args):
                    "bins": w.bins, "iterator": "quantile (two-sided)", "parallelism": f"replicas x{ws}",
                    "pipeline_chunk": args.chunk,
                    "l2": "inputs larger than L2: 840 MB of ensemble state per step"},
-        "gpu_launches": 8 * args.steps,
+        "gpu_launches": launches,
         "clocks": clocks,
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -403,6 +656,10 @@ def run_ours(args):
         "fp64_vs_fp32": fp64,
         "convergence": conv,
         "batched": batched,
+        "unfused": unfused,
+        "plain_ou": plain,
+        "adjoint": adjoint,
+        "fast16": large,
     }
     print(json.dumps(line), flush=True)
     solver.close()
@@ -423,6 +680,13 @@ def main():
     ap.add_argument("--no-conv", action="store_true", help="skip the convergence study")
     ap.add_argument("--chunk", type=int, default=5, help="slices per pipelined chunk (0: sequential)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-serving leg")
+    ap.add_argument("--no-unfused", action="store_true", help="skip standalone restriction/matching/coarse timing")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain OU workload legs")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--adjoint-n", type=int, default=None, help="particles of the adjoint leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the 16-dimensional fast-space leg")
+    ap.add_argument("--large-n", type=int, default=None, help="particles of the 16-dimensional leg")
+    ap.add_argument("--large-k", type=int, default=None, help="slices of the 16-dimensional leg")
     ap.add_argument("--n", type=int, default=None, help="particles (smaller case for profiling)")
     ap.add_argument("--k", type=int, default=None, help="slices (smaller case for profiling)")
     args = ap.parse_args()

@@ -251,8 +251,10 @@ pr_status pr_iterate(pr_iterator iterator, pr_quantile_mode qmode, const pr_grid
  * pass takes exactly the steps and random numbers of pr_fine_propagate over
  * slices slice_begin .. slice_begin + n_slices - 1 in sequence (slice s + 1
  * starting where slice s ended), storing (x, y) every ckpt_every steps in
- * the workspace; the backward pass replays each checkpoint segment and runs
- * the adjoint recursion, accumulating in FP64.
+ * the workspace; the backward pass replays each checkpoint segment (leaving
+ * sub-checkpoints every 12 steps in the workspace), replays each 12-step
+ * block once more into shared memory and runs the adjoint recursion over it,
+ * accumulating in FP64.
  *   x0, y0      (device) [n] float start states
  *   x_T, y_T    (device) [n] float end states, or NULL
  *   xbar_T      (device) [n] double dL/dX_T per particle, or NULL
@@ -262,7 +264,8 @@ pr_status pr_iterate(pr_iterator iterator, pr_quantile_mode qmode, const pr_grid
  *   xbar_0, ybar_0 (device) [n] double dL/dX_0, dL/dY_0 (per particle: dX_T/dX_0, dX_T/dY_0
  *               without seeds), or NULL
  *   workspace   (device) >= pr_fine_adjoint_workspace(...) bytes, 256-byte aligned,
- *               caller-owned scratch (checkpoints and partial sums)
+ *               caller-owned scratch: 8 n B per checkpoint, 8 n B per sub-checkpoint
+ *               of one segment, 24 B per 128 particles of partial sums
  */
 size_t pr_fine_adjoint_workspace(int64_t n, int32_t n_slices, int32_t steps, int32_t ckpt_every);
 pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, const float* x0, const float* y0,
@@ -278,7 +281,7 @@ pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, const float*
  * forbids cudaMalloc/cudaFree after start-up because they can block and
  * synchronise the device, or a host whose device memory belongs to another
  * allocator.  Arguments and results are those of pr_fine_adjoint; the
- * checkpoints and partial sums live instead in a fixed 32 MiB device array
+ * checkpoints, sub-checkpoints and partial sums live instead in a fixed 32 MiB device array
  * inside the library, which every GPU that loads the library holds until the
  * process exits (pr_fine_adjoint_noalloc_capacity() gives its size).
  *  - A problem whose pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every)

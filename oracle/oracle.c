@@ -45,6 +45,16 @@ int or_num_threads(void)
 #endif
 }
 
+/* Cap the threads of the OpenMP loops (timing at one core and at all cores). */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Random numbers.  The paper draws the EM increments dU_m, dV_m ~ N(0, dt)  */
 /* independently (Section 2.1.3, Eqs. EMx/EMy) and reuses the same numbers  */

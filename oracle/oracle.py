@@ -53,6 +53,7 @@ def lib():
                                  ctypes.c_uint32, ctypes.c_uint64)
         vp = ctypes.c_void_p
         _lib.or_num_threads.restype = i32
+        _lib.or_set_num_threads.argtypes = [i32]
         _lib.or_philox_batch.argtypes = [vp, i64, u64, vp]
         _lib.or_uniform.argtypes = [u32]
         _lib.or_uniform.restype = d
@@ -125,6 +126,11 @@ class Grid:
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Cap the oracle's OpenMP threads (n >= 1); timing only, results do not depend on it."""
+    lib().or_set_num_threads(int(n))
 
 
 def philox(ctr: np.ndarray, seed: int) -> np.ndarray:

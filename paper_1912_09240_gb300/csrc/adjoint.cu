@@ -9,13 +9,18 @@
 // draws and taking exactly its steps (em_step_f32), and stores (x, y) every
 // `ckpt_every` steps in the caller's workspace.
 // Backward, for each checkpoint segment from the last: the segment is
-// replayed once from its checkpoint to leave sub-checkpoints every 16 steps in
-// shared memory; each 16-step block is then replayed once more, keeping its
-// states and noise increments in shared memory, and the adjoint recursion
+// replayed once from its checkpoint to leave sub-checkpoints every 12 steps in
+// a scratch area of the workspace (16 B per particle per 12 steps); each
+// 12-step block is then replayed once more, keeping its states and noise
+// increments in shared memory, and the adjoint recursion
 //   lbar_t = J_t^T lbar_{t+1},  g += lbar_{t+1} . d(step_t)/d theta
 // runs backwards over the block.  Per-block partial sums are binary32; they
 // are added into binary64 accumulators per particle, and the ensemble sum is
 // reduced in a fixed order (deterministic).
+// When every slice has an even number of steps and the checkpoint interval is
+// even, each Philox block serves a pair of steps that never straddles a slice
+// or a replay block (adjoint_paired_kernel); otherwise the steps are walked
+// one by one (adjoint_kernel).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -28,7 +33,7 @@
 namespace pr {
 
 constexpr int kAdjThreads = 128;
-constexpr int kSub = 16;   // steps per replay block
+constexpr int kSub = 12;   // steps per replay block (even: pairs never straddle one)
 
 struct AdjArgs {
     const float* x0;
@@ -43,6 +48,7 @@ struct AdjArgs {
     float inv2beta, inv2eps, rel_over_eps;       // derivative factors: 1/(2 beta), 1/(2 eps), dt/eps^2
     uint32_t k0, k1, chi;
     float* ckpt_buf;          // [n_ckpt][2][n]
+    float* sub_buf;           // [ceil(min(ckpt, total) / kSub)][2][n]
     double* partial;          // [gridDim.x][3] (ensemble-sum mode)
     float* xT;
     float* yT;
@@ -88,15 +94,82 @@ struct NoiseWalker {
     }
 };
 
+// One block of the adjoint recursion, backwards over `len` steps whose states
+// and noise increments are in shared memory:
+//   lbar_t = J_t^T lbar_{t+1},  g += lbar_{t+1} . d(step_t)/d theta.
 template <int KIND>
-__global__ void __launch_bounds__(kAdjThreads)
+__device__ __forceinline__ void backward_block(const AdjArgs& a, int len, int T, int tid, const float* bx,
+                                               const float* by, const float* bnx, const float* bny, float& lx,
+                                               float& ly, double& g0, double& g1, double& g2)
+{
+    float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
+    for (int i = len - 1; i >= 0; --i) {
+        const float xi = bx[i * T + tid], yi = by[i * T + tid];
+        const float nx = bnx[i * T + tid], ny = bny[i * T + tid];
+        float jxx, jxy, dxdl;
+        if (KIND == PR_MODEL_OU) {          // d_x F = x - lam y
+            jxx = 1.0f - a.ddt;
+            jxy = a.lam * a.ddt;
+            dxdl = a.ddt * yi;
+        } else {                            // d_x F = x^3 - x + lam y
+            jxx = 1.0f - a.ddt * (3.0f * xi * xi - 1.0f);
+            jxy = -a.lam * a.ddt;
+            dxdl = -a.ddt * yi;
+        }
+        const float jyx = a.rel, jyy = 1.0f - a.rel;
+        p0 = fmaf(lx, dxdl, p0);                                   // d/d lambda
+        p1 = fmaf(lx, -nx * a.inv2beta, p1);                       // d/d beta (noise amplitude)
+        p2 = fmaf(ly, -a.rel_over_eps * (xi - yi) - ny * a.inv2eps, p2);   // d/d eps
+        const float nlx = lx * jxx + ly * jyx;
+        const float nly = lx * jxy + ly * jyy;
+        lx = nlx;
+        ly = nly;
+    }
+    g0 += (double)p0;
+    g1 += (double)p1;
+    g2 += (double)p2;
+}
+
+// Fixed-order block reduction of the three per-particle sums into partial[block].
+__device__ __forceinline__ void block_partials(const AdjArgs& a, double g0, double g1, double g2)
+{
+    __shared__ double red[3][kAdjThreads / 32];
+    double v[3] = {g0, g1, g2};
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        if (lane == 0) red[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double s = 0.0;
+        for (int w = 0; w < (int)blockDim.x / 32; ++w) s += red[tid][w];
+        a.partial[(size_t)blockIdx.x * 3 + tid] = s;
+    }
+}
+
+__device__ __forceinline__ void store_outputs(const AdjArgs& a, int64_t p, float lx, float ly, double g0, double g1,
+                                              double g2)
+{
+    if (a.xbar0) a.xbar0[p] = (double)lx;
+    if (a.ybar0) a.ybar0[p] = (double)ly;
+    if (a.grad_pp) {
+        a.grad_pp[p * 3 + 0] = g0;
+        a.grad_pp[p * 3 + 1] = g1;
+        a.grad_pp[p * 3 + 2] = g2;
+    }
+}
+
+// Any step count: steps walked one by one, the Philox block of a pair cached.
+template <int KIND>
+__global__ void __launch_bounds__(kAdjThreads, 8)
 adjoint_kernel(AdjArgs a)
 {
     extern __shared__ float asm_[];
     const int T = blockDim.x, tid = threadIdx.x;
-    float* subx = asm_;
-    float* suby = subx + kSub * T;
-    float* bx = suby + kSub * T;
+    float* bx = asm_;
     float* by = bx + kSub * T;
     float* bnx = by + kSub * T;
     float* bny = bnx + kSub * T;
@@ -125,6 +198,10 @@ adjoint_kernel(AdjArgs a)
             em_step_f32<KIND>(x, y, q * a.sxk, c, q * a.syk, s, a.lam, a.ddt, a.rel);
             nw.advance(S);
         }
+        if (a.total == 0) {
+            a.ckpt_buf[p] = x;
+            a.ckpt_buf[a.n + p] = y;
+        }
         if (a.xT) a.xT[p] = x;
         if (a.yT) a.yT[p] = y;
 
@@ -139,8 +216,8 @@ adjoint_kernel(AdjArgs a)
             y = a.ckpt_buf[(c * 2 + 1) * a.n + p];
             nw.seek(t0, S);
             for (int j = 0; j < nsub; ++j) {
-                subx[j * T + tid] = x;
-                suby[j * T + tid] = y;
+                a.sub_buf[(int64_t)(2 * j) * a.n + p] = x;
+                a.sub_buf[(int64_t)(2 * j + 1) * a.n + p] = y;
                 const int len = min(kSub, L - j * kSub);
                 for (int i = 0; i < len; ++i) {
                     float q, cc, s;
@@ -151,8 +228,8 @@ adjoint_kernel(AdjArgs a)
             }
             for (int j = nsub - 1; j >= 0; --j) {
                 const int len = min(kSub, L - j * kSub);
-                x = subx[j * T + tid];
-                y = suby[j * T + tid];
+                x = a.sub_buf[(int64_t)(2 * j) * a.n + p];
+                y = a.sub_buf[(int64_t)(2 * j + 1) * a.n + p];
                 nw.seek(t0 + (int64_t)j * kSub, S);
                 for (int i = 0; i < len; ++i) {
                     float q, cc, s;
@@ -165,60 +242,115 @@ adjoint_kernel(AdjArgs a)
                     em_step_f32<KIND>(x, y, ax, cc, ay, s, a.lam, a.ddt, a.rel);
                     nw.advance(S);
                 }
-                float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
-                for (int i = len - 1; i >= 0; --i) {
-                    const float xi = bx[i * T + tid], yi = by[i * T + tid];
-                    const float nx = bnx[i * T + tid], ny = bny[i * T + tid];
-                    float jxx, jxy, dxdl;
-                    if (KIND == PR_MODEL_OU) {          // d_x F = x - lam y
-                        jxx = 1.0f - a.ddt;
-                        jxy = a.lam * a.ddt;
-                        dxdl = a.ddt * yi;
-                    } else {                            // d_x F = x^3 - x + lam y
-                        jxx = 1.0f - a.ddt * (3.0f * xi * xi - 1.0f);
-                        jxy = -a.lam * a.ddt;
-                        dxdl = -a.ddt * yi;
-                    }
-                    const float jyx = a.rel, jyy = 1.0f - a.rel;
-                    p0 = fmaf(lx, dxdl, p0);                                   // d/d lambda
-                    p1 = fmaf(lx, -nx * a.inv2beta, p1);                       // d/d beta (noise amplitude)
-                    p2 = fmaf(ly, -a.rel_over_eps * (xi - yi) - ny * a.inv2eps, p2);   // d/d eps
-                    const float nlx = lx * jxx + ly * jyx;
-                    const float nly = lx * jxy + ly * jyy;
-                    lx = nlx;
-                    ly = nly;
-                }
-                g0 += (double)p0;
-                g1 += (double)p1;
-                g2 += (double)p2;
+                backward_block<KIND>(a, len, T, tid, bx, by, bnx, bny, lx, ly, g0, g1, g2);
             }
         }
-        if (a.xbar0) a.xbar0[p] = (double)lx;
-        if (a.ybar0) a.ybar0[p] = (double)ly;
-        if (a.grad_pp) {
-            a.grad_pp[p * 3 + 0] = g0;
-            a.grad_pp[p * 3 + 1] = g1;
-            a.grad_pp[p * 3 + 2] = g2;
-        }
+        store_outputs(a, p, lx, ly, g0, g1, g2);
     }
-    if (a.partial) {
-        // fixed-order block reduction of the three sums
-        __shared__ double red[3][kAdjThreads / 32];
-        double v[3] = {g0, g1, g2};
-        const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-            if (lane == 0) red[k][warp] = v[k];
+    if (a.partial) block_partials(a, g0, g1, g2);
+}
+
+// Even steps per slice and an even checkpoint interval: every replay starts
+// at an even step of a slice, so each Philox block serves the pair of steps
+// (m, m+1) with words (x, y) and (z, w), as in pr_fine_propagate.
+template <int KIND>
+__global__ void __launch_bounds__(kAdjThreads, 8)
+adjoint_paired_kernel(AdjArgs a)
+{
+    extern __shared__ float asm_[];
+    const int T = blockDim.x, tid = threadIdx.x;
+    float* bx = asm_;
+    float* by = bx + kSub * T;
+    float* bnx = by + kSub * T;
+    float* bny = bnx + kSub * T;
+    const int64_t p = (int64_t)blockIdx.x * T + tid;
+    const bool ok = p < a.n;
+    const uint32_t pid = (uint32_t)p;
+    const int S = a.steps;
+    const float lam = a.lam, ddt = a.ddt, rel = a.rel, sxk = a.sxk, syk = a.syk;
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    float lx = 0.0f, ly = 0.0f;
+
+    auto pair = [&](int slice, int m, float& x, float& y) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(m >> 1), pid, (uint32_t)(a.slice_begin + slice), a.chi),
+                                      a.k0, a.k1);
+        float q0, c0, s0, q1, c1, s1;
+        box_muller_qcs(w.x, w.y, q0, c0, s0);
+        box_muller_qcs(w.z, w.w, q1, c1, s1);
+        em_step_f32<KIND>(x, y, q0 * sxk, c0, q0 * syk, s0, lam, ddt, rel);
+        em_step_f32<KIND>(x, y, q1 * sxk, c1, q1 * syk, s1, lam, ddt, rel);
+    };
+
+    if (ok) {
+        // ---- forward with checkpoints ----
+        float x = a.x0[p], y = a.y0[p];
+        int slice = 0, m = 0;
+        for (int64_t c = 0; c < a.n_ckpt; ++c) {
+            a.ckpt_buf[(c * 2) * a.n + p] = x;
+            a.ckpt_buf[(c * 2 + 1) * a.n + p] = y;
+            const int L = (int)min((int64_t)a.ckpt, a.total - c * a.ckpt);
+            for (int i = 0; i < L; i += 2) {
+                pair(slice, m, x, y);
+                m += 2;
+                if (m == S) { m = 0; ++slice; }
+            }
         }
-        __syncthreads();
-        if (tid < 3) {
-            double s = 0.0;
-            for (int w = 0; w < T / 32; ++w) s += red[tid][w];
-            a.partial[(size_t)blockIdx.x * 3 + tid] = s;
+        if (a.xT) a.xT[p] = x;
+        if (a.yT) a.yT[p] = y;
+
+        // ---- backward ----
+        lx = a.xbar ? (float)a.xbar[p] : 1.0f;
+        ly = a.ybar ? (float)a.ybar[p] : 0.0f;
+        for (int64_t c = a.n_ckpt - 1; c >= 0; --c) {
+            const int64_t t0 = c * a.ckpt;
+            const int L = (int)min((int64_t)a.ckpt, a.total - t0);
+            const int nsub = (L + kSub - 1) / kSub;
+            x = a.ckpt_buf[(c * 2) * a.n + p];
+            y = a.ckpt_buf[(c * 2 + 1) * a.n + p];
+            int slice = (int)(t0 / S), m = (int)(t0 - (int64_t)slice * S);
+            for (int j = 0; j < nsub; ++j) {
+                a.sub_buf[(int64_t)(2 * j) * a.n + p] = x;
+                a.sub_buf[(int64_t)(2 * j + 1) * a.n + p] = y;
+                const int len = min(kSub, L - j * kSub);
+                for (int i = 0; i < len; i += 2) {
+                    pair(slice, m, x, y);
+                    m += 2;
+                    if (m == S) { m = 0; ++slice; }
+                }
+            }
+            for (int j = nsub - 1; j >= 0; --j) {
+                const int len = min(kSub, L - j * kSub);
+                x = a.sub_buf[(int64_t)(2 * j) * a.n + p];
+                y = a.sub_buf[(int64_t)(2 * j + 1) * a.n + p];
+                const int64_t tb = t0 + (int64_t)j * kSub;
+                slice = (int)(tb / S);
+                m = (int)(tb - (int64_t)slice * S);
+                for (int i = 0; i < len; i += 2) {
+                    const uint4 w = philox4x32_10(
+                        make_uint4((uint32_t)(m >> 1), pid, (uint32_t)(a.slice_begin + slice), a.chi), a.k0, a.k1);
+                    float q0, c0, s0, q1, c1, s1;
+                    box_muller_qcs(w.x, w.y, q0, c0, s0);
+                    box_muller_qcs(w.z, w.w, q1, c1, s1);
+                    const float ax0 = q0 * sxk, ay0 = q0 * syk, ax1 = q1 * sxk, ay1 = q1 * syk;
+                    bx[i * T + tid] = x;
+                    by[i * T + tid] = y;
+                    bnx[i * T + tid] = ax0 * c0;
+                    bny[i * T + tid] = ay0 * s0;
+                    em_step_f32<KIND>(x, y, ax0, c0, ay0, s0, lam, ddt, rel);
+                    bx[(i + 1) * T + tid] = x;
+                    by[(i + 1) * T + tid] = y;
+                    bnx[(i + 1) * T + tid] = ax1 * c1;
+                    bny[(i + 1) * T + tid] = ay1 * s1;
+                    em_step_f32<KIND>(x, y, ax1, c1, ay1, s1, lam, ddt, rel);
+                    m += 2;
+                    if (m == S) { m = 0; ++slice; }
+                }
+                backward_block<KIND>(a, len, T, tid, bx, by, bnx, bny, lx, ly, g0, g1, g2);
+            }
         }
+        store_outputs(a, p, lx, ly, g0, g1, g2);
     }
+    if (a.partial) block_partials(a, g0, g1, g2);
 }
 
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int64_t blocks, double* __restrict__ grad)
@@ -295,41 +427,59 @@ inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 using namespace pr;
 
-extern "C" size_t pr_fine_adjoint_workspace(int64_t n, int32_t n_slices, int32_t steps, int32_t ckpt_every)
+namespace pr {
+
+struct AdjLayout {
+    int64_t total, n_ckpt, nsub, blocks;
+    size_t ckpt_bytes, sub_bytes, partial_bytes;
+};
+
+static AdjLayout adjoint_layout(int64_t n, int32_t n_slices, int32_t steps, int32_t ckpt_every)
 {
-    if (n < 1 || n_slices < 1 || steps < 0 || ckpt_every < 1) return 0;
-    const int64_t total = (int64_t)n_slices * steps;
-    const int64_t n_ckpt = std::max<int64_t>(1, (total + ckpt_every - 1) / ckpt_every);
-    const int64_t blocks = (n + kAdjThreads - 1) / kAdjThreads;
-    return align256((size_t)n_ckpt * 2 * n * sizeof(float)) + align256((size_t)blocks * 3 * sizeof(double));
+    AdjLayout l{};
+    l.total = (int64_t)n_slices * steps;
+    l.n_ckpt = std::max<int64_t>(1, (l.total + ckpt_every - 1) / ckpt_every);
+    l.nsub = std::max<int64_t>(1, (std::min<int64_t>(ckpt_every, l.total) + kSub - 1) / kSub);
+    l.blocks = (n + kAdjThreads - 1) / kAdjThreads;
+    l.ckpt_bytes = align256((size_t)l.n_ckpt * 2 * n * sizeof(float));
+    l.sub_bytes = align256((size_t)l.nsub * 2 * n * sizeof(float));
+    l.partial_bytes = align256((size_t)l.blocks * 3 * sizeof(double));
+    return l;
 }
 
-extern "C" pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, const float* x0, const float* y0,
-                                     int64_t n, int32_t slice_begin, int32_t n_slices, int32_t steps, double dt,
-                                     int32_t ckpt_every, float* x_T, float* y_T, const double* xbar_T,
-                                     const double* ybar_T, double* grad, double* xbar_0, double* ybar_0,
-                                     void* workspace, size_t workspace_bytes, void* stream)
+static pr_status adjoint_check(const pr_model* model, const pr_rng* rng, const float* x0, const float* y0,
+                               int64_t n, int32_t slice_begin, int32_t n_slices, int32_t steps, double dt,
+                               int32_t ckpt_every, const double* xbar_T, const double* ybar_T, const double* grad)
 {
-    if (!model || !rng || !x0 || !y0 || !grad || !workspace) return PR_ERR_INVALID_ARG;
+    if (!model || !rng || !x0 || !y0 || !grad) return PR_ERR_INVALID_ARG;
     if (model->kind != PR_MODEL_OU && model->kind != PR_MODEL_DOUBLE_WELL) return PR_ERR_UNSUPPORTED;
     if (model->fast_dim != 1) return PR_ERR_UNSUPPORTED;
     if (!(model->beta > 0.0) || !(model->eps > 0.0) || !(model->tau_x > 0.0)) return PR_ERR_INVALID_ARG;
     if (n < 1 || n > 0xFFFFFFFFll || n_slices < 1 || slice_begin < 0 || steps < 0 || ckpt_every < 1) return PR_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !isfinite(dt) || rng->problem_id >= (1u << 24)) return PR_ERR_INVALID_ARG;
     if (ybar_T && !xbar_T) return PR_ERR_INVALID_ARG;
-    const size_t need = pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every);
-    if (workspace_bytes < need || ((uintptr_t)workspace & 255)) return PR_ERR_INVALID_ARG;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return PR_OK;
+}
 
+// Fills the arguments and launches; `ws` holds checkpoints, sub-checkpoints
+// and per-block partial sums, in that order (every word is written before it
+// is read in the same call, so nothing is cleared).
+static pr_status adjoint_launch(const pr_model* model, const pr_rng* rng, const float* x0, const float* y0,
+                                int64_t n, int32_t slice_begin, int32_t n_slices, int32_t steps, double dt,
+                                int32_t ckpt_every, float* x_T, float* y_T, const double* xbar_T,
+                                const double* ybar_T, double* grad, double* xbar_0, double* ybar_0, void* ws,
+                                cudaStream_t st)
+{
+    const AdjLayout l = adjoint_layout(n, n_slices, steps, ckpt_every);
     AdjArgs a{};
     a.x0 = x0;
     a.y0 = y0;
     a.n = n;
     a.slice_begin = slice_begin;
     a.steps = steps;
-    a.total = (int64_t)n_slices * steps;
+    a.total = l.total;
     a.ckpt = ckpt_every;
-    a.n_ckpt = std::max<int64_t>(1, (a.total + ckpt_every - 1) / ckpt_every);
+    a.n_ckpt = l.n_ckpt;
     const double drift_dt = dt / model->tau_x, relax = dt / model->eps;
     const double sx = sqrt(2.0 * (1.0 / model->beta) / model->tau_x) * sqrt(dt);
     const double sy = sqrt(2.0 / model->eps) * sqrt(dt);
@@ -344,12 +494,11 @@ extern "C" pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, c
     a.k0 = (uint32_t)(rng->seed & 0xFFFFFFFFull);
     a.k1 = (uint32_t)(rng->seed >> 32);
     a.chi = rng->problem_id << 8;
-    const int64_t blocks = (n + kAdjThreads - 1) / kAdjThreads;
-    a.ckpt_buf = static_cast<float*>(workspace);
+    char* base = static_cast<char*>(ws);
+    a.ckpt_buf = reinterpret_cast<float*>(base);
+    a.sub_buf = reinterpret_cast<float*>(base + l.ckpt_bytes);
     const bool sum_mode = xbar_T != nullptr;
-    a.partial = sum_mode ? reinterpret_cast<double*>(static_cast<char*>(workspace) +
-                                                     align256((size_t)a.n_ckpt * 2 * n * sizeof(float)))
-                         : nullptr;
+    a.partial = sum_mode ? reinterpret_cast<double*>(base + l.ckpt_bytes + l.sub_bytes) : nullptr;
     a.xT = x_T;
     a.yT = y_T;
     a.xbar = xbar_T;
@@ -357,21 +506,47 @@ extern "C" pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, c
     a.grad_pp = sum_mode ? nullptr : grad;
     a.xbar0 = xbar_0;
     a.ybar0 = ybar_0;
-    const size_t smem = (size_t)6 * kSub * kAdjThreads * sizeof(float);
+    const size_t smem = (size_t)4 * kSub * kAdjThreads * sizeof(float);
+    const bool paired = steps > 0 && (steps % 2) == 0 && (ckpt_every % 2) == 0;
+    const unsigned grid = (unsigned)l.blocks;
     if (model->kind == PR_MODEL_OU) {
-        PR_TRY_CUDA(cudaFuncSetAttribute(adjoint_kernel<PR_MODEL_OU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        adjoint_kernel<PR_MODEL_OU><<<(unsigned)blocks, kAdjThreads, smem, st>>>(a);
+        if (paired) adjoint_paired_kernel<PR_MODEL_OU><<<grid, kAdjThreads, smem, st>>>(a);
+        else adjoint_kernel<PR_MODEL_OU><<<grid, kAdjThreads, smem, st>>>(a);
     } else {
-        PR_TRY_CUDA(cudaFuncSetAttribute(adjoint_kernel<PR_MODEL_DOUBLE_WELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        adjoint_kernel<PR_MODEL_DOUBLE_WELL><<<(unsigned)blocks, kAdjThreads, smem, st>>>(a);
+        if (paired) adjoint_paired_kernel<PR_MODEL_DOUBLE_WELL><<<grid, kAdjThreads, smem, st>>>(a);
+        else adjoint_kernel<PR_MODEL_DOUBLE_WELL><<<grid, kAdjThreads, smem, st>>>(a);
     }
     PR_CHECK_LAUNCH();
     if (sum_mode) {
-        reduce_partials_kernel<<<1, 256, 0, st>>>(a.partial, blocks, grad);
+        reduce_partials_kernel<<<1, 256, 0, st>>>(a.partial, l.blocks, grad);
         PR_CHECK_LAUNCH();
     }
     return PR_OK;
+}
+
+}  // namespace pr
+
+extern "C" size_t pr_fine_adjoint_workspace(int64_t n, int32_t n_slices, int32_t steps, int32_t ckpt_every)
+{
+    if (n < 1 || n_slices < 1 || steps < 0 || ckpt_every < 1) return 0;
+    const AdjLayout l = adjoint_layout(n, n_slices, steps, ckpt_every);
+    return l.ckpt_bytes + l.sub_bytes + l.partial_bytes;
+}
+
+extern "C" pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, const float* x0, const float* y0,
+                                     int64_t n, int32_t slice_begin, int32_t n_slices, int32_t steps, double dt,
+                                     int32_t ckpt_every, float* x_T, float* y_T, const double* xbar_T,
+                                     const double* ybar_T, double* grad, double* xbar_0, double* ybar_0,
+                                     void* workspace, size_t workspace_bytes, void* stream)
+{
+    const pr_status chk = adjoint_check(model, rng, x0, y0, n, slice_begin, n_slices, steps, dt, ckpt_every,
+                                        xbar_T, ybar_T, grad);
+    if (chk != PR_OK) return chk;
+    if (!workspace) return PR_ERR_INVALID_ARG;
+    const size_t need = pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every);
+    if (workspace_bytes < need || ((uintptr_t)workspace & 255)) return PR_ERR_INVALID_ARG;
+    return adjoint_launch(model, rng, x0, y0, n, slice_begin, n_slices, steps, dt, ckpt_every, x_T, y_T, xbar_T,
+                          ybar_T, grad, xbar_0, ybar_0, workspace, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" size_t pr_order_statistics_workspace(int64_t n)
@@ -442,71 +617,14 @@ extern "C" pr_status pr_fine_adjoint_noalloc(const pr_model* model, const pr_rng
                                              const double* xbar_T, const double* ybar_T, double* grad,
                                              double* xbar_0, double* ybar_0, void* stream)
 {
-    if (!model || !rng || !x0 || !y0 || !grad) return PR_ERR_INVALID_ARG;
-    if (model->kind != PR_MODEL_OU && model->kind != PR_MODEL_DOUBLE_WELL) return PR_ERR_UNSUPPORTED;
-    if (model->fast_dim != 1) return PR_ERR_UNSUPPORTED;
-    if (!(model->beta > 0.0) || !(model->eps > 0.0) || !(model->tau_x > 0.0)) return PR_ERR_INVALID_ARG;
-    if (n < 1 || n > 0xFFFFFFFFll || n_slices < 1 || slice_begin < 0 || steps < 0 || ckpt_every < 1) return PR_ERR_INVALID_ARG;
-    if (!(dt > 0.0) || !isfinite(dt) || rng->problem_id >= (1u << 24)) return PR_ERR_INVALID_ARG;
-    if (ybar_T && !xbar_T) return PR_ERR_INVALID_ARG;
+    const pr_status chk = adjoint_check(model, rng, x0, y0, n, slice_begin, n_slices, steps, dt, ckpt_every,
+                                        xbar_T, ybar_T, grad);
+    if (chk != PR_OK) return chk;
     // the problem must fit the fixed array (checked before anything else runs)
     if (pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every) > kNoAllocScratchBytes) return PR_ERR_NOMEM;
     void* scratch = nullptr;
     const pr_status got = adjoint_scratch_address(&scratch);
     if (got != PR_OK) return got;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-
-    AdjArgs a{};
-    a.x0 = x0;
-    a.y0 = y0;
-    a.n = n;
-    a.slice_begin = slice_begin;
-    a.steps = steps;
-    a.total = (int64_t)n_slices * steps;
-    a.ckpt = ckpt_every;
-    a.n_ckpt = std::max<int64_t>(1, (a.total + ckpt_every - 1) / ckpt_every);
-    const double drift_dt = dt / model->tau_x, relax = dt / model->eps;
-    const double sx = sqrt(2.0 * (1.0 / model->beta) / model->tau_x) * sqrt(dt);
-    const double sy = sqrt(2.0 / model->eps) * sqrt(dt);
-    a.lam = (float)model->lambda;
-    a.ddt = (float)drift_dt;
-    a.rel = (float)relax;
-    a.sxk = (float)(sx * 1.1774100225154746910);
-    a.syk = (float)(sy * 1.1774100225154746910);
-    a.inv2beta = (float)(0.5 / model->beta);
-    a.inv2eps = (float)(0.5 / model->eps);
-    a.rel_over_eps = (float)(dt / (model->eps * model->eps));
-    a.k0 = (uint32_t)(rng->seed & 0xFFFFFFFFull);
-    a.k1 = (uint32_t)(rng->seed >> 32);
-    a.chi = rng->problem_id << 8;
-    const int64_t blocks = (n + kAdjThreads - 1) / kAdjThreads;
-    // checkpoints first, then the per-block partial sums; every word is
-    // written before it is read in the same call, so nothing is cleared
-    a.ckpt_buf = static_cast<float*>(scratch);
-    const bool sum_mode = xbar_T != nullptr;
-    a.partial = sum_mode ? reinterpret_cast<double*>(static_cast<char*>(scratch) +
-                                                     align256((size_t)a.n_ckpt * 2 * n * sizeof(float)))
-                         : nullptr;
-    a.xT = x_T;
-    a.yT = y_T;
-    a.xbar = xbar_T;
-    a.ybar = ybar_T;
-    a.grad_pp = sum_mode ? nullptr : grad;
-    a.xbar0 = xbar_0;
-    a.ybar0 = ybar_0;
-    const size_t smem = (size_t)6 * kSub * kAdjThreads * sizeof(float);
-    if (model->kind == PR_MODEL_OU) {
-        PR_TRY_CUDA(cudaFuncSetAttribute(adjoint_kernel<PR_MODEL_OU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        adjoint_kernel<PR_MODEL_OU><<<(unsigned)blocks, kAdjThreads, smem, st>>>(a);
-    } else {
-        PR_TRY_CUDA(cudaFuncSetAttribute(adjoint_kernel<PR_MODEL_DOUBLE_WELL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        adjoint_kernel<PR_MODEL_DOUBLE_WELL><<<(unsigned)blocks, kAdjThreads, smem, st>>>(a);
-    }
-    PR_CHECK_LAUNCH();
-    if (sum_mode) {
-        reduce_partials_kernel<<<1, 256, 0, st>>>(a.partial, blocks, grad);
-        PR_CHECK_LAUNCH();
-    }
-    return PR_OK;
+    return adjoint_launch(model, rng, x0, y0, n, slice_begin, n_slices, steps, dt, ckpt_every, x_T, y_T, xbar_T,
+                          ybar_T, grad, xbar_0, ybar_0, scratch, static_cast<cudaStream_t>(stream));
 }

@@ -123,13 +123,14 @@ batch_fine_kernel(BatchFineArgs a)
             prior = a.fprev + P.c_off + (int64_t)(s - 1) * (bins + 1);
         }
         MatchSmem ms = carve_match_smem(mbase, bins);
-        if (do_match) build_match_table(P.g, prior, a.rho + P.r_off + (int64_t)s * (bins + 1), ms);
+        if (do_match) build_match_table(P.g, thr, prior, a.rho + P.r_off + (int64_t)s * (bins + 1), ms);
         __syncthreads();
+        const BinF32 bf = make_bin_f32(thr, bins, P.lo_f, P.inv_h_f);
         float* xout = a.xb + P.x_off + (int64_t)s * n;
         float* yout = a.yb + P.x_off + (int64_t)s * n;
         const int steps = a.steps_div > 1 ? (P.steps + a.steps_div - 1) / a.steps_div : P.steps;
         const D1Consts c{P.lam, P.ddt, P.rel, P.sxk, P.syk, P.k0, P.k1, P.chi};
-        const D1Smem sm{thr, hs, he, &ms, bins, P.lo_f, P.inv_h_f, do_match, true, true};
+        const D1Smem sm{thr, hs, he, &ms, bf, do_match, true, true};
         if (P.kind == PR_MODEL_OU)
             fine_d1_range<PR_MODEL_OU, PPT>(xin, yin, xout, yout, it.begin, it.end, (uint32_t)s, steps, c, sm);
         else

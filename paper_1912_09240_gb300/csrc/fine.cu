@@ -136,11 +136,12 @@ fine_f32_d1_kernel(FineArgs a, FineSmemOffsets so, int flags)
         }
         if (do_match) {
             ms = carve_match_smem(smem + so.match, bins);
-            build_match_table(a.g, a.cdf_prior + (size_t)s * (bins + 1),
+            build_match_table(a.g, thr, a.cdf_prior + (size_t)s * (bins + 1),
                               a.cdf_target + (size_t)s * (bins + 1), ms);
         }
         __syncthreads();
     }
+    const BinF32 bf = any_grid ? make_bin_f32(thr, bins, a.lo_f, a.inv_h_f) : BinF32{};
 
     const int64_t N = a.n;
     const float* __restrict__ xin = static_cast<const float*>(a.x_in) + (int64_t)s * a.in_slice_stride;
@@ -148,7 +149,7 @@ fine_f32_d1_kernel(FineArgs a, FineSmemOffsets so, int flags)
     float* __restrict__ xout = static_cast<float*>(a.x_out) + (int64_t)s * N;
     float* __restrict__ yout = static_cast<float*>(a.y_out) + (int64_t)s * N;
     D1Consts cst{a.lam_f, a.drift_dt_f, a.relax_f, a.sxk_f, a.syk_f, a.k0, a.k1, a.ctr_hi};
-    D1Smem sm{thr, hist_s, hist_e, &ms, bins, a.lo_f, a.inv_h_f, do_match, do_hs, do_he};
+    D1Smem sm{thr, hist_s, hist_e, &ms, bf, do_match, do_hs, do_he};
     const int64_t span = (int64_t)a.tiles_per_cta * blockDim.x * PPT;
     const int64_t p_begin = (int64_t)blockIdx.x * span;
     fine_d1_range<KIND, PPT>(xin, yin, xout, yout, p_begin, min(N, p_begin + span), slice, a.steps, cst, sm);
@@ -167,7 +168,7 @@ fine_f32_d1_kernel(FineArgs a, FineSmemOffsets so, int flags)
 // ---------------------------------------------------------------------------
 
 template <int KIND, int D>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -187,11 +188,12 @@ fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
         }
         if (do_match) {
             ms = carve_match_smem(smem + so.match, bins);
-            build_match_table(a.g, a.cdf_prior + (size_t)s * (bins + 1),
+            build_match_table(a.g, thr, a.cdf_prior + (size_t)s * (bins + 1),
                               a.cdf_target + (size_t)s * (bins + 1), ms);
         }
         __syncthreads();
     }
+    const BinF32 bf = any_grid ? make_bin_f32(thr, bins, a.lo_f, a.inv_h_f) : BinF32{};
     const int64_t N = a.n;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = p < N;
@@ -204,8 +206,8 @@ fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
     float y[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) y[j] = ok ? yin[(int64_t)j * N + p] : 0.0f;
-    if (do_match && ok) x = match_one_f32(ms, thr, bins, a.lo_f, a.inv_h_f, x);
-    if (do_hs && ok) atomicAdd(&hist_s[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x)], 1u);
+    if (do_match && ok) x = match_one_f32(ms, thr, bf, x);
+    if (do_hs && ok) atomicAdd(&hist_s[bin_fast_f32(bf, thr, x)], 1u);
 
     const float lam = a.lam_f, ddt = a.drift_dt_f, rel = a.relax_f;
     const float sx = a.sx_f, sy = a.sy_f;
@@ -235,7 +237,7 @@ fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
         xout[p] = x;
 #pragma unroll
         for (int j = 0; j < D; ++j) yout[(int64_t)j * N + p] = y[j];
-        if (do_he) atomicAdd(&hist_e[bin_of_f32(thr, bins, a.lo_f, a.inv_h_f, x)], 1u);
+        if (do_he) atomicAdd(&hist_e[bin_fast_f32(bf, thr, x)], 1u);
     }
     if (do_hs || do_he) {
         __syncthreads();
@@ -372,28 +374,77 @@ counts_to_cdf_kernel(const uint32_t* __restrict__ counts, int64_t n, int bins, d
 // standalone restriction: histogram per slice, binary32 or binary64 input
 // ---------------------------------------------------------------------------
 
+// Streams the elements [b, e) of one slice: `op1(value)` on a scalar head up
+// to the next 16-byte boundary and on a scalar tail, `op8(u0, u1)` on pairs
+// of 16-byte vectors (two loads in flight per thread) and `op4(u)` on a last
+// single vector.
+template <typename Op1, typename Op4, typename Op8>
+__device__ __forceinline__ void for_each_f32(const float* __restrict__ xs, int64_t b, int64_t e, Op1 op1, Op4 op4,
+                                             Op8 op8)
+{
+    const int T = blockDim.x, t = threadIdx.x;
+    const int64_t mis = (int64_t)(((uintptr_t)(xs + b) >> 2) & 3);
+    const int64_t hb = min(e, b + ((4 - mis) & 3));
+    for (int64_t p = b + t; p < hb; p += T) op1(xs[p]);
+    const int64_t nv = (e - hb) >> 2;
+    const float4* __restrict__ v = reinterpret_cast<const float4*>(xs + hb);
+    int64_t q = t;
+    for (; q + T < nv; q += 2 * T) op8(__ldcs(v + q), __ldcs(v + q + T));
+    if (q < nv) op4(__ldcs(v + q));
+    for (int64_t p = hb + 4 * nv + t; p < e; p += T) op1(xs[p]);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(512)
 restrict_kernel(const T* __restrict__ x, int64_t n, GridDev g, float lo_f, float inv_h_f,
                 uint32_t* __restrict__ counts, int64_t per_block)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float s_thr[2];
     const int bins = g.bins;
-    float* thr = reinterpret_cast<float*>(smem);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + align16((size_t)(bins + 1) * sizeof(float)));
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
     const int s = blockIdx.y;
-    if (sizeof(T) == 4) build_thresholds(g, thr);
+    if (threadIdx.x == 0) {
+        s_thr[0] = __double2float_ru(edge(g, 0));
+        s_thr[1] = __double2float_ru(edge(g, bins));
+    }
     for (int i = threadIdx.x; i < bins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
     const T* xs = x + (int64_t)s * n;
     const int64_t b = (int64_t)blockIdx.x * per_block;
     const int64_t e = min(n, b + per_block);
-    for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
-        const T v = xs[p];
-        int i;
-        if (sizeof(T) == 4) i = bin_of_f32(thr, bins, lo_f, inv_h_f, (float)v);
-        else i = bin_of_f64(g, (double)v);
-        atomicAdd(&hist[i], 1u);
+    if (sizeof(T) == 4) {
+        // thresholds are computed only for the few particles near an edge,
+        // decided once per group of values so that the common case has no
+        // divergent branch
+        const BinF32 bf = make_bin_f32(s_thr[0], s_thr[1], bins, lo_f, inv_h_f);
+        const auto thr_of = [g](int k) { return __double2float_ru(edge(g, k)); };
+        auto group4 = [&](float4 u, int m) {
+            int i0 = bin_try_f32(bf, u.x);
+            int i1 = m > 1 ? bin_try_f32(bf, u.y) : 0;
+            int i2 = m > 2 ? bin_try_f32(bf, u.z) : 0;
+            int i3 = m > 3 ? bin_try_f32(bf, u.w) : 0;
+            if ((i0 | i1 | i2 | i3) < 0) {
+                if (i0 < 0) i0 = bin_slow_f32(bf, thr_of, u.x);
+                if (i1 < 0) i1 = bin_slow_f32(bf, thr_of, u.y);
+                if (i2 < 0) i2 = bin_slow_f32(bf, thr_of, u.z);
+                if (i3 < 0) i3 = bin_slow_f32(bf, thr_of, u.w);
+            }
+            atomicAdd(&hist[i0], 1u);
+            if (m > 1) atomicAdd(&hist[i1], 1u);
+            if (m > 2) atomicAdd(&hist[i2], 1u);
+            if (m > 3) atomicAdd(&hist[i3], 1u);
+        };
+        for_each_f32(
+            reinterpret_cast<const float*>(xs), b, e, [&](float v) { group4(make_float4(v, v, v, v), 1); },
+            [&](float4 u) { group4(u, 4); },
+            [&](float4 u0, float4 u1) {
+                group4(u0, 4);
+                group4(u1, 4);
+            });
+    } else {
+        for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x)
+            atomicAdd(&hist[bin_of_f64(g, (double)xs[p])], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < bins; i += blockDim.x)
@@ -404,7 +455,7 @@ restrict_kernel(const T* __restrict__ x, int64_t n, GridDev g, float lo_f, float
 // standalone matching
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
 match_f32_kernel(const float* __restrict__ xp, float* __restrict__ xo, int64_t n, GridDev g,
                  float lo_f, float inv_h_f, const double* __restrict__ cp,
                  const double* __restrict__ ct, int64_t per_block)
@@ -415,13 +466,41 @@ match_f32_kernel(const float* __restrict__ xp, float* __restrict__ xo, int64_t n
     MatchSmem ms = carve_match_smem(smem + align16((size_t)(bins + 1) * sizeof(float)), bins);
     const int s = blockIdx.y;
     build_thresholds(g, thr);
-    build_match_table(g, cp + (size_t)s * (bins + 1), ct + (size_t)s * (bins + 1), ms);
+    build_match_table(g, thr, cp + (size_t)s * (bins + 1), ct + (size_t)s * (bins + 1), ms);
+    const BinF32 bf = make_bin_f32(thr, bins, lo_f, inv_h_f);
     const int64_t b = (int64_t)blockIdx.x * per_block;
     const int64_t e = min(n, b + per_block);
     const float* xs = xp + (int64_t)s * n;
     float* os = xo + (int64_t)s * n;
-    for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x)
-        os[p] = match_one_f32(ms, thr, bins, lo_f, inv_h_f, xs[p]);
+    // vector stores need the output at the same offset from a 16-byte boundary
+    if ((((uintptr_t)xs ^ (uintptr_t)os) & 15) == 0) {
+        const int T = blockDim.x, t = threadIdx.x;
+        const int64_t mis = (int64_t)(((uintptr_t)(xs + b) >> 2) & 3);
+        const int64_t hb = min(e, b + ((4 - mis) & 3));
+        for (int64_t p = b + t; p < hb; p += T) os[p] = match_one_f32(ms, thr, bf, xs[p]);
+        const int64_t nv = (e - hb) >> 2;
+        const float4* __restrict__ v = reinterpret_cast<const float4*>(xs + hb);
+        float4* __restrict__ w = reinterpret_cast<float4*>(os + hb);
+        auto map4 = [&](float4 u) {
+            u.x = match_one_f32(ms, thr, bf, u.x);
+            u.y = match_one_f32(ms, thr, bf, u.y);
+            u.z = match_one_f32(ms, thr, bf, u.z);
+            u.w = match_one_f32(ms, thr, bf, u.w);
+            return u;
+        };
+        int64_t q = t;
+        for (; q + T < nv; q += 2 * T) {
+            const float4 u0 = __ldcs(v + q);
+            const float4 u1 = __ldcs(v + q + T);
+            __stcs(w + q, map4(u0));
+            __stcs(w + q + T, map4(u1));
+        }
+        if (q < nv) __stcs(w + q, map4(__ldcs(v + q)));
+        for (int64_t p = hb + 4 * nv + t; p < e; p += T) os[p] = match_one_f32(ms, thr, bf, xs[p]);
+    } else {
+        for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x)
+            os[p] = match_one_f32(ms, thr, bf, xs[p]);
+    }
 }
 
 __global__ void __launch_bounds__(256)
@@ -463,6 +542,18 @@ static bool model_ok(const pr_model* m)
     return true;
 }
 
+// Elements per CTA for a streaming pass over n_slices x n elements: as many
+// CTAs per slice as fit one wave (per_sm CTAs per SM) over all slices, at
+// least min_per elements each, a multiple of 4 (whole vectors).
+static int64_t stream_range(int64_t n, int n_slices, int64_t min_per, int per_sm)
+{
+    const int64_t slots = (int64_t)num_sms() * per_sm;
+    int64_t bps = std::max<int64_t>(1, slots / n_slices);
+    bps = std::min<int64_t>(bps, std::max<int64_t>(1, n / min_per));
+    int64_t per = (n + bps - 1) / bps;
+    return (per + 3) & ~(int64_t)3;
+}
+
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes)
 {
@@ -498,7 +589,9 @@ template <int KIND, int D>
 static pr_status launch_f32_dn(const FineArgs& a, FineSmemOffsets so, int flags, size_t smem,
                                int n_slices, cudaStream_t st)
 {
-    const int threads = a.n >= 4096 ? 256 : 64;
+    // 512 threads: the matching table (up to ~90 KB at 1024 bins) allows two
+    // CTAs per SM, so larger CTAs keep more warps resident
+    const int threads = a.n >= 16384 ? 512 : (a.n >= 4096 ? 256 : 64);
     dim3 grid((unsigned)((a.n + threads - 1) / threads), (unsigned)n_slices);
     auto k = fine_f32_dn_kernel<KIND, D>;
     PR_TRY_CUDA(set_smem(k, smem));
@@ -690,18 +783,15 @@ extern "C" pr_status pr_restrict(pr_precision precision, const void* x, int64_t 
     PR_TRY_CUDA(cudaMemsetAsync(counts, 0, (size_t)n_slices * bins * 4, st));
     const GridDev g = make_grid(*grid);
     const float lo_f = (float)grid->x_lo, inv_h_f = (float)(1.0 / g.h);
-    // enough CTAs for ~4 per SM over all slices, each a contiguous range
-    const int sms = num_sms();
-    int64_t blocks_per_slice = ((int64_t)sms * 4 + n_slices - 1) / n_slices;
-    const int64_t min_per = 8192;
-    blocks_per_slice = std::max<int64_t>(1, std::min<int64_t>(blocks_per_slice, (n + min_per - 1) / min_per));
-    const int64_t per_block = (n + blocks_per_slice - 1) / blocks_per_slice;
-    const size_t smem = align16((size_t)(bins + 1) * 4) + align16((size_t)bins * 4);
+    // one wave of 512-thread CTAs (4 per SM), each a contiguous range of one slice
+    const int64_t per_block = stream_range(n, n_slices, 4096, 4);
+    const int64_t blocks_per_slice = (n + per_block - 1) / per_block;
+    const size_t smem = align16((size_t)bins * 4);
     dim3 gr((unsigned)blocks_per_slice, (unsigned)n_slices);
     if (precision == PR_F32) {
-        restrict_kernel<float><<<gr, 1024, smem, st>>>(static_cast<const float*>(x), n, g, lo_f, inv_h_f, counts, per_block);
+        restrict_kernel<float><<<gr, 512, smem, st>>>(static_cast<const float*>(x), n, g, lo_f, inv_h_f, counts, per_block);
     } else {
-        restrict_kernel<double><<<gr, 1024, smem, st>>>(static_cast<const double*>(x), n, g, lo_f, inv_h_f, counts, per_block);
+        restrict_kernel<double><<<gr, 512, smem, st>>>(static_cast<const double*>(x), n, g, lo_f, inv_h_f, counts, per_block);
     }
     PR_CHECK_LAUNCH();
     if (cdf) {
@@ -721,16 +811,14 @@ extern "C" pr_status pr_match(pr_precision precision, const void* x_prior, void*
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int bins = grid->bins;
     const GridDev g = make_grid(*grid);
-    const int sms = num_sms();
-    int64_t blocks_per_slice = ((int64_t)sms * 2 + n_slices - 1) / n_slices;
-    const int64_t min_per = 16384;
-    blocks_per_slice = std::max<int64_t>(1, std::min<int64_t>(blocks_per_slice, (n + min_per - 1) / min_per));
-    const int64_t per_block = (n + blocks_per_slice - 1) / blocks_per_slice;
+    // one 1024-thread CTA per SM: the table is built once per SM (FP64 work)
+    const int64_t per_block = stream_range(n, n_slices, 16384, 1);
+    const int64_t blocks_per_slice = (n + per_block - 1) / per_block;
     dim3 gr((unsigned)blocks_per_slice, (unsigned)n_slices);
     if (precision == PR_F32) {
         const size_t smem = align16((size_t)(bins + 1) * 4) + match_smem_bytes(bins);
         PR_TRY_CUDA(set_smem(match_f32_kernel, smem));
-        match_f32_kernel<<<gr, 512, smem, st>>>(static_cast<const float*>(x_prior), static_cast<float*>(x_out), n, g,
+        match_f32_kernel<<<gr, 1024, smem, st>>>(static_cast<const float*>(x_prior), static_cast<float*>(x_out), n, g,
                                                 (float)grid->x_lo, (float)(1.0 / g.h), cdf_prior, cdf_target, per_block);
     } else {
         const size_t smem = match_smem_bytes(bins);

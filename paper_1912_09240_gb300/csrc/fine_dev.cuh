@@ -19,8 +19,7 @@ struct D1Smem {
     uint32_t* hist_s;                // restriction of the start state [bins]
     uint32_t* hist_e;                // restriction of the end state [bins]
     const MatchSmem* ms;             // matching table (when do_match)
-    int bins;
-    float lo_f, inv_h_f;
+    BinF32 bf;                       // binning constants (after thr is built)
     bool do_match, do_hs, do_he;
 };
 
@@ -52,12 +51,12 @@ __device__ __forceinline__ void fine_d1_range(const float* __restrict__ xin, con
         if (sm.do_match) {
 #pragma unroll
             for (int k = 0; k < PPT; ++k)
-                if (ok[k]) x[k] = match_one_f32(*sm.ms, sm.thr, sm.bins, sm.lo_f, sm.inv_h_f, x[k]);
+                if (ok[k]) x[k] = match_one_f32(*sm.ms, sm.thr, sm.bf, x[k]);
         }
         if (sm.do_hs) {
 #pragma unroll
             for (int k = 0; k < PPT; ++k)
-                if (ok[k]) atomicAdd(&sm.hist_s[bin_of_f32(sm.thr, sm.bins, sm.lo_f, sm.inv_h_f, x[k])], 1u);
+                if (ok[k]) atomicAdd(&sm.hist_s[bin_fast_f32(sm.bf, sm.thr, x[k])], 1u);
         }
         for (int mp = 0; mp < pairs; ++mp) {
 #pragma unroll
@@ -86,7 +85,7 @@ __device__ __forceinline__ void fine_d1_range(const float* __restrict__ xin, con
             const int64_t p = base + (int64_t)k * blockDim.x;
             xout[p] = x[k];
             yout[p] = y[k];
-            if (sm.do_he) atomicAdd(&sm.hist_e[bin_of_f32(sm.thr, sm.bins, sm.lo_f, sm.inv_h_f, x[k])], 1u);
+            if (sm.do_he) atomicAdd(&sm.hist_e[bin_fast_f32(sm.bf, sm.thr, x[k])], 1u);
         }
     }
 }

@@ -18,57 +18,70 @@
 
 namespace pr {
 
-// Shared-memory layout of the binary32 table (bins = I):
-//   Cp, Ct      : double [I+1]     prior / target CDF
-//   nzpre       : int    [I+1]     number of non-empty target bins below j
-//   nzlist      : int    [I]       non-empty target bins in order
-//   jfirst      : int    [I]       first piece's target bin of prior bin i
-//   pstart      : int    [I+1]     first piece of prior bin i (pstart[i] == pstart[i+1]: identity)
-//   fend, alpha, beta : float [2I+1]
-//   jp          : int    [2I+1]    target bin of each piece (the result is clamped into it)
+// Shared-memory layout (bins = I).  The table, live while particles are mapped:
+//   piece  : float4 [2I+1]  (f_end, alpha, beta, target bin j as int bits):
+//            on prior bin i the map is X = clamp(alpha + beta f, thr[j], thr[j+1])
+//            for the first piece of the bin whose f_end >= f (or its last piece)
+//   pst    : int2   [I]     pieces [pst.x, pst.y) of prior bin i (pst.x == pst.y: identity)
+// Build scratch, dead once the table is built:
+//   Cp, Ct : double [I+1]   prior / target CDF
+//   nzpre  : int    [I+1]   number of non-empty target bins below j
+//   nzlist : int    [I]     non-empty target bins in order
+//   jfirst : int    [I]     first piece's target bin of prior bin i
+//   pstart : int    [I+1]   first piece of prior bin i
+// The binary64 path keeps using Cp, Ct, nzpre and nzlist while it maps.
 struct MatchSmem {
+    float4* piece;
+    int2* pst;
     double* Cp;
     double* Ct;
     int* nzpre;
     int* nzlist;
     int* jfirst;
     int* pstart;
-    float* fend;
-    float* alpha;
-    float* beta;
-    int* jp;
     int* scratch;   // [blockDim.x / 32 + 1] for scans
 };
 
-__host__ __device__ inline size_t match_smem_bytes(int bins)
+__host__ __device__ inline size_t match_table_bytes(int bins)
+{
+    const size_t I = (size_t)bins;
+    return (((2 * I + 1) * 16 + I * 8) + 15) & ~(size_t)15;
+}
+
+__host__ __device__ inline size_t match_build_bytes(int bins)
 {
     const size_t I = (size_t)bins;
     size_t b = 2 * (I + 1) * sizeof(double);
     b += (I + 1 + I + I + I + 1) * sizeof(int);
-    b += 3 * (2 * I + 1) * sizeof(float);
-    b += (2 * I + 1) * sizeof(int);
     b += 64 * sizeof(int);
     return (b + 15) & ~(size_t)15;
 }
 
+__host__ __device__ inline size_t match_smem_bytes(int bins) { return match_table_bytes(bins) + match_build_bytes(bins); }
+
+// `base` 16-byte aligned; the build scratch starts match_table_bytes(bins) after it.
 __device__ inline MatchSmem carve_match_smem(unsigned char* base, int bins)
 {
     const int I = bins;
     MatchSmem m;
-    m.Cp = reinterpret_cast<double*>(base);
+    m.piece = reinterpret_cast<float4*>(base);
+    m.pst = reinterpret_cast<int2*>(m.piece + (2 * I + 1));
+    m.Cp = reinterpret_cast<double*>(base + match_table_bytes(bins));
     m.Ct = m.Cp + (I + 1);
     int* ip = reinterpret_cast<int*>(m.Ct + (I + 1));
     m.nzpre = ip;
     m.nzlist = m.nzpre + (I + 1);
     m.jfirst = m.nzlist + I;
     m.pstart = m.jfirst + I;
-    float* fp = reinterpret_cast<float*>(m.pstart + (I + 1));
-    m.fend = fp;
-    m.alpha = m.fend + (2 * I + 1);
-    m.beta = m.alpha + (2 * I + 1);
-    m.jp = reinterpret_cast<int*>(m.beta + (2 * I + 1));
-    m.scratch = m.jp + (2 * I + 1);
+    m.scratch = m.pstart + (I + 1);
     return m;
+}
+
+// Equality of two doubles by their bits (+0 and -0 equal); no FP64 unit.
+__device__ __forceinline__ bool deq(double a, double b)
+{
+    const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+    return x == y || ((x | y) << 1) == 0;
 }
 
 // Block-wide exclusive scan of v[0..n) (ints) into out[0..n], out[n] = total.
@@ -138,7 +151,9 @@ __device__ __forceinline__ int target_bin(const double* Ct, const int* nzpre, co
 }
 
 // Build the binary32 table for one slice.  All threads of the block call it.
-__device__ inline void build_match_table(const GridDev& g, const double* __restrict__ cp_g,
+// thr[] (the binary32 thresholds of the grid) must be written by the block
+// before the call; it is read after the first barrier inside.
+__device__ inline void build_match_table(const GridDev& g, const float* thr, const double* __restrict__ cp_g,
                                          const double* __restrict__ ct_g, MatchSmem& m)
 {
     const int I = g.bins;
@@ -159,7 +174,7 @@ __device__ inline void build_match_table(const GridDev& g, const double* __restr
     // pieces per prior bin (pstart used as the count array)
     for (int i = threadIdx.x; i < I; i += blockDim.x) {
         int cnt = 0;
-        const bool ident = (m.Cp[i] == m.Ct[i]) && (m.Cp[i + 1] == m.Ct[i + 1]);
+        const bool ident = deq(m.Cp[i], m.Ct[i]) && deq(m.Cp[i + 1], m.Ct[i + 1]);
         if (!ident && nnz > 0) {
             const int j0 = target_bin(m.Ct, m.nzpre, m.nzlist, I, m.Cp[i]);
             const int j1 = target_bin(m.Ct, m.nzpre, m.nzlist, I, m.Cp[i + 1]);
@@ -181,8 +196,13 @@ __device__ inline void build_match_table(const GridDev& g, const double* __restr
         __syncthreads();
     }
     const int npieces = m.pstart[I];
-    const double h = g.h;
-    // one thread per piece: its prior bin by binary search over pstart
+    const float h_f = (float)g.h;
+    for (int i = threadIdx.x; i < I; i += blockDim.x) m.pst[i] = make_int2(m.pstart[i], m.pstart[i + 1]);
+    // one thread per piece: its prior bin by binary search over pstart.  CDF
+    // values are subtracted in FP64 (they cancel); the quotients, which end
+    // up rounded to binary32 anyway, are taken in binary32, and the target
+    // bin's left edge is its binary32 threshold, so the table costs four FP64
+    // subtractions per piece and no FP64 division.
     for (int k = threadIdx.x; k < npieces; k += blockDim.x) {
         int lo = 0, hi = I - 1;
         while (lo < hi) {   // last i with pstart[i] <= k
@@ -192,43 +212,42 @@ __device__ inline void build_match_table(const GridDev& g, const double* __restr
         const int i = lo;
         const int r = m.jfirst[i] + (k - m.pstart[i]);
         const int j = m.nzlist[min(r, nnz - 1)];
-        const double rho_bar = __dsub_rn(m.Cp[i + 1], m.Cp[i]);
-        const double rho_j = __dsub_rn(m.Ct[j + 1], m.Ct[j]);
-        const double hr = __ddiv_rn(h, rho_j);
-        const double a = __dadd_rn(edge(g, j), __dmul_rn(__dsub_rn(m.Cp[i], m.Ct[j]), hr));
-        const double b = __dmul_rn(rho_bar, hr);
+        const double dij = __dsub_rn(m.Cp[i], m.Ct[j]);
+        const float rbf = (float)__dsub_rn(m.Cp[i + 1], m.Cp[i]);
+        const float rho_j = fmaxf((float)__dsub_rn(m.Ct[j + 1], m.Ct[j]), 1e-30f);
+        const float hr = __fdiv_rn(h_f, rho_j);
+        const float a = __fadd_rn(thr[j], __fmul_rn((float)dij, hr));
+        const float b = __fmul_rn(rbf, hr);
         float fe = 2.0f;
-        if (k + 1 < m.pstart[i + 1] && rho_bar > 0.0)
-            fe = (float)__ddiv_rn(__dsub_rn(m.Ct[j + 1], m.Cp[i]), rho_bar);
-        m.fend[k] = fe;
+        if (k + 1 < m.pstart[i + 1] && rbf > 0.0f)
+            fe = __fdiv_rn((float)__dsub_rn(m.Ct[j + 1], m.Cp[i]), rbf);
         // a target bin of negligible mass makes the slope huge; saturate so
         // that the clamp into the bin below never sees inf - inf
-        m.alpha[k] = (float)fmax(fmin(a, 1e30), -1e30);
-        m.beta[k] = (float)fmin(b, 1e30);
-        m.jp[k] = j;
+        m.piece[k] = make_float4(fe, fmaxf(fminf(a, 1e30f), -1e30f), fminf(b, 1e30f), __int_as_float(j));
     }
     __syncthreads();
 }
 
 // Map one binary32 particle through the table.
-__device__ __forceinline__ float match_one_f32(const MatchSmem& m, const float* __restrict__ thr,
-                                               int bins, float lo_f, float inv_h_f, float x)
+__device__ __forceinline__ float match_one_f32(const MatchSmem& m, const float* __restrict__ thr, const BinF32& bf,
+                                               float x)
 {
-    const int i = bin_of_f32(thr, bins, lo_f, inv_h_f, x);
-    const int k0 = m.pstart[i], k1 = m.pstart[i + 1];
-    if (k0 == k1) return x;   // identity on this bin
-    const bool below = !(x >= thr[0]);
-    const bool above = x >= thr[bins];
-    float f = (x - thr[i]) * inv_h_f;
+    const int i = bin_fast_f32(bf, thr, x);
+    const int2 kk = m.pst[i];
+    if (kk.x == kk.y) return x;   // identity on this bin
+    const bool below = !(x >= bf.thr0);
+    const bool above = x >= bf.thrI;
+    float f = (x - thr[i]) * bf.inv_h;
     f = fminf(fmaxf(f, 0.0f), 1.0f);
     if (below) f = 0.0f;
     if (above) f = 1.0f;
-    int k = k0;
-    while (k < k1 - 1 && f > m.fend[k]) ++k;
-    const int j = m.jp[k];
-    const float xn = fminf(fmaxf(fmaf(m.beta[k], f, m.alpha[k]), thr[j]), thr[j + 1]);
-    if (below) return x + (xn - thr[0]);
-    if (above) return x + (xn - thr[bins]);
+    int k = kk.x;
+    float4 pc = m.piece[k];
+    while (k < kk.y - 1 && f > pc.x) pc = m.piece[++k];
+    const int j = __float_as_int(pc.w);
+    const float xn = fminf(fmaxf(fmaf(pc.z, f, pc.y), thr[j]), thr[j + 1]);
+    if (below) return x + (xn - bf.thr0);
+    if (above) return x + (xn - bf.thrI);
     return xn;
 }
 
@@ -257,7 +276,7 @@ __device__ inline double match_one_f64(const MatchSmem& m, const GridDev& g, dou
 {
     const int I = g.bins;
     const int i = bin_of_f64(g, x);
-    if (m.Cp[i] == m.Ct[i] && m.Cp[i + 1] == m.Ct[i + 1]) return x;
+    if (deq(m.Cp[i], m.Ct[i]) && deq(m.Cp[i + 1], m.Ct[i + 1])) return x;
     if (m.nzpre[I] == 0) return x;
     const double ei = edge(g, i);
     double frac = __ddiv_rn(__dsub_rn(x, ei), g.h);

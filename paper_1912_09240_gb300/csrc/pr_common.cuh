@@ -210,6 +210,75 @@ __device__ __forceinline__ int bin_of_f32(const float* __restrict__ thr, int bin
     return i;
 }
 
+// Binary32 binning with a fast path that reads no threshold.  With
+// c = -(lo_f inv_h_f + 1/2) (binary32), g = fma(x, inv_h_f, c) differs from
+// the exact (x - lo) / h - 1/2 by less than
+// 2^-24 (max(|lo|, |hi|) / h + 3 |lo| / h + bins + 4) for x within a bin of
+// the grid (rounding of inv_h, of lo, of c and of the fma).  r = round(g)
+// comes from the low mantissa bits of g + 1.5 * 2^23 (exact for |g| < 2^22;
+// larger |g| gives an index outside [0, bins) or fails the test below).  When
+// |g - r| <= 1/2 - margin, margin at least twice that bound, (x - lo) / h lies
+// at least the bound away from every integer, so r = floor((x - lo) / h) is
+// the exact bin.  Elsewhere (near an edge, outside the grid, NaN) the
+// thresholds decide as in bin_of_f32; the result equals bin_of_f32's for
+// every x, and the common case needs one fma, three adds and no conversion.
+struct BinF32 {
+    float lo, inv_h, c, thr0, thrI, half_m;
+    int bins;
+};
+
+__device__ __forceinline__ BinF32 make_bin_f32(float thr0, float thrI, int bins, float lo_f, float inv_h_f)
+{
+    BinF32 b;
+    b.lo = lo_f;
+    b.inv_h = inv_h_f;
+    b.bins = bins;
+    b.thr0 = thr0;
+    b.thrI = thrI;
+    b.c = -(lo_f * inv_h_f + 0.5f);
+    const float span = fmaxf(fabsf(thr0), fabsf(thrI)) * inv_h_f;
+    const float m = 1.25e-7f * (span + 3.0f * fabsf(lo_f) * inv_h_f + (float)bins + 4.0f);
+    b.half_m = m < 0.25f ? 0.5f - m : -1.0f;   // -1: never take the fast path
+    return b;
+}
+
+// After thr[] is complete and visible to the calling thread.
+__device__ __forceinline__ BinF32 make_bin_f32(const float* thr, int bins, float lo_f, float inv_h_f)
+{
+    return make_bin_f32(thr[0], thr[bins], bins, lo_f, inv_h_f);
+}
+
+// The fast path alone: the bin, or -1 when the thresholds must decide.
+__device__ __forceinline__ int bin_try_f32(const BinF32& b, float x)
+{
+    const float g = fmaf(x, b.inv_h, b.c);
+    const float t = g + 12582912.0f;
+    const float r = t - 12582912.0f;
+    const float d = g - r;
+    const int i = __float_as_int(t) - 0x4B400000;
+    return ((unsigned)i < (unsigned)b.bins && fabsf(d) <= b.half_m) ? i : -1;
+}
+
+// Exact bin by comparison with the thresholds thr(i) (bin_of_f32's rule).
+template <typename Thr>
+__device__ __forceinline__ int bin_slow_f32(const BinF32& b, Thr thr, float x)
+{
+    if (!(x >= b.thr0)) return 0;
+    if (x >= b.thrI) return b.bins - 1;
+    int i = __float2int_rd((x - b.lo) * b.inv_h);
+    i = max(0, min(i, b.bins - 1));
+    while (i > 0 && x < thr(i)) --i;
+    while (i < b.bins - 1 && x >= thr(i + 1)) ++i;
+    return i;
+}
+
+__device__ __forceinline__ int bin_fast_f32(const BinF32& b, const float* __restrict__ thr, float x)
+{
+    const int i = bin_try_f32(b, x);
+    if (i >= 0) return i;
+    return bin_slow_f32(b, [thr](int k) { return thr[k]; }, x);
+}
+
 // thr[i] for i = 0..bins, cooperatively by the block.
 __device__ __forceinline__ void build_thresholds(const GridDev& g, float* thr)
 {

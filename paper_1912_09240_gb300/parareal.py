@@ -26,6 +26,12 @@ ordered by an event (fine(k+1, c) waits for the sweep of chunk c and for
 fine(k, c+1), which reads the slice fine(k+1, c) overwrites).  Results are
 bit for bit those of the sequential mode.  ``join()`` (called by every
 accessor) makes the caller's stream wait for the outstanding work.
+
+Graph mode (``graph=True``): iterations k >= 1 are replayed as one CUDA graph
+each (two graphs, one per binding of the double buffers), which removes the
+per-launch host cost that dominates small workloads.  In pipelined graph mode
+the chunks still overlap within an iteration; consecutive iterations are
+ordered by the graph launches themselves.
 """
 from __future__ import annotations
 
@@ -37,7 +43,8 @@ from . import _lib as L
 class PararealSolver:
     def __init__(self, model: L.Model, grid: L.Grid, n: int, K: int, steps: int, dt: float,
                  precision: int = L.PR_F32, rng: L.Rng = L.Rng(), iterator: int = L.PR_ITER_QUANTILE,
-                 qmode: int = L.PR_QMODE_TWO_SIDED, device: str = "cuda", stream=None, chunk: int = 0):
+                 qmode: int = L.PR_QMODE_TWO_SIDED, device: str = "cuda", stream=None, chunk: int = 0,
+                 graph: bool = False):
         self.model, self.grid, self.n, self.K, self.steps, self.dt = model, grid, n, K, steps, dt
         self.precision, self.rng, self.iterator, self.qmode = precision, rng, iterator, qmode
         self.device = torch.device(device)
@@ -68,12 +75,19 @@ class PararealSolver:
         # when a list, (start, end) CUDA events around the main fine launch of
         # every sequential iteration are appended to it
         self.fine_events = None
+        # kernels of libpr.so enqueued by iterate() so far (the fine call with
+        # both fused restrictions is 3: the fine kernel and two counts->CDF)
+        self.launches = 0
         if self.chunk:
             self._sf = [torch.cuda.Stream(self.device), torch.cuda.Stream(self.device)]
             self._su = torch.cuda.Stream(self.device, priority=-1)
             self._ev_fine = [None] * nch     # fine(k, c) of the latest enqueued iteration
             self._ev_upd = [None] * nch      # sweep(k, c) of the latest enqueued iteration
         self._pending = False
+        self.graph = bool(graph)
+        self._swaps = 0                  # iterations since construction (buffer binding parity)
+        self._graphs = [None, None]
+        self._graph_launches = [0, 0]
 
     # -- plumbing ----------------------------------------------------------------
     def _s(self):
@@ -135,6 +149,7 @@ class PararealSolver:
                                 self.xb[0], self.yb[0], n, 0, 1, self.steps, self.dt, self.grid,
                                 None, None, self.counts_s[0], self.start[0], self.counts_e[0],
                                 self.f_star[0], stream=stream)
+            self.launches += 3
             a = 1
         if b <= a:
             return
@@ -151,54 +166,98 @@ class PararealSolver:
                             self.xb[a:b], self.yb[a:b], n, a, b - a, self.steps, self.dt, self.grid,
                             prior, self._rho[a:b], self.counts_s[a:b], self.start[a:b], self.counts_e[a:b],
                             self.f_star[a:b], stream=stream)
+        self.launches += 3
         if ev is not None:
             ev[1].record(stream)
             self.fine_events.append(ev)
 
     def iterate(self):
-        K = self.K
-        first = self.k == 0
-        if not self.chunk:
-            s = self._s()
-            self._fine(0, K, first, s)
-            L.pr_coarse_fp(self.coarse, self.start, self.c_star, K, stream=s)
-            L.pr_parareal_update(self.coarse, self.iterator, self.qmode, K, self.cdf0, self.f_star, self.c_star,
-                                 self._rho_next, self._status[0], stream=s)
+        if self.graph and self.k >= 1:
+            self._replay()
         else:
-            C = self.chunk
-            nch = len(self._ev_upd)
-            fork = torch.cuda.Event()
-            fork.record(self._s())
-            for st in (*self._sf, self._su):
-                st.wait_event(fork)
-            new_fine, new_upd = [None] * nch, [None] * nch
-            for c in range(nch):
-                a, b = c * C, min(K, (c + 1) * C)
-                sf = self._sf[c % 2]
-                for ev in (self._ev_upd[c], self._ev_fine[c + 1] if c + 1 < nch else None):
-                    if ev is not None:
-                        sf.wait_event(ev)
-                self._fine(a, b, first, sf)
-                ef = torch.cuda.Event()
-                ef.record(sf)
-                new_fine[c] = ef
-                su = self._su
-                su.wait_event(ef)
-                L.pr_coarse_fp(self.coarse, self.start[a:b], self.c_star[a:b], b - a, stream=su)
-                state = self.cdf0 if a == 0 else self._rho_next[a]
-                L.pr_parareal_update(self.coarse, self.iterator, self.qmode, b - a, state, self.f_star[a:b],
-                                     self.c_star[a:b], self._rho_next[a:b + 1], self._status[c], stream=su)
-                eu = torch.cuda.Event()
-                eu.record(su)
-                new_upd[c] = eu
-            self._ev_fine, self._ev_upd = new_fine, new_upd
-            self._pending = True
+            self._enqueue(self._s(), self.k == 0, in_graph=False)
+        self._advance()
+
+    def _advance(self):
         # the fine results become the priors of the next matching
         self.xa, self.xb = self.xb, self.xa
         self.ya, self.yb = self.yb, self.ya
         self.f_star, self.f_star_prev = self.f_star_prev, self.f_star
         self._rho, self._rho_next = self._rho_next, self._rho
+        self._swaps += 1
         self.k += 1
+
+    def _enqueue(self, s, first: bool, in_graph: bool):
+        """Enqueue one iteration behind the work already on stream `s`."""
+        K = self.K
+        if not self.chunk:
+            self._fine(0, K, first, s)
+            L.pr_coarse_fp(self.coarse, self.start, self.c_star, K, stream=s)
+            L.pr_parareal_update(self.coarse, self.iterator, self.qmode, K, self.cdf0, self.f_star, self.c_star,
+                                 self._rho_next, self._status[0], stream=s)
+            self.launches += 2
+            return
+        C = self.chunk
+        nch = len(self._ev_upd)
+        fork = torch.cuda.Event()
+        fork.record(s)
+        for st in (*self._sf, self._su):
+            st.wait_event(fork)
+        new_fine, new_upd = [None] * nch, [None] * nch
+        for c in range(nch):
+            a, b = c * C, min(K, (c + 1) * C)
+            sf = self._sf[c % 2]
+            if not in_graph:   # a graph launch starts after the previous iteration has ended
+                for ev in (self._ev_upd[c], self._ev_fine[c + 1] if c + 1 < nch else None):
+                    if ev is not None:
+                        sf.wait_event(ev)
+            self._fine(a, b, first, sf)
+            ef = torch.cuda.Event()
+            ef.record(sf)
+            new_fine[c] = ef
+            su = self._su
+            su.wait_event(ef)
+            L.pr_coarse_fp(self.coarse, self.start[a:b], self.c_star[a:b], b - a, stream=su)
+            state = self.cdf0 if a == 0 else self._rho_next[a]
+            L.pr_parareal_update(self.coarse, self.iterator, self.qmode, b - a, state, self.f_star[a:b],
+                                 self.c_star[a:b], self._rho_next[a:b + 1], self._status[c], stream=su)
+            self.launches += 2
+            eu = torch.cuda.Event()
+            eu.record(su)
+            new_upd[c] = eu
+        if in_graph:       # every forked stream rejoins the capturing stream
+            for ev in new_fine + new_upd:
+                s.wait_event(ev)
+            self._ev_fine, self._ev_upd = [None] * nch, [None] * nch
+        else:
+            self._ev_fine, self._ev_upd = new_fine, new_upd
+            self._pending = True
+
+    def _replay(self):
+        """Iterations k >= 1 as one CUDA graph each.  The buffers alternate
+        between two bindings, so there is one graph per binding, captured on
+        first use (capture enqueues nothing; the replay does the work)."""
+        p = self._swaps % 2
+        s = self._s()
+        if self._graphs[p] is None:
+            self.join()
+            cs = torch.cuda.Stream(self.device)
+            cs.wait_stream(s)
+            g = torch.cuda.CUDAGraph()
+            n0, events = self.launches, self.fine_events
+            self.fine_events = None      # no timing events inside a graph
+            try:
+                with torch.cuda.graph(g, stream=cs):
+                    self._enqueue(cs, False, in_graph=True)
+            finally:
+                self.fine_events = events
+            self._graph_launches[p] = self.launches - n0
+            self.launches = n0
+            s.wait_stream(cs)
+            self._graphs[p] = g
+        with torch.cuda.stream(s):
+            self._graphs[p].replay()
+        self.launches += self._graph_launches[p]
 
     # -- the serial fine solution with the same random numbers -----------------
     def serial_reference(self):

@@ -82,8 +82,13 @@ def test_seeded_sum_equals_contracted_per_particle(L):
     tot2 = torch.zeros(3, dtype=torch.float64, device="cuda")
     L.pr_fine_adjoint(gm, L.Rng(0), x0, y0, n, 0, slices, steps, dt, 256, None, None, seeds, None, tot2, None, None, ws)
     torch.cuda.synchronize()
-    ref = (seeds[:, None] * per).sum(0).cpu().numpy()
-    np.testing.assert_allclose(tot.cpu().numpy(), ref, rtol=1e-5)
+    terms = (seeds[:, None] * per).cpu().numpy()
+    ref = terms.sum(0)
+    # both sides run the binary32 recursion over 200 steps (relative error per
+    # particle up to ~200 x 2^-24 = 1.2e-5, differently rounded with the seed
+    # folded in); the sum over particles cancels, so the bound scales with
+    # the sum of magnitudes
+    assert np.all(np.abs(tot.cpu().numpy() - ref) <= 2e-5 * np.abs(terms).sum(0))
     np.testing.assert_array_equal(tot.cpu().numpy(), tot2.cpu().numpy())   # deterministic reduction
 
 

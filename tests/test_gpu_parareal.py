@@ -169,3 +169,97 @@ def test_pipelined_driver_equals_sequential(L, chunk):
                 np.testing.assert_array_equal(s.state()[0].cpu().numpy(), xa_ref[k])
     assert int(s.status.item()) == 0
     s.close()
+
+
+@pytest.mark.parametrize("chunk", [0, 2])
+def test_exactness_theorem_fast16_on_gpu(L, chunk):
+    """The 16-dimensional fast space (coupling lambda mean(y)): iterate k equals
+    the serial fine solution on slices n <= k, bit for bit, with the sequential
+    and the pipelined driver."""
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    w = workloads.LARGE_FAST.scaled(N=5003, K=5, T=5e-3, bins=1024)
+    model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    s = PararealSolver(model, L.Grid(w.bins, w.lo, w.hi), w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                       rng=L.Rng(w.seed, 3), chunk=chunk)
+    x0, y0 = workloads.initial_ensemble(w)
+    s.set_initial(torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                  torch.tensor(y0, dtype=torch.float32, device="cuda"))
+    xs, ys, rs = s.serial_reference()
+    rs_ = rs.cpu().numpy()
+    for k in range(1, w.K + 1):
+        s.iterate()
+        rho = s.rho.cpu().numpy()
+        for n in range(k + 1):
+            np.testing.assert_array_equal(rho[n], rs_[n])
+        xa, ya, _ = s.state()
+        for n in range(1, k + 1):
+            np.testing.assert_array_equal(xa[n - 1].cpu().numpy(), xs[n].cpu().numpy())
+            np.testing.assert_array_equal(ya[n - 1].cpu().numpy(), ys[n].cpu().numpy())
+    assert int(s.status.item()) == 0
+    s.close()
+
+
+def test_fast16_full_size_sampled_parity(L, orc):
+    """4e6 particles x 100 slices x 1000 steps with a 16-dimensional fast
+    space, 1024 bins, binary32, pipelined as bench.py runs it: the first
+    parareal iteration (every slice matched from X_0 to the coarse sweep);
+    sampled particles of several slices, all 17 coordinates, against the
+    oracle run on those particles only (their own Philox keys)."""
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    w = workloads.LARGE_FAST
+    model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    grid = L.Grid(w.bins, w.lo, w.hi)
+    s = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32, rng=L.Rng(w.seed, 0),
+                       chunk=5)
+    x0 = workloads.initial_slow(w)
+    x0t = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    s.set_initial(x0t, x0t.expand(w.fast_dim, w.N).contiguous())
+    rho0 = s.rho.cpu().numpy().copy()
+    s.iterate()
+    xa, ya, _ = s.state()
+    rng = np.random.default_rng(5)
+    ids = np.sort(rng.choice(w.N, 128, replace=False)).astype(np.uint32)
+    ids[0], ids[-1] = 0, w.N - 1
+    om, og = _oracle_objs(orc, w)
+    x0f = x0.astype(np.float32).astype(np.float64)
+    _, cdf0 = orc.restrict(x0f[None], og)
+    np.testing.assert_array_equal(rho0[0], cdf0[0])
+    for n in (0, 1, 42, 99):
+        start = x0f[ids] if n == 0 else orc.match(x0f[ids][None], og, cdf0, rho0[n][None])[0]
+        ystart = np.repeat(x0f[ids][None], w.fast_dim, axis=0)
+        ox, oy = orc.fine_propagate(om, w.seed, start[None], ystart[None], n, w.steps, w.step_dt, ids=ids)
+        gx = xa[n][torch.from_numpy(ids.astype(np.int64)).cuda()].double().cpu().numpy()
+        gy = ya[n][:, torch.from_numpy(ids.astype(np.int64)).cuda()].double().cpu().numpy()
+        assert np.all(np.abs(gx - ox[0]) <= 2e-3 * np.maximum(np.abs(ox[0]), 1.0)), n
+        assert np.all(np.abs(gy - oy[0]) <= 2e-3 * np.maximum(np.abs(oy[0]), 1.0)), n
+    assert int(s.status.item()) == 0
+    s.close()
+
+
+@pytest.mark.parametrize("chunk", [0, 3])
+def test_graph_mode_equals_eager(L, chunk):
+    """Iterations replayed as CUDA graphs give the eager sequential driver's
+    results bit for bit, for both bindings of the double buffers (a second run
+    starts after an odd number of iterations)."""
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    w = workloads.DOUBLE_WELL.scaled(N=3001, K=10, T=0.1, dt=1e-3, bins=128)
+    ref, x0, y0 = _solver(L, w, L.PR_F32)
+    rho_ref, xa_ref = [], []
+    for _ in range(5):
+        ref.iterate()
+        rho_ref.append(ref.rho.cpu().numpy().copy())
+        xa_ref.append(ref.xa.cpu().numpy().copy())
+    ref.close()
+    model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    s = PararealSolver(model, L.Grid(w.bins, w.lo, w.hi), w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                       rng=L.Rng(w.seed, 0), chunk=chunk, graph=True)
+    for iters in (3, 5):
+        s.set_initial(torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                      torch.tensor(y0, dtype=torch.float32, device="cuda"))
+        for k in range(iters):
+            s.iterate()
+            np.testing.assert_array_equal(s.rho.cpu().numpy(), rho_ref[k])
+            np.testing.assert_array_equal(s.state()[0].cpu().numpy(), xa_ref[k])
+    assert all(g is not None for g in s._graphs)
+    assert int(s.status.item()) == 0
+    s.close()

@@ -218,6 +218,66 @@ def test_match_f32_close(L, orc, bins, lo, hi):
     assert orc.w1(og, c_got[0], c_ref[0]) < 1e-5
 
 
+@pytest.mark.parametrize("off_in,off_out", [(0, 0), (1, 1), (3, 0), (0, 2), (2, 2)])
+def test_match_f32_alignment_paths(L, orc, off_in, off_out):
+    """Slices of a ragged length at every offset from a 16-byte boundary, in
+    place and out of place: the vector and scalar paths of the standalone
+    binary32 matching give the same bits, and agree with the oracle."""
+    og = orc.Grid(512, -3.0, 3.0)
+    rng = np.random.default_rng(11)
+    n, S = 40_001, 3
+    xs, cps, cts = [], [], []
+    for _ in range(S):
+        x, _, ct = _cdf_pair(orc, og, rng, n)
+        x32 = x.astype(np.float32)
+        _, cp = orc.restrict(x32.astype(np.float64)[None], og)
+        xs.append(x32)
+        cps.append(cp[0])
+        cts.append(ct)
+    x32, cp, ct = np.stack(xs), np.stack(cps), np.stack(cts)
+    buf_in = torch.zeros(S * n + 8, dtype=torch.float32, device=DEV)
+    gin = buf_in[off_in:off_in + S * n]
+    gin.copy_(_t(x32.reshape(-1)))
+    if off_in == off_out:     # in place
+        gout = gin
+        src = gin.clone()
+        L.pr_match(L.PR_F32, gin, gout, n, S, L.Grid(512, -3.0, 3.0), _t(cp), _t(ct))
+    else:
+        src = gin
+        buf_out = torch.zeros(S * n + 8, dtype=torch.float32, device=DEV)
+        gout = buf_out[off_out:off_out + S * n]
+        L.pr_match(L.PR_F32, gin, gout, n, S, L.Grid(512, -3.0, 3.0), _t(cp), _t(ct))
+    # per-slice launches at a 16-byte-aligned copy are the reference bits
+    ref_bits = []
+    for s_ in range(S):
+        a = src[s_ * n:(s_ + 1) * n].clone()
+        o = torch.empty_like(a)
+        L.pr_match(L.PR_F32, a, o, n, 1, L.Grid(512, -3.0, 3.0), _t(cp[s_:s_ + 1]), _t(ct[s_:s_ + 1]))
+        ref_bits.append(o)
+    torch.cuda.synchronize()
+    got = gout.reshape(S, n).cpu().numpy()
+    np.testing.assert_array_equal(got, torch.stack(ref_bits).cpu().numpy())
+    ref = orc.match(x32.astype(np.float64), og, cp, ct)
+    assert np.all(np.abs(got - ref) <= 2e-3 * np.maximum(np.abs(ref), 1.0))
+
+
+@pytest.mark.parametrize("off", [1, 2, 3])
+def test_restrict_f32_offsets(L, orc, off):
+    """Binary32 restriction of ragged slices starting off a 16-byte boundary."""
+    og = orc.Grid(512, -3.0, 3.0)
+    rng = np.random.default_rng(12)
+    n, S = 70_003, 5
+    x = _awkward_x(S, n, og, rng).astype(np.float32)
+    buf = torch.zeros(S * n + 8, dtype=torch.float32, device=DEV)
+    gx = buf[off:off + S * n]
+    gx.copy_(_t(x.reshape(-1)))
+    counts = torch.empty(S, 512, dtype=torch.int32, device=DEV)
+    L.pr_restrict(0, gx, n, S, L.Grid(512, -3.0, 3.0), counts, None)
+    torch.cuda.synchronize()
+    oc, _ = orc.restrict(x.astype(np.float64), og)
+    np.testing.assert_array_equal(counts.cpu().numpy().view(np.uint32), oc)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_match_strong_projection_exact(L, orc, prec):
     og = orc.Grid(128, -3.0, 3.0)

@@ -116,6 +116,13 @@ def batched_problems(n_problems: int = 64, seed: int = 0, K: int = 32, T: float 
     return BatchedWorkload(problems=probs)
 
 
+def initial_slow(w: Workload, seed: int | None = None) -> np.ndarray:
+    """X0 [N] alone (the first draws of the stream of `initial_ensemble`);
+    for workloads with Y0 = X0 the fast start is its broadcast."""
+    rng = np.random.default_rng(np.random.PCG64(w.seed if seed is None else seed))
+    return rng.normal(w.x0_mean, w.x0_std, w.N)
+
+
 def initial_ensemble(w: Workload, seed: int | None = None):
     """X0 [N] and Y0 [d][N] in float64, from a PCG64 stream keyed by `seed`."""
     rng = np.random.default_rng(np.random.PCG64(w.seed if seed is None else seed))
