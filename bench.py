@@ -410,6 +410,8 @@ def run_ours(args):
         b.build()
     if dist:
         dist.barrier()
+    if args.update_cluster:
+        L.pr_set_update_cluster(args.update_cluster)
     w = WORKLOAD
     model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
     grid = L.Grid(w.bins, w.lo, w.hi)
@@ -646,7 +648,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "N": w.N, "K": w.K, "steps_per_slice": w.steps, "dt": w.step_dt,
                    "bins": w.bins, "iterator": "quantile (two-sided)", "parallelism": f"replicas x{ws}",
-                   "pipeline_chunk": args.chunk,
+                   "pipeline_chunk": args.chunk, "update_cluster": args.update_cluster or 8,
                    "l2": "inputs larger than L2: 840 MB of ensemble state per step"},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -678,6 +680,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU sample")
     ap.add_argument("--no-conv", action="store_true", help="skip the convergence study")
+    ap.add_argument("--update-cluster", type=int, default=None, help="CTAs of the serial-sweep cluster")
     ap.add_argument("--chunk", type=int, default=5, help="slices per pipelined chunk (0: sequential)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-serving leg")
     ap.add_argument("--no-unfused", action="store_true", help="skip standalone restriction/matching/coarse timing")

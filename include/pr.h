@@ -216,7 +216,9 @@ pr_status pr_coarse_fp(void* handle, const double* cdf_in, double* cdf_out, int3
                        void* stream);
 
 /*
- * Serial update of Section 3.2.3 (Eq. mm_sequential), one CTA:
+ * Serial update of Section 3.2.3 (Eq. mm_sequential), on one thread-block
+ * cluster (8 CTAs by default, one CTA below 64 bins) that splits the FP64
+ * work of each slice; the result does not depend on the cluster size:
  *   rho^0 = cdf0,
  *   rho^{n+1} = J(C_dT(rho^n), rho_f*[n], rho_c*[n]),  n = 0 .. n_slices-1,
  * with J the chosen iterator (Section 4; PR_ITER_NONE: rho^{n+1} = C_dT(rho^n)).
@@ -234,6 +236,10 @@ pr_status pr_parareal_update(void* coarse, pr_iterator iterator, pr_quantile_mod
                              int32_t n_slices, const double* cdf0, const double* cdf_f_star,
                              const double* cdf_c_star, double* cdf_next, int32_t* status,
                              void* stream);
+
+/* CTAs of the cluster running pr_parareal_update: 1, 2, 4 or 8 (default);
+ * other values select 8.  Process-wide; affects later calls only. */
+void pr_set_update_cluster(int32_t ctas);
 
 /*
  * One iterator J(a, b, c) on n_vec independent triples (Section 4), no coarse

@@ -22,7 +22,7 @@ PR_QMODE_TWO_SIDED, PR_QMODE_MIDPOINT = 0, 1
 
 EXPORTED = (
     "pr_status_string", "pr_version", "pr_rng_words", "pr_fine_propagate", "pr_set_particles_per_thread",
-    "pr_set_tiles_per_cta", "pr_restrict", "pr_counts_to_cdf", "pr_match", "pr_coarse_create", "pr_coarse_destroy",
+    "pr_set_tiles_per_cta", "pr_set_update_cluster", "pr_restrict", "pr_counts_to_cdf", "pr_match", "pr_coarse_create", "pr_coarse_destroy",
     "pr_coarse_matrix", "pr_coarse_fp", "pr_parareal_update", "pr_iterate", "pr_w1",
     "pr_fine_adjoint_workspace", "pr_fine_adjoint", "pr_order_statistics_workspace", "pr_order_statistics",
     "pr_fine_adjoint_noalloc_capacity", "pr_fine_adjoint_noalloc",
@@ -127,6 +127,8 @@ def lib() -> ctypes.CDLL:
     L.pr_set_particles_per_thread.restype = None
     L.pr_set_tiles_per_cta.argtypes = [i32]
     L.pr_set_tiles_per_cta.restype = None
+    L.pr_set_update_cluster.argtypes = [i32]
+    L.pr_set_update_cluster.restype = None
     L.pr_restrict.argtypes = [i32, vp, i64, i32, P(_Grid), vp, vp, vp]
     L.pr_counts_to_cdf.argtypes = [vp, i64, i32, i32, vp, vp]
     L.pr_match.argtypes = [i32, vp, vp, i64, i32, P(_Grid), vp, vp, vp]
@@ -162,7 +164,7 @@ def lib() -> ctypes.CDLL:
     L.pr_batch_tune.argtypes = [vp, i32, P(d), vp]
     for name in EXPORTED:
         if name not in ("pr_status_string", "pr_version", "pr_set_particles_per_thread",
-                        "pr_set_tiles_per_cta", "pr_fine_adjoint_workspace",
+                        "pr_set_tiles_per_cta", "pr_set_update_cluster", "pr_fine_adjoint_workspace",
                         "pr_order_statistics_workspace", "pr_fine_adjoint_noalloc_capacity",
                         "pr_batch_particle_steps"):
             getattr(L, name).restype = i32
@@ -221,6 +223,10 @@ def pr_set_particles_per_thread(ppt: int):
 
 def pr_set_tiles_per_cta(tiles: int):
     lib().pr_set_tiles_per_cta(tiles)
+
+
+def pr_set_update_cluster(ctas: int):
+    lib().pr_set_update_cluster(ctas)
 
 
 def pr_restrict(precision: int, x, n: int, n_slices: int, grid: Grid, counts, cdf=None, stream=None):

@@ -167,14 +167,16 @@ coarse_fp_kernel(const double* __restrict__ P, int I, const double* __restrict__
     for (int i = threadIdx.x; i <= I; i += blockDim.x) dst[i] = out[i];
 }
 
-// The serial sweep of Section 3.2.3 on one CTA.
+// The serial sweep of Section 3.2.3 on one CTA (CL = 1) or on a cluster of
+// CL CTAs (launched with that cluster size).
+template <int CL>
 __global__ void __launch_bounds__(kCoarseThreads)
 parareal_update_kernel(const double* __restrict__ P, GridDev g, int iterator, int qmode, int K,
                        const double* __restrict__ cdf0, const double* __restrict__ fstar,
                        const double* __restrict__ cstar, double* __restrict__ next, int32_t* status)
 {
     extern __shared__ __align__(16) unsigned char usm[];
-    serial_sweep(usm, P, g, iterator, qmode, K, cdf0, fstar, cstar, next, status);
+    serial_sweep<CL>(usm, P, g, iterator, qmode, K, cdf0, fstar, cstar, next, status);
 }
 
 __global__ void __launch_bounds__(kCoarseThreads)
@@ -218,6 +220,9 @@ w1_kernel(GridDev g, const double* __restrict__ c1, const double* __restrict__ c
     const double s = block_sum_f64(acc, wsum);
     if (threadIdx.x == 0) w1[blockIdx.x] = s;
 }
+
+// CTAs of the cluster that runs the serial sweep (1, 2, 4 or 8; portable sizes).
+static int g_update_cluster = 8;
 
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t bytes)
@@ -337,11 +342,47 @@ extern "C" pr_status pr_parareal_update(void* coarse, pr_iterator iterator, pr_q
     auto* h = static_cast<CoarseHandle*>(coarse);
     if (h->g.bins > kUpdateMaxBins) return PR_ERR_UNSUPPORTED;
     const size_t smem = update_smem(h->g.bins);
-    PR_TRY_CUDA(allow_smem(parareal_update_kernel, smem));
-    parareal_update_kernel<<<1, kCoarseThreads, smem, static_cast<cudaStream_t>(stream)>>>(
-        h->P, h->g, (int)iterator, (int)qmode, n_slices, cdf0, cdf_f_star, cdf_c_star, cdf_next, status);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int cl = h->g.bins >= 64 ? g_update_cluster : 1;
+    if (cl == 1) {
+        PR_TRY_CUDA(allow_smem(parareal_update_kernel<1>, smem));
+        parareal_update_kernel<1><<<1, kCoarseThreads, smem, st>>>(h->P, h->g, (int)iterator, (int)qmode, n_slices,
+                                                                  cdf0, cdf_f_star, cdf_c_star, cdf_next, status);
+        PR_CHECK_LAUNCH();
+        return PR_OK;
+    }
+    auto launch = [&](auto kernel) -> cudaError_t {
+        cudaError_t e = allow_smem(kernel, smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)cl);
+        cfg.blockDim = dim3(kCoarseThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kernel, (const double*)h->P, h->g, (int)iterator, (int)qmode, (int)n_slices,
+                                  cdf0, cdf_f_star, cdf_c_star, cdf_next, status);
+    };
+    cudaError_t e;
+    switch (cl) {
+    case 2: e = launch(parareal_update_kernel<2>); break;
+    case 4: e = launch(parareal_update_kernel<4>); break;
+    default: e = launch(parareal_update_kernel<8>); break;
+    }
+    if (e != cudaSuccess) return PR_ERR_CUDA;
     PR_CHECK_LAUNCH();
     return PR_OK;
+}
+
+extern "C" void pr_set_update_cluster(int32_t ctas)
+{
+    g_update_cluster = (ctas == 1 || ctas == 2 || ctas == 4) ? ctas : 8;
 }
 
 extern "C" pr_status pr_iterate(pr_iterator iterator, pr_quantile_mode qmode, const pr_grid* grid, int32_t n_vec,

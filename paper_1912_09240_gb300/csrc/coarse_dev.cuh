@@ -4,12 +4,55 @@
 // shared by the single-problem and the batched kernels.
 #pragma once
 
+#include <cooperative_groups.h>
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 
 #include "pr_common.cuh"
 
 namespace pr {
+
+namespace cg = cooperative_groups;
+
+// Work split over the CL CTAs of a thread-block cluster (CL = 1: one CTA).
+// Each CTA computes its share [lo(n), hi(n)) of an index range into an
+// array in its shared memory; share() copies that part into the same array
+// of every other CTA of the cluster (the arrays sit at the same offsets in
+// every CTA, distributed shared memory) and synchronises the cluster, so
+// that every CTA then holds the whole array.  Each element is computed by
+// one CTA with the arithmetic of the single-CTA code, so the results do not
+// depend on CL.
+template <int CL>
+struct Dist {
+    int rank;
+    __device__ static Dist make()
+    {
+        Dist d;
+        d.rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
+        return d;
+    }
+    __device__ int lo(int n) const { return (int)(((long long)n * rank) / CL); }
+    __device__ int hi(int n) const { return (int)(((long long)n * (rank + 1)) / CL); }
+    template <typename T>
+    __device__ void share(T* arr, int b, int e) const
+    {
+        __syncthreads();
+        if constexpr (CL > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            for (int q = 1; q < CL; ++q) {
+                T* dst = cl.map_shared_rank(arr, (unsigned)((rank + q) % CL));
+                for (int i = b + (int)threadIdx.x; i < e; i += (int)blockDim.x) dst[i] = arr[i];
+            }
+            cl.sync();
+        }
+    }
+    __device__ void sync() const
+    {
+        if constexpr (CL > 1) cg::this_cluster().sync();
+        else __syncthreads();
+    }
+};
 
 constexpr int kCoarseThreads = 512;   // every coarse apply uses this block size
 constexpr int kUpdateMaxBins = 1024;
@@ -115,13 +158,16 @@ __device__ inline double block_sum_f64(double v, double* wsum)
 // All in shared memory; every thread of a kCoarseThreads block calls it.
 // ---------------------------------------------------------------------------
 
+template <int CL = 1>
 __device__ inline void coarse_apply_block(const double* __restrict__ P, int I, const double* cdf_in,
-                                   double* out, double* mass, double* mp, double* wsum)
+                                          double* out, double* mass, double* mp, double* wsum,
+                                          const Dist<CL> d = Dist<CL>{0})
 {
     for (int c = threadIdx.x; c < I; c += blockDim.x) mass[c] = __dsub_rn(cdf_in[c + 1], cdf_in[c]);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r = warp; r < I; r += nw) {
+    const int r0 = d.lo(I), r1 = d.hi(I);
+    for (int r = r0 + warp; r < r1; r += nw) {
         const double* row = P + (size_t)r * I;
         double acc = 0.0;
         for (int c = lane; c < I; c += 32) acc = fma(row[c], mass[c], acc);
@@ -129,10 +175,11 @@ __device__ inline void coarse_apply_block(const double* __restrict__ P, int I, c
         for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
         if (lane == 0) mp[r] = acc > kTailMass ? acc : 0.0;
     }
-    __syncthreads();
+    d.share(mp, r0, r1);
     block_scan_f64(mp, mp, I, wsum);
     const double total = mp[I - 1];
-    for (int r = threadIdx.x; r < I - 1; r += blockDim.x) {
+    const int q0 = d.lo(I - 1), q1 = d.hi(I - 1);
+    for (int r = q0 + threadIdx.x; r < q1; r += blockDim.x) {
         double v = total > 0.0 ? __ddiv_rn(mp[r], total) : 0.0;
         out[r + 1] = v < 1.0 ? v : 1.0;
     }
@@ -140,19 +187,19 @@ __device__ inline void coarse_apply_block(const double* __restrict__ P, int I, c
         out[0] = 0.0;
         out[I] = 1.0;
     }
-    __syncthreads();
+    d.share(out, 1 + q0, 1 + q1);
 }
 
 // ---------------------------------------------------------------------------
 // Quantile iterator J_q (Section 4.4) on CDFs in shared memory.
 // ---------------------------------------------------------------------------
 
-// Ordered 64-bit key of a double (zeros canonicalised): signed comparison of
-// keys is numeric comparison.
+// Ordered 64-bit key of a non-NaN double: signed comparison of keys is
+// numeric comparison, and -0 and +0 both map to 0.
 __device__ __forceinline__ long long okey(double v)
 {
     const long long b = __double_as_longlong(v);
-    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll) + 1;
 }
 
 __device__ __forceinline__ int count_lt(const double* F, int n, double v)   // #F < v
@@ -206,8 +253,8 @@ __device__ __forceinline__ void quantiles(const GridDev& g, const double* F, dou
 
 struct JqSmem {
     double* levels;   // [3(I+1)]
-    double* kq;       // [6(I+1)]  (merged values first, then knots)
-    double* bsum;     // [6(I+1)]  sums of pooled blocks
+    double* kq;       // [6(I+1)]  knots
+    double* bsum;     // [6(I+1)]  merged levels, then sums of pooled blocks
     int* ibuf;        // [6(I+1)]  (distinct flags, then the descent list)
     int* bpos;        // [6(I+1)]  pooled blocks: start | end << 16
     int* flag;        // [0]: level count, [1]: input not a CDF, [2]: knots need repair
@@ -235,25 +282,30 @@ __device__ inline JqSmem carve_jq(unsigned char* base, int bins)
 }
 
 // out = J_q(A, B, C).  A, B, C, out: [I+1] in shared memory (out distinct).
-// Returns through flag[1] a non-zero value if an input was not a CDF.
+// Returns through flag[1] a non-zero value if an input was not a CDF.  With a
+// cluster (CL > 1) the quantiles at the levels and the read-back at the edges
+// are split over its CTAs; the rest runs in every CTA on identical data.
+template <int CL = 1>
 __device__ inline void quantile_iterate_block(const GridDev& g, int qmode, const double* A, const double* B,
-                                       const double* C, double* out, JqSmem& s)
+                                              const double* C, double* out, JqSmem& s,
+                                              const Dist<CL> d = Dist<CL>{0})
 {
     const int I = g.bins;
     const int n1 = I + 1;
     const int M = 3 * n1;
     if (threadIdx.x == 0) s.flag[2] = 0;
-    // validity: finite, non-decreasing, in [0, 1]
+    // validity: in [0, 1] (NaN fails) and non-decreasing, by ordered keys
+    const long long k0 = okey(0.0), k1 = okey(1.0);
     for (int i = threadIdx.x; i < n1; i += blockDim.x) {
         const double* Fs[3] = {A, B, C};
         for (int f = 0; f < 3; ++f) {
-            const double v = Fs[f][i];
-            bool bad = !(v >= 0.0 && v <= 1.0);
-            if (i > 0 && !(Fs[f][i - 1] <= v)) bad = true;
+            const long long kv = okey(Fs[f][i]);
+            bool bad = kv < k0 || kv > k1;
+            if (i > 0 && okey(Fs[f][i - 1]) > kv) bad = true;
             if (bad) s.flag[1] = 1;
         }
     }
-    // 1. sorted union of the 3(I+1) levels (stable merge by rank)
+    // 1. sorted union of the 3(I+1) levels (stable merge by rank) into bsum
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
         const int f = k / n1, i = k - f * n1;
         double v;
@@ -261,11 +313,11 @@ __device__ inline void quantile_iterate_block(const GridDev& g, int qmode, const
         if (f == 0) { v = A[i]; r = i + count_lt(B, n1, v) + count_lt(C, n1, v); }
         else if (f == 1) { v = B[i]; r = i + count_le(A, n1, v) + count_lt(C, n1, v); }
         else { v = C[i]; r = i + count_le(A, n1, v) + count_le(B, n1, v); }
-        s.kq[r] = v;
+        s.bsum[r] = v;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < M; k += blockDim.x)
-        s.ibuf[k] = (k == 0 || s.kq[k] != s.kq[k - 1]) ? 1 : 0;
+        s.ibuf[k] = (k == 0 || !deq(s.bsum[k], s.bsum[k - 1])) ? 1 : 0;
     __syncthreads();
     // exclusive scan of the distinct flags -> positions (ints, deterministic)
     {
@@ -288,7 +340,7 @@ __device__ inline void quantile_iterate_block(const GridDev& g, int qmode, const
         for (int w = 0; w < warp; ++w) off += wtot[w];
         int run = off + incl - loc;
         for (int i = b; i < e; ++i) {
-            if (s.ibuf[i]) s.levels[run] = s.kq[i];
+            if (s.ibuf[i]) s.levels[run] = s.bsum[i];
             run += s.ibuf[i];
         }
         if (threadIdx.x == T - 1) s.flag[0] = run;   // number of levels L
@@ -299,7 +351,8 @@ __device__ inline void quantile_iterate_block(const GridDev& g, int qmode, const
     // 2-3. quantiles of A, B, C at every level and the combined knots
     const bool two = qmode == PR_QMODE_TWO_SIDED;
     const int nk = two ? 2 * L - 2 : L;
-    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    const int l0 = d.lo(L), l1 = d.hi(L);
+    for (int l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
         const double p = s.levels[l];
         const bool first = l == 0, last = l == L - 1;
         double am, ap, bm, bp, cm, cp;
@@ -321,104 +374,139 @@ __device__ inline void quantile_iterate_block(const GridDev& g, int qmode, const
             s.kq[l] = __dadd_rn(__dadd_rn(qb, __dsub_rn(qa, qc)), 0.0);
         }
     }
-    __syncthreads();
-    // 4. monotone repair: pool adjacent violators with equal weights.  The
-    //    descents q[k+1] < q[k] are listed in parallel; one thread then runs
-    //    the pooling from descent to descent, visiting only the knots that
-    //    pool (stretches between descents are singleton blocks that pool with
-    //    nothing).  The merges, and the order of the additions, are those of
-    //    the plain left-to-right algorithm.
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) s.ibuf[k] = (k + 1 < nk && s.kq[k + 1] < s.kq[k]) ? 1 : 0;
-    __syncthreads();
+    // knots of levels [l0, l1): 2l - 1 and 2l (two-sided), l (midpoint)
+    if (two) d.share(s.kq, max(2 * l0 - 1, 0), min(2 * l1 - 1, nk));
+    else d.share(s.kq, l0, l1);
+    // 4. monotone repair: pool adjacent violators (PAV) with equal weights.
+    //    A boundary between knots k-1 and k where max(q[0..k-1]) <= min(q[k..])
+    //    is never crossed by a pooled block, and the left-to-right stack
+    //    algorithm does the same merges, with the same additions in the same
+    //    order, on each side of it as it does on the whole.  So the knots are
+    //    cut at every such boundary (exact integer max/min scans on ordered
+    //    keys) and each segment is pooled by its own thread with that
+    //    algorithm; the bits are those of the single sequential pass.
     {
-        // compact the descent flags into a sorted list (deterministic scan)
-        const int T = blockDim.x;
+        long long* pm = reinterpret_cast<long long*>(s.bsum);   // prefix max of the keys
+        long long* wl = reinterpret_cast<long long*>(s.wsum);
+        const int T = blockDim.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int chunk = (nk + T - 1) / T;
-        const int b = threadIdx.x * chunk, e = min(nk, b + chunk);
-        int loc = 0;
-        for (int i = b; i < e; ++i) loc += s.ibuf[i];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        int incl = loc;
+        // prefix maximum, chunks in index order
+        {
+            const int b0 = threadIdx.x * chunk, e0 = min(nk, b0 + chunk);
+            long long loc = LLONG_MIN;
+            for (int i = b0; i < e0; ++i) loc = max(loc, okey(s.kq[i]));
+            long long incl = loc;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        int* wtot = reinterpret_cast<int*>(s.wsum);
-        if (lane == 31) wtot[warp] = incl;
-        __syncthreads();
-        int off = 0;
-        for (int w = 0; w < warp; ++w) off += wtot[w];
-        int run = off + incl - loc;
-        // flags are read into the compacted positions of bpos (not ibuf, which is being read)
-        for (int i = b; i < e; ++i) {
-            if (s.ibuf[i]) s.bpos[run] = i;
-            run += s.ibuf[i];
-        }
-        if (threadIdx.x == T - 1) s.flag[2] = run;   // number of descents
-    }
-    __syncthreads();
-    const int nd = s.flag[2];
-    if (nd > 0) {
-        for (int k = threadIdx.x; k < nd; k += blockDim.x) s.ibuf[k] = s.bpos[k];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double* bsum = s.bsum;
-            int* bpos = s.bpos;   // start | end << 16 of the pooled blocks on the stack
-            int nb = 0, pos = 0;
-            for (int q = 0; q < nd; ++q) {
-                const int d = s.ibuf[q];
-                if (d + 1 < pos) continue;   // inside a block already pooled
-                int cs = d + 1, ce = d + 2, cn = 1;
-                double csum = s.kq[d + 1];
-                for (;;) {
-                    // pool with the block on the left while its mean is larger
-                    for (;;) {
-                        if (cs == 0) break;
-                        double lsum;
-                        int ls, ln;
-                        const bool top = nb > 0 && (bpos[nb - 1] >> 16) == cs;
-                        if (top) {
-                            ls = bpos[nb - 1] & 0xFFFF;
-                            ln = cs - ls;
-                            lsum = bsum[nb - 1];
-                        } else {
-                            ls = cs - 1;
-                            ln = 1;
-                            lsum = s.kq[cs - 1];
-                        }
-                        // mean(left) > mean(cur) as lsum * cn > csum * ln
-                        if (!(__dmul_rn(lsum, (double)cn) > __dmul_rn(csum, (double)ln))) break;
-                        csum = __dadd_rn(lsum, csum);
-                        cn += ln;
-                        cs = ls;
-                        if (top) --nb;
-                    }
-                    // take in the next knot while it lies below the block's mean
-                    if (ce < nk && __dmul_rn(csum, 1.0) > __dmul_rn(s.kq[ce], (double)cn)) {
-                        csum = __dadd_rn(csum, s.kq[ce]);
-                        ++cn;
-                        ++ce;
-                        continue;
-                    }
-                    break;
-                }
-                bsum[nb] = csum;
-                bpos[nb] = cs | (ce << 16);
-                ++nb;
-                pos = ce;
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl = max(incl, t);
             }
-            for (int bi = 0; bi < nb; ++bi) {
-                const int bs = bpos[bi] & 0xFFFF, be = bpos[bi] >> 16;
-                if (be - bs < 2) continue;      // a knot that pooled with nothing keeps its bits
-                const double mean = __dadd_rn(__ddiv_rn(bsum[bi], (double)(be - bs)), 0.0);
-                for (int k = bs; k < be; ++k) s.kq[k] = mean;
+            if (lane == 31) wl[warp] = incl;
+            __syncthreads();
+            long long run = LLONG_MIN;
+            for (int w = 0; w < warp; ++w) run = max(run, wl[w]);
+            const long long prev = __shfl_up_sync(0xffffffffu, incl, 1);
+            if (lane > 0) run = max(run, prev);
+            for (int i = b0; i < e0; ++i) {
+                run = max(run, okey(s.kq[i]));
+                pm[i] = run;
+            }
+            __syncthreads();
+        }
+        // suffix minimum, chunks in reverse index order; segment starts into ibuf
+        {
+            const int r0 = threadIdx.x * chunk, r1 = min(nk, r0 + chunk);   // reversed positions
+            long long loc = LLONG_MAX;
+            for (int r = r0; r < r1; ++r) loc = min(loc, okey(s.kq[nk - 1 - r]));
+            long long incl = loc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl = min(incl, t);
+            }
+            if (lane == 31) wl[warp] = incl;
+            __syncthreads();
+            long long run = LLONG_MAX;
+            for (int w = 0; w < warp; ++w) run = min(run, wl[w]);
+            const long long prev = __shfl_up_sync(0xffffffffu, incl, 1);
+            if (lane > 0) run = min(run, prev);
+            for (int r = r0; r < r1; ++r) {
+                const int k = nk - 1 - r;
+                run = min(run, okey(s.kq[k]));
+                s.ibuf[k] = (k == 0 || pm[k - 1] <= run) ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        // segment starts -> sorted list in bpos (deterministic compaction)
+        {
+            const int b0 = threadIdx.x * chunk, e0 = min(nk, b0 + chunk);
+            int loc = 0;
+            for (int i = b0; i < e0; ++i) loc += s.ibuf[i];
+            int incl = loc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            int* wtot = reinterpret_cast<int*>(s.wsum);
+            if (lane == 31) wtot[warp] = incl;
+            __syncthreads();
+            int off = 0;
+            for (int w = 0; w < warp; ++w) off += wtot[w];
+            int run = off + incl - loc;
+            for (int i = b0; i < e0; ++i) {
+                if (s.ibuf[i]) s.bpos[run] = i;
+                run += s.ibuf[i];
+            }
+            if (threadIdx.x == T - 1) {
+                s.flag[2] = run;      // number of segments
+                s.bpos[run] = nk;     // end of the last one
+            }
+        }
+        __syncthreads();
+        const int nseg = s.flag[2];
+        // each segment [a, e) by one thread: the stack of pooled blocks below
+        // the top lives in bsum[a..] (sums) and ibuf[a..] (counts), the top
+        // block in registers
+        for (int j = threadIdx.x; j < nseg; j += T) {
+            const int a = s.bpos[j], e = s.bpos[j + 1];
+            if (e - a < 2) continue;   // one knot: nothing to pool
+            double R = s.kq[a];
+            int nr = 1, nb = 0;
+            for (int k = a + 1; k < e; ++k) {
+                s.bsum[a + nb] = R;
+                s.ibuf[a + nb] = nr;
+                ++nb;
+                R = s.kq[k];
+                nr = 1;
+                while (nb > 0) {
+                    const double Ls = s.bsum[a + nb - 1];
+                    const int nl = s.ibuf[a + nb - 1];
+                    // mean(left) > mean(right) as sum_l * n_r > sum_r * n_l
+                    if (!(__dmul_rn(Ls, (double)nr) > __dmul_rn(R, (double)nl))) break;
+                    R = __dadd_rn(Ls, R);
+                    nr += nl;
+                    --nb;
+                }
+            }
+            s.bsum[a + nb] = R;
+            s.ibuf[a + nb] = nr;
+            ++nb;
+            int k = a;
+            for (int t = 0; t < nb; ++t) {
+                const int c = s.ibuf[a + t];
+                if (c >= 2) {   // a knot that pooled with nothing keeps its bits
+                    const double mean = __dadd_rn(__ddiv_rn(s.bsum[a + t], (double)c), 0.0);
+                    for (int u = 0; u < c; ++u) s.kq[k + u] = mean;
+                }
+                k += c;
             }
         }
     }
     __syncthreads();
     // 5. PL CDF through the knots, right-continuous, read at the interior edges
-    for (int i = 1 + threadIdx.x; i < I; i += blockDim.x) {
+    const int e0 = 1 + d.lo(I - 1), e1 = 1 + d.hi(I - 1);
+    for (int i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
         const double x = edge(g, i);
         const long long kx = okey(x);
         int lo = 0, hi = nk;   // first knot with kq > x
@@ -446,7 +534,7 @@ __device__ inline void quantile_iterate_block(const GridDev& g, int qmode, const
         out[0] = 0.0;
         out[I] = 1.0;
     }
-    __syncthreads();
+    d.share(out, e0, e1);
 }
 
 // Additive (4.1), multiplicative (4.2) and rotation (4.3) iterators on masses.
@@ -504,13 +592,21 @@ __host__ __device__ inline size_t update_smem(int bins)
 }
 
 // The serial update of Section 3.2.3 (Eq. mm_sequential) for one problem on
-// the calling CTA (kCoarseThreads threads, update_smem(bins) bytes at usm):
+// the calling CTA, or on the CL CTAs of a cluster (kCoarseThreads threads,
+// update_smem(bins) bytes at usm in each):
 //   rho^0 = cdf0, rho^{n+1} = J(C(rho^n), fstar[n], cstar[n]), n < K.
+// Every CTA of the cluster holds the whole state; the matrix-vector product,
+// the normalisation, the quantiles and the read-back are split between them
+// (Dist), so the FP64 work per slice spreads over CL SMs.  Results do not
+// depend on CL.
+template <int CL = 1>
 __device__ inline void serial_sweep(unsigned char* usm, const double* __restrict__ P, const GridDev& g,
                                     int iterator, int qmode, int K, const double* __restrict__ cdf0,
                                     const double* __restrict__ fstar, const double* __restrict__ cstar,
                                     double* __restrict__ next, int32_t* status)
 {
+    const Dist<CL> d = Dist<CL>::make();
+    const bool writer = d.rank == 0;
     const int I = g.bins;
     double* cur = reinterpret_cast<double*>(usm);
     double* Ab = cur + (I + 1);
@@ -523,11 +619,11 @@ __device__ inline void serial_sweep(unsigned char* usm, const double* __restrict
     if (threadIdx.x == 0) js.flag[1] = 0;
     for (int i = threadIdx.x; i <= I; i += blockDim.x) {
         cur[i] = cdf0[i];
-        next[i] = cdf0[i];
+        if (writer) next[i] = cdf0[i];
     }
-    __syncthreads();
+    d.sync();   // every CTA of the cluster runs before any writes into its shared memory
     for (int n = 0; n < K; ++n) {
-        coarse_apply_block(P, I, cur, Ab, mass, mp, js.wsum);
+        coarse_apply_block<CL>(P, I, cur, Ab, mass, mp, js.wsum, d);
         double* res = Ab;
         if (iterator != PR_ITER_NONE) {
             for (int i = threadIdx.x; i <= I; i += blockDim.x) {
@@ -535,7 +631,7 @@ __device__ inline void serial_sweep(unsigned char* usm, const double* __restrict
                 Cb[i] = cstar[(size_t)n * (I + 1) + i];
             }
             __syncthreads();
-            if (iterator == PR_ITER_QUANTILE) quantile_iterate_block(g, qmode, Ab, Bb, Cb, Ob, js);
+            if (iterator == PR_ITER_QUANTILE) quantile_iterate_block<CL>(g, qmode, Ab, Bb, Cb, Ob, js, d);
             else mass_iterate_block(iterator, I, Ab, Bb, Cb, Ob, js.kq, js.wsum);
             res = Ob;
         }
@@ -543,11 +639,12 @@ __device__ inline void serial_sweep(unsigned char* usm, const double* __restrict
             const double v = res[i];
             if (!isfinite(v)) js.flag[1] = 1;
             cur[i] = v;
-            next[(size_t)(n + 1) * (I + 1) + i] = v;
+            if (writer) next[(size_t)(n + 1) * (I + 1) + i] = v;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && status) *status = js.flag[1] ? PR_ERR_NUMERIC : PR_OK;
+    if (threadIdx.x == 0 && status && writer) *status = js.flag[1] ? PR_ERR_NUMERIC : PR_OK;
+    d.sync();   // no CTA leaves while another may still write into its shared memory
 }
 
 }  // namespace pr

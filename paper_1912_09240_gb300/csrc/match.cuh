@@ -77,13 +77,6 @@ __device__ inline MatchSmem carve_match_smem(unsigned char* base, int bins)
     return m;
 }
 
-// Equality of two doubles by their bits (+0 and -0 equal); no FP64 unit.
-__device__ __forceinline__ bool deq(double a, double b)
-{
-    const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
-    return x == y || ((x | y) << 1) == 0;
-}
-
 // Block-wide exclusive scan of v[0..n) (ints) into out[0..n], out[n] = total.
 // Deterministic; every thread of the block must call it; v may equal out.
 __device__ inline void block_exclusive_scan_int(const int* v, int* out, int n, int* scratch)

@@ -285,6 +285,14 @@ __device__ __forceinline__ void build_thresholds(const GridDev& g, float* thr)
     for (int i = threadIdx.x; i <= g.bins; i += blockDim.x) thr[i] = __double2float_ru(edge(g, i));
 }
 
+// Equality of two non-NaN doubles by their bits (+0 and -0 equal), on the
+// integer units.
+__device__ __forceinline__ bool deq(double a, double b)
+{
+    const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+    return x == y || ((x | y) << 1) == 0;
+}
+
 // Exact ordering of non-negative doubles through their bit patterns.
 __device__ __forceinline__ long long dkey(double v) { return __double_as_longlong(v); }
 

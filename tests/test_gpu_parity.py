@@ -432,3 +432,38 @@ def test_parareal_update_matches_oracle(L, orc):
             np.testing.assert_allclose(got[n + 1], r, rtol=0, atol=1e-12)
     finally:
         L.pr_coarse_destroy(h)
+
+
+@pytest.mark.parametrize("bins", [64, 512, 1024])
+def test_update_cluster_sizes_agree(L, bins):
+    """The serial sweep split over a cluster of 2, 4 or 8 CTAs gives the
+    one-CTA sweep's results bit for bit, for every iterator and both quantile
+    modes (each element is computed by one CTA with the same arithmetic)."""
+    K = 7
+    gm = L.Model(1, 1, 0.5, 3.0, 0.01)
+    rng = np.random.default_rng(bins)
+    cdf0 = _rand_cdf(rng, bins, 0.5)
+    fs = np.stack([_rand_cdf(rng, bins, 0.3) for _ in range(K)])
+    cs = np.stack([_rand_cdf(rng, bins, 0.0) for _ in range(K)])
+    h = L.pr_coarse_create(gm, L.Grid(bins, -3.0, 3.0), 0.1)
+    try:
+        cases = [(L.PR_ITER_QUANTILE, 0), (L.PR_ITER_QUANTILE, 1), (L.PR_ITER_ADD, 0), (L.PR_ITER_NONE, 0)]
+        for it, qm in cases:
+            ref = None
+            for cl in (1, 2, 4, 8):
+                L.pr_set_update_cluster(cl)
+                out = torch.full((K + 1, bins + 1), float("nan"), dtype=torch.float64, device=DEV)
+                st = torch.full((1,), -1, dtype=torch.int32, device=DEV)
+                none = it == L.PR_ITER_NONE
+                L.pr_parareal_update(h, it, qm, K, _t(cdf0), None if none else _t(fs), None if none else _t(cs),
+                                     out, st)
+                torch.cuda.synchronize()
+                assert int(st.item()) == 0, (it, qm, cl)
+                got = out.cpu().numpy()
+                if ref is None:
+                    ref = got
+                else:
+                    np.testing.assert_array_equal(got, ref, err_msg=f"iterator {it} mode {qm} cluster {cl}")
+    finally:
+        L.pr_set_update_cluster(8)
+        L.pr_coarse_destroy(h)
