@@ -37,12 +37,13 @@ WORKLOAD = workloads.DOUBLE_WELL
 # (d = 1, 4 particles per thread): ncu smsp__inst_issued.sum x 32 over the
 # particle-steps of the launch, double-well workload at 2^16 particles x 9
 # slices x 1000 steps (profiles/fine_f32_d1_double_well.md).
-INST_PER_PARTICLE_STEP = 41.70
+INST_PER_PARTICLE_STEP = 41.42
 # DRAM bytes per particle per slice of that kernel, read + write (ncu
-# dram__bytes_read.sum + dram__bytes_write.sum of a full-size 49-slice launch
-# after iteration 0, profiles/launches_double_well_full.md); the algorithmic
-# figure is 16 B (x and y read once and written once, binary32).
-TRAFFIC_BYTES_PER_PARTICLE_SLICE = 15.32
+# dram__bytes_read.sum + dram__bytes_write.sum of the 9-slice launch at 2^21
+# particles, inputs larger than L2, scaled by particle-slices to the full
+# launch; profiles/fine_f32_d1_double_well.md); the algorithmic figure is
+# 16 B (x and y read once and written once, binary32).
+TRAFFIC_BYTES_PER_PARTICLE_SLICE = 13.77
 SMS = 152
 ISSUE_LANES_PER_SM_CLK = 4 * 32       # 4 sub-partitions x one 32-wide warp instruction per clock
 
