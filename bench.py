@@ -526,6 +526,7 @@ def run_ours(args):
     conv = None
     if not args.no_conv:
         _, _, rho_ser = solver.serial_reference()
+        solver.w1_to(rho_ser).max().item()   # first launch of the W1 kernel (module load) outside the clock
         solver.set_initial(x0t, y0t)
         w1_hist, k_star = [], None
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
