@@ -624,3 +624,152 @@ double or_w1(int I, double lo, double hi, const double* C1, const double* C2)
     }
     return acc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Matching that preserves the conditional distribution (Section 5.2):      */
+/* mu = mubar f(x) with f = rho / rhobar, sampled by reweighting the prior  */
+/* ensemble, W^p = Wbar^p rho_i / rhobar_i with i the bin of Xbar^p, and    */
+/* optionally by stratified resampling after it (Eq. stratified), or its     */
+/* deterministic variant u~ = 1/2.  Positions are not moved.                 */
+/* Readings: rhobar and rho are the bin masses of the given prior and target */
+/* CDFs.  A target bin with mass where the prior has none gives half of it   */
+/* to the nearest bin with prior mass on its left and half to the nearest    */
+/* one on its right, or all of it to the only side that has one; the bins    */
+/* are visited from left to right, each adding to the running masses.  A     */
+/* particle in a bin without prior mass (possible only with a prior CDF that */
+/* is not this ensemble's) gets weight 0.                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Per-bin factors r_i = rho'_i / rhobar_i (0 where rhobar_i = 0), with rho'
+ * the target masses after the relocation above. */
+void or_reweight_factors(int I, const double* Cp, const double* Ct, double* r)
+{
+    double* rb = (double*)malloc(sizeof(double) * I);
+    double* rt = (double*)malloc(sizeof(double) * I);
+    double* rn = (double*)malloc(sizeof(double) * I);
+    for (int i = 0; i < I; ++i) {
+        rb[i] = Cp[i + 1] - Cp[i];
+        rt[i] = Ct[i + 1] - Ct[i];
+        rn[i] = rb[i] > 0.0 ? rt[i] : 0.0;
+    }
+    for (int i = 0; i < I; ++i) {
+        if (rb[i] > 0.0 || !(rt[i] > 0.0)) continue;
+        int L = i - 1, R = i + 1;
+        while (L >= 0 && !(rb[L] > 0.0)) --L;
+        while (R < I && !(rb[R] > 0.0)) ++R;
+        if (L >= 0 && R < I) {
+            rn[L] += 0.5 * rt[i];
+            rn[R] += 0.5 * rt[i];
+        } else if (L >= 0) {
+            rn[L] += rt[i];
+        } else if (R < I) {
+            rn[R] += rt[i];
+        }
+    }
+    for (int i = 0; i < I; ++i) r[i] = rb[i] > 0.0 ? rn[i] / rb[i] : 0.0;
+    free(rb); free(rt); free(rn);
+}
+
+/* W^p = Wbar^p r_{bin(Xbar^p)}; wbar NULL means the uniform weight 1/N.
+ * x, wbar, w: [n_slices][N]; cdf_prior, cdf_target: [n_slices][I+1]. */
+void or_reweight(const double* x, const double* wbar, int64_t N, int n_slices, int I, double lo, double hi,
+                 const double* cdf_prior, const double* cdf_target, double* w)
+{
+    double* r = (double*)malloc(sizeof(double) * I);
+    const double w0 = 1.0 / (double)N;
+    for (int s = 0; s < n_slices; ++s) {
+        or_reweight_factors(I, cdf_prior + (int64_t)s * (I + 1), cdf_target + (int64_t)s * (I + 1), r);
+        for (int64_t p = 0; p < N; ++p) {
+            const int64_t k = (int64_t)s * N + p;
+            const double wb = wbar ? wbar[k] : w0;
+            w[k] = wb * r[or_bin(x[k], I, lo, hi)];
+        }
+    }
+    free(r);
+}
+
+/* Weights in fixed point: round(W 2^61) as a 64-bit integer (W >= 0; the
+ * scaling by a power of two is exact and the rounding is to nearest, ties
+ * to even).  Sums of these are exact in any order.  The weights are
+ * probability weights (Section 5.2: they sum to one); sums up to 8 fit. */
+uint64_t or_weight_fixed(double w)
+{
+    if (!(w > 0.0)) return 0;
+    return (uint64_t)llrint(ldexp(w, 61));
+}
+
+/* Stratified resampling (Section 5.2, Eq. stratified) of N weighted
+ * particles into N equally weighted ones: output j takes the particle p
+ * whose cumulative-weight interval [sum_{q<p} W^q, sum_{q<=p} W^q) holds
+ * u_j = (j + u~_j) / N, the points scaled by the total weight T.
+ * Readings: the cumulative weights are taken in the fixed point above, so
+ * that the selection is exact and independent of the order of summation;
+ * u~_j = a_j / 2^24 with a_j the odd 24-bit integer of the uniform of word 0
+ * of Philox block (j, 0xFFFFFFFF, slice, problem << 8 | 0xFE) (stratified,
+ * mode 0) or a_j = 2^23 (u~ = 1/2, deterministic, mode 1); the point is
+ * U_j = floor(T (j 2^24 + a_j) / (N 2^24)); a point on a boundary goes to the
+ * particle on its right (the paper's strict inequalities leave it to none).
+ * With T = 0 (no weight at all) output j takes particle j.
+ * w: [n_slices][N]; idx: [n_slices][N], the particle of each output. */
+void or_resample(const double* w, int64_t N, int n_slices, int mode, uint64_t seed, uint32_t problem,
+                 uint32_t slice_begin, uint32_t* idx)
+{
+    uint64_t* C = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)N);
+    const uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    for (int s = 0; s < n_slices; ++s) {
+        const double* ws = w + (int64_t)s * N;
+        uint32_t* is = idx + (int64_t)s * N;
+        uint64_t run = 0;
+        for (int64_t p = 0; p < N; ++p) {
+            run += or_weight_fixed(ws[p]);
+            C[p] = run;
+        }
+        const uint64_t T = run;
+        int64_t p = 0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (T == 0) { is[j] = (uint32_t)j; continue; }
+            uint64_t a = (uint64_t)1 << 23;
+            if (mode == 0) {
+                const uint32_t ctr[4] = {(uint32_t)j, 0xFFFFFFFFu, slice_begin + (uint32_t)s, (problem << 8) | 0xFEu};
+                uint32_t out[4];
+                or_philox4x32_10(ctr, key, out);
+                a = 2 * (uint64_t)(out[0] >> 9) + 1;
+            }
+            const unsigned __int128 num = (unsigned __int128)T * (((uint64_t)j << 24) + a);
+            const uint64_t U = (uint64_t)(num / ((unsigned __int128)N << 24));
+            /* the points increase with j, so the search resumes where it stopped */
+            while (C[p] <= U) ++p;
+            is[j] = (uint32_t)p;
+        }
+    }
+    free(C);
+}
+
+/* Restriction with weights (the general form of Section 3.2.2, Eq. binning,
+ * rho_i = sum of the weights in bin i), in the fixed point above:
+ * C_0 = 0, C_i = (sum of fixed weights in bins < i) / (total), both sums
+ * exact integers converted to double once.  With no weight at all the CDF
+ * is that of an empty histogram read as uniform (C_i = i / I). */
+void or_restrict_weighted(const double* x, const double* w, int64_t N, int n_slices, int I, double lo,
+                          double hi, double* cdf)
+{
+    uint64_t* h = (uint64_t*)malloc(sizeof(uint64_t) * I);
+    for (int s = 0; s < n_slices; ++s) {
+        for (int i = 0; i < I; ++i) h[i] = 0;
+        for (int64_t p = 0; p < N; ++p) {
+            const int64_t k = (int64_t)s * N + p;
+            h[or_bin(x[k], I, lo, hi)] += or_weight_fixed(w[k]);
+        }
+        uint64_t T = 0;
+        for (int i = 0; i < I; ++i) T += h[i];
+        double* Cs = cdf + (int64_t)s * (I + 1);
+        uint64_t below = 0;
+        Cs[0] = 0.0;
+        for (int i = 0; i < I; ++i) {
+            below += h[i];
+            Cs[i + 1] = T > 0 ? (double)below / (double)T : (double)(i + 1) / (double)I;
+        }
+        Cs[I] = 1.0;
+    }
+    free(h);
+}

@@ -76,6 +76,12 @@ def lib():
         _lib.or_iterator_mass.argtypes = [i32, i32, vp, vp, vp, vp]
         _lib.or_w1.argtypes = [i32, d, d, vp, vp]
         _lib.or_w1.restype = d
+        _lib.or_reweight_factors.argtypes = [i32, vp, vp, vp]
+        _lib.or_reweight.argtypes = [vp, vp, i64, i32, i32, d, d, vp, vp, vp]
+        _lib.or_weight_fixed.argtypes = [d]
+        _lib.or_weight_fixed.restype = u64
+        _lib.or_resample.argtypes = [vp, i64, i32, i32, u64, u32, u32, vp]
+        _lib.or_restrict_weighted.argtypes = [vp, vp, i64, i32, i32, d, d, vp]
     return _lib
 
 
@@ -233,6 +239,64 @@ def match(x_prior: np.ndarray, grid: Grid, cdf_prior: np.ndarray, cdf_target: np
     return out
 
 
+# --------------------------------------------------------------------------
+# Matching preserving the conditional distribution (Section 5.2)
+# --------------------------------------------------------------------------
+
+RESAMPLE_STRATIFIED, RESAMPLE_DETERMINISTIC = 0, 1
+
+
+def reweight_factors(grid: Grid, cdf_prior: np.ndarray, cdf_target: np.ndarray) -> np.ndarray:
+    """r_i = rho'_i / rhobar_i for one prior/target pair (mass of target bins
+    the prior does not support moved half left, half right)."""
+    cp = np.ascontiguousarray(cdf_prior, dtype=np.float64)
+    ct = np.ascontiguousarray(cdf_target, dtype=np.float64)
+    r = np.empty(grid.bins)
+    lib().or_reweight_factors(grid.bins, _p(cp), _p(ct), _p(r))
+    return r
+
+
+def reweight(x: np.ndarray, grid: Grid, cdf_prior: np.ndarray, cdf_target: np.ndarray,
+             wbar: np.ndarray | None = None) -> np.ndarray:
+    """W^p = Wbar^p rho'_i / rhobar_i; x, wbar: [n_slices][N] (wbar None: 1/N)."""
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    n_slices, N = x.shape
+    cp = np.ascontiguousarray(np.atleast_2d(cdf_prior), dtype=np.float64)
+    ct = np.ascontiguousarray(np.atleast_2d(cdf_target), dtype=np.float64)
+    assert cp.shape == ct.shape == (n_slices, grid.bins + 1)
+    wb = None if wbar is None else np.ascontiguousarray(np.atleast_2d(wbar), dtype=np.float64)
+    w = np.empty_like(x)
+    lib().or_reweight(_p(x), None if wb is None else _p(wb), N, n_slices, grid.bins, grid.lo, grid.hi,
+                      _p(cp), _p(ct), _p(w))
+    return w
+
+
+def weight_fixed(w) -> int:
+    """round(w 2^61) as an integer (the fixed point of the cumulative weights)."""
+    return int(lib().or_weight_fixed(float(w)))
+
+
+def resample(w: np.ndarray, mode: int, seed: int, slice_begin: int, problem: int = 0) -> np.ndarray:
+    """Stratified (mode 0) or deterministic (mode 1) resampling: index[n_slices][N]
+    of the particle each output takes."""
+    w = np.ascontiguousarray(np.atleast_2d(w), dtype=np.float64)
+    n_slices, N = w.shape
+    idx = np.empty((n_slices, N), dtype=np.uint32)
+    lib().or_resample(_p(w), N, n_slices, mode, seed, problem, slice_begin, _p(idx))
+    return idx
+
+
+def restrict_weighted(x: np.ndarray, w: np.ndarray, grid: Grid) -> np.ndarray:
+    """Weighted restriction: CDFs [n_slices][I+1] of the bin sums of the weights."""
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    w = np.ascontiguousarray(np.atleast_2d(w), dtype=np.float64)
+    n_slices, N = x.shape
+    assert w.shape == x.shape
+    cdf = np.empty((n_slices, grid.bins + 1))
+    lib().or_restrict_weighted(_p(x), _p(w), N, n_slices, grid.bins, grid.lo, grid.hi, _p(cdf))
+    return cdf
+
+
 QMODE_TWO_SIDED, QMODE_MIDPOINT = 0, 1
 ITER_QUANTILE, ITER_ADD, ITER_MULT, ITER_ROT = 0, 1, 2, 3
 
@@ -343,6 +407,7 @@ class PararealResult:
     rho: list         # rho[k] = CDFs [K+1][I+1], rho_k^n
     serial_x: np.ndarray | None = None
     serial_rho: np.ndarray | None = None
+    w: list | None = None   # w[k] = weights [K+1][N] (uniform 1/N except in "reweight" mode)
 
 
 def serial_fine(model: Model, seed: int, x0, y0, K: int, steps: int, dt: float, problem: int = 0):
@@ -360,15 +425,40 @@ def serial_fine(model: Model, seed: int, x0, y0, K: int, steps: int, dt: float, 
     return xs, ys
 
 
+MATCHINGS = ("quantile", "resample", "resample_det", "reweight")
+
+
+def _conditional_match(grid: Grid, xp, yp, cdf_prior, cdf_target, matching: str, seed: int, problem: int,
+                       slice_begin: int, wbar=None):
+    """Section 5.2 on slices slice_begin..: reweight the priors xp[S][N] (weights
+    wbar, None: 1/N) to the targets, then resample (stratified or u~ = 1/2) or
+    keep the weights.  Returns (x, y, w) with w None after resampling."""
+    w = reweight(xp, grid, cdf_prior, cdf_target, wbar)
+    if matching == "reweight":
+        return xp.copy(), yp.copy(), w
+    mode = RESAMPLE_STRATIFIED if matching == "resample" else RESAMPLE_DETERMINISTIC
+    idx = resample(w, mode, seed, slice_begin, problem).astype(np.int64)
+    x = np.take_along_axis(xp, idx, axis=1)
+    y = np.stack([yp[s][:, idx[s]] for s in range(xp.shape[0])])
+    return x, y, None
+
+
 def parareal(model: Model, grid: Grid, seed: int, x0, y0, K: int, steps: int, dt: float,
              iters: int, qmode: int = QMODE_TWO_SIDED, iterator: int = ITER_QUANTILE,
-             problem: int = 0) -> PararealResult:
+             problem: int = 0, matching: str = "quantile") -> PararealResult:
+    """Sections 3.2.3-3.2.4 with the matching of Section 5.1 ("quantile") or
+    of Section 5.2 ("resample": reweighting and stratified resampling,
+    "resample_det": u~ = 1/2, "reweight": weights carried by the ensembles,
+    restrictions weighted).  res.w[k] holds the weights in "reweight" mode."""
+    assert matching in MATCHINGS
     x0 = np.asarray(x0, dtype=np.float64)
     y0 = np.asarray(y0, dtype=np.float64).reshape(model.fast_dim, -1)
     N = x0.shape[0]
+    weighted = matching == "reweight"
+    uni = np.full(N, 1.0 / N)
+    R = (lambda x, w: restrict_weighted(x, w, grid)) if weighted else (lambda x, w: restrict(x, grid)[1])
     P = coarse_propagator(model, grid, steps * dt)
-    _, cdf0 = restrict(x0[None], grid)
-    cdf0 = cdf0[0]
+    cdf0 = R(x0[None], uni[None])[0]
 
     # iteration 0: coarse sweep, then matching against the initial ensemble
     rho = np.empty((K + 1, grid.bins + 1))
@@ -377,18 +467,27 @@ def parareal(model: Model, grid: Grid, seed: int, x0, y0, K: int, steps: int, dt
         rho[n + 1] = coarse_apply(P, rho[n])[0]
     X = np.empty((K + 1, N))
     Y = np.empty((K + 1, model.fast_dim, N))
+    W = np.tile(uni, (K + 1, 1))
     X[0] = x0
     Y[0] = y0
-    for n in range(1, K + 1):
-        X[n] = match(x0[None], grid, cdf0[None], rho[n][None])[0]
-        Y[n] = y0
+    if matching == "quantile":
+        for n in range(1, K + 1):
+            X[n] = match(x0[None], grid, cdf0[None], rho[n][None])[0]
+            Y[n] = y0
+    else:
+        xs, ys, ws = _conditional_match(grid, np.tile(x0, (K, 1)), np.tile(y0, (K, 1, 1)),
+                                        np.tile(cdf0, (K, 1)), rho[1:], matching, seed, problem, 1)
+        X[1:], Y[1:] = xs, ys
+        if ws is not None:
+            W[1:] = ws
     res = PararealResult(x=[X.copy()], y=[Y.copy()], rho=[rho.copy()])
+    res.w = [W.copy()]
 
     for _k in range(iters):
         # parallel phase
         Xbar, Ybar = fine_propagate(model, seed, X[:K], Y[:K], 0, steps, dt, problem)
-        _, f_star = restrict(Xbar, grid)
-        _, start = restrict(X[:K], grid)
+        f_star = R(Xbar, W[:K])
+        start = R(X[:K], W[:K])
         c_star = coarse_apply(P, start)
         # serial phase
         new_rho = np.empty_like(rho)
@@ -399,12 +498,21 @@ def parareal(model: Model, grid: Grid, seed: int, x0, y0, K: int, steps: int, dt
         # matching with the fine results as priors
         Xn = np.empty_like(X)
         Yn = np.empty_like(Y)
+        Wn = np.tile(uni, (K + 1, 1))
         Xn[0] = x0
         Yn[0] = y0
-        Xn[1:] = match(Xbar, grid, f_star, new_rho[1:])
-        Yn[1:] = Ybar
-        X, Y, rho = Xn, Yn, new_rho
+        if matching == "quantile":
+            Xn[1:] = match(Xbar, grid, f_star, new_rho[1:])
+            Yn[1:] = Ybar
+        else:
+            xs, ys, ws = _conditional_match(grid, Xbar, Ybar, f_star, new_rho[1:], matching, seed, problem, 1,
+                                            W[:K] if weighted else None)
+            Xn[1:], Yn[1:] = xs, ys
+            if ws is not None:
+                Wn[1:] = ws
+        X, Y, W, rho = Xn, Yn, Wn, new_rho
         res.x.append(X.copy())
         res.y.append(Y.copy())
         res.rho.append(rho.copy())
+        res.w.append(W.copy())
     return res
