@@ -71,6 +71,10 @@ typedef enum {
  * exactly); MIDPOINT takes the midpoint, as the paper prints it. */
 typedef enum { PR_QMODE_TWO_SIDED = 0, PR_QMODE_MIDPOINT = 1 } pr_quantile_mode;
 
+/* Resampling of Section 5.2: stratified points u_j = (j + u~_j)/N with u~_j
+ * uniform (Eq. stratified), or the deterministic variant u~_j = 1/2. */
+typedef enum { PR_RESAMPLE_STRATIFIED = 0, PR_RESAMPLE_DETERMINISTIC = 1 } pr_resample_mode;
+
 typedef struct {
     int32_t kind;       /* pr_model_kind */
     int32_t fast_dim;   /* d, the dimension of Y */
@@ -186,6 +190,65 @@ pr_status pr_counts_to_cdf(const uint32_t* counts, int64_t n, int32_t n_slices, 
 pr_status pr_match(pr_precision precision, const void* x_prior, void* x_out, int64_t n,
                    int32_t n_slices, const pr_grid* grid,
                    const double* cdf_prior, const double* cdf_target, void* stream);
+
+/*
+ * Matching that preserves the conditional distribution (Section 5.2), step
+ * one: reweighting, W^p = Wbar^p rho'_i / rhobar_i with i the bin of Xbar^p,
+ * rhobar and rho the bin masses of cdf_prior and cdf_target.  Target mass in
+ * bins without prior mass moves half to the nearest bin with prior mass on
+ * each side (all of it to the only side that has one); a particle in a bin
+ * without prior mass gets weight 0.  Positions are not touched.  Equal CDFs
+ * leave the weights unchanged bit for bit.
+ *   x_prior    (device) [n_slices][n] (binary32 or binary64), or [n] shared by
+ *              all slices when broadcast_input is non-zero
+ *   w_prior    (device) same layout as x_prior, double, or NULL (1/n each)
+ *   cdf_prior, cdf_target (device) [n_slices][bins+1]
+ *   w_out      (device) [n_slices][n] double
+ */
+pr_status pr_reweight(pr_precision precision, const void* x_prior, int32_t broadcast_input,
+                      const double* w_prior, int64_t n, int32_t n_slices, const pr_grid* grid,
+                      const double* cdf_prior, const double* cdf_target, double* w_out, void* stream);
+
+/*
+ * Step two: stratified resampling (Section 5.2, Eq. stratified) of n
+ * weighted particles into n equally weighted ones.  Output j takes the
+ * particle p with C_{p-1} <= U_j < C_p, where C_p are the cumulative weights
+ * in fixed point (round(W 2^61) as 64-bit integers: exact in any summation
+ * order), T = C_{n-1} and U_j = floor(T (j 2^24 + a_j) / (n 2^24)): a_j the
+ * odd 24-bit integer of the uniform of word 0 of Philox block
+ * (j, 0xFFFFFFFF, slice, problem_id << 8 | 0xFE) for PR_RESAMPLE_STRATIFIED,
+ * 2^23 (u~ = 1/2) for PR_RESAMPLE_DETERMINISTIC; slice = slice_begin + s.
+ * Equal weights give output j = particle j (strong projection).  T = 0 (no
+ * weight) gives the identity as well.  Weights are probability weights: their
+ * sum must stay below 8.
+ *   x_in, y_in (device) [n_slices][n], [n_slices][fast_dim][n] (or one slice
+ *              with broadcast_input), precision as given; may be NULL when the
+ *              matching output is NULL
+ *   w          (device) [n_slices][n] double
+ *   index_out  (device) [n_slices][n] uint32 or NULL: the particle each output takes
+ *   x_out, y_out (device) gathered states, same layouts as the inputs without
+ *              broadcast, or NULL; not aliasing the inputs
+ *   workspace  (device) >= pr_resample_workspace(n, n_slices) bytes, 256-byte aligned
+ */
+size_t pr_resample_workspace(int64_t n, int32_t n_slices);
+pr_status pr_resample(pr_precision precision, int32_t fast_dim, const void* x_in, const void* y_in,
+                      int32_t broadcast_input, const double* w, int64_t n, int32_t n_slices,
+                      int32_t slice_begin, pr_resample_mode mode, const pr_rng* rng, uint32_t* index_out,
+                      void* x_out, void* y_out, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Restriction with weights (Section 3.2.2, Eq. binning with weights W^p):
+ * bin sums of the weights in the fixed point above (exact, any order), then
+ * the CDF at the edges, C_i = (sum over bins < i) / (total) with C_0 = 0 and
+ * C_bins = 1 (the uniform CDF i / bins when no particle has weight).
+ *   x (device) [n_slices][n]; w (device) [n_slices][n] double (probability weights)
+ *   cdf (device) [n_slices][bins+1]
+ *   workspace (device) >= pr_restrict_weighted_workspace(n_slices, bins) bytes, 8-byte aligned
+ */
+size_t pr_restrict_weighted_workspace(int32_t n_slices, int32_t bins);
+pr_status pr_restrict_weighted(pr_precision precision, const void* x, const double* w, int64_t n,
+                               int32_t n_slices, const pr_grid* grid, double* cdf, void* workspace,
+                               size_t workspace_bytes, void* stream);
 
 /*
  * Coarse propagator C_dT (Section 2.2.2): finite volumes on the detailed-

@@ -19,6 +19,7 @@ PR_F32, PR_F64 = 0, 1
 PR_MODEL_OU, PR_MODEL_DOUBLE_WELL, PR_MODEL_DW_MULTI = 0, 1, 2
 PR_ITER_QUANTILE, PR_ITER_ADD, PR_ITER_MULT, PR_ITER_ROT, PR_ITER_NONE = 0, 1, 2, 3, 4
 PR_QMODE_TWO_SIDED, PR_QMODE_MIDPOINT = 0, 1
+PR_RESAMPLE_STRATIFIED, PR_RESAMPLE_DETERMINISTIC = 0, 1
 
 EXPORTED = (
     "pr_status_string", "pr_version", "pr_rng_words", "pr_fine_propagate", "pr_set_particles_per_thread",
@@ -28,7 +29,8 @@ EXPORTED = (
     "pr_fine_adjoint_noalloc_capacity", "pr_fine_adjoint_noalloc",
     "pr_batch_create", "pr_batch_destroy", "pr_batch_particle_steps", "pr_batch_set_initial", "pr_batch_iterate",
     "pr_batch_rho", "pr_batch_fine_state", "pr_batch_status", "pr_batch_set_config", "pr_batch_get_config",
-    "pr_batch_tune",
+    "pr_batch_tune", "pr_reweight", "pr_resample_workspace", "pr_resample", "pr_restrict_weighted_workspace",
+    "pr_restrict_weighted",
 )
 
 
@@ -162,11 +164,19 @@ def lib() -> ctypes.CDLL:
     L.pr_batch_set_config.argtypes = [vp, i32, d]
     L.pr_batch_get_config.argtypes = [vp, P(i32), P(d), P(i32)]
     L.pr_batch_tune.argtypes = [vp, i32, P(d), vp]
+    L.pr_reweight.argtypes = [i32, vp, i32, vp, i64, i32, P(_Grid), vp, vp, vp, vp]
+    L.pr_resample_workspace.argtypes = [i64, i32]
+    L.pr_resample_workspace.restype = ctypes.c_size_t
+    L.pr_resample.argtypes = [i32, i32, vp, vp, i32, vp, i64, i32, i32, i32, P(_Rng), vp, vp, vp, vp,
+                              ctypes.c_size_t, vp]
+    L.pr_restrict_weighted_workspace.argtypes = [i32, i32]
+    L.pr_restrict_weighted_workspace.restype = ctypes.c_size_t
+    L.pr_restrict_weighted.argtypes = [i32, vp, vp, i64, i32, P(_Grid), vp, vp, ctypes.c_size_t, vp]
     for name in EXPORTED:
         if name not in ("pr_status_string", "pr_version", "pr_set_particles_per_thread",
                         "pr_set_tiles_per_cta", "pr_set_update_cluster", "pr_fine_adjoint_workspace",
                         "pr_order_statistics_workspace", "pr_fine_adjoint_noalloc_capacity",
-                        "pr_batch_particle_steps"):
+                        "pr_batch_particle_steps", "pr_resample_workspace", "pr_restrict_weighted_workspace"):
             getattr(L, name).restype = i32
     _lib = L
     return L
@@ -303,6 +313,40 @@ def pr_fine_adjoint(model: Model, rng: Rng, x0, y0, n: int, slice_begin: int, n_
 
 def pr_order_statistics_workspace(n: int) -> int:
     return lib().pr_order_statistics_workspace(n)
+
+
+def pr_reweight(precision: int, x_prior, broadcast_input: bool, w_prior, n: int, n_slices: int, grid: Grid,
+                cdf_prior, cdf_target, w_out, stream=None):
+    g = grid.c()
+    _check("pr_reweight", lib().pr_reweight(precision, _ptr(x_prior), int(bool(broadcast_input)), _ptr(w_prior), n,
+                                            n_slices, ctypes.byref(g), _ptr(cdf_prior), _ptr(cdf_target),
+                                            _ptr(w_out), _stream(stream)))
+
+
+def pr_resample_workspace(n: int, n_slices: int) -> int:
+    return lib().pr_resample_workspace(n, n_slices)
+
+
+def pr_resample(precision: int, fast_dim: int, x_in, y_in, broadcast_input: bool, w, n: int, n_slices: int,
+                slice_begin: int, mode: int, rng: Rng, index_out, x_out, y_out, workspace, stream=None):
+    r = rng.c()
+    wbytes = workspace.numel() * workspace.element_size()
+    _check("pr_resample", lib().pr_resample(precision, fast_dim, _ptr(x_in), _ptr(y_in), int(bool(broadcast_input)),
+                                            _ptr(w), n, n_slices, slice_begin, mode, ctypes.byref(r),
+                                            _ptr(index_out), _ptr(x_out), _ptr(y_out), _ptr(workspace), wbytes,
+                                            _stream(stream)))
+
+
+def pr_restrict_weighted_workspace(n_slices: int, bins: int) -> int:
+    return lib().pr_restrict_weighted_workspace(n_slices, bins)
+
+
+def pr_restrict_weighted(precision: int, x, w, n: int, n_slices: int, grid: Grid, cdf, workspace, stream=None):
+    g = grid.c()
+    wbytes = workspace.numel() * workspace.element_size()
+    _check("pr_restrict_weighted", lib().pr_restrict_weighted(precision, _ptr(x), _ptr(w), n, n_slices,
+                                                              ctypes.byref(g), _ptr(cdf), _ptr(workspace), wbytes,
+                                                              _stream(stream)))
 
 
 def pr_order_statistics(x, n: int, ranks, n_ranks: int, index_out, workspace, stream=None):
