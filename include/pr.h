@@ -241,13 +241,14 @@ pr_status pr_resample(pr_precision precision, int32_t fast_dim, const void* x_in
  * bin sums of the weights in the fixed point above (exact, any order), then
  * the CDF at the edges, C_i = (sum over bins < i) / (total) with C_0 = 0 and
  * C_bins = 1 (the uniform CDF i / bins when no particle has weight).
- *   x (device) [n_slices][n]; w (device) [n_slices][n] double (probability weights)
+ *   x (device) [n_slices][n], or [n] shared by all slices when broadcast_input is non-zero
+ *   w (device) [n_slices][n] double (probability weights)
  *   cdf (device) [n_slices][bins+1]
  *   workspace (device) >= pr_restrict_weighted_workspace(n_slices, bins) bytes, 8-byte aligned
  */
 size_t pr_restrict_weighted_workspace(int32_t n_slices, int32_t bins);
-pr_status pr_restrict_weighted(pr_precision precision, const void* x, const double* w, int64_t n,
-                               int32_t n_slices, const pr_grid* grid, double* cdf, void* workspace,
+pr_status pr_restrict_weighted(pr_precision precision, const void* x, int32_t broadcast_input, const double* w,
+                               int64_t n, int32_t n_slices, const pr_grid* grid, double* cdf, void* workspace,
                                size_t workspace_bytes, void* stream);
 
 /*

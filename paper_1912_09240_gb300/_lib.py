@@ -171,7 +171,7 @@ def lib() -> ctypes.CDLL:
                               ctypes.c_size_t, vp]
     L.pr_restrict_weighted_workspace.argtypes = [i32, i32]
     L.pr_restrict_weighted_workspace.restype = ctypes.c_size_t
-    L.pr_restrict_weighted.argtypes = [i32, vp, vp, i64, i32, P(_Grid), vp, vp, ctypes.c_size_t, vp]
+    L.pr_restrict_weighted.argtypes = [i32, vp, i32, vp, i64, i32, P(_Grid), vp, vp, ctypes.c_size_t, vp]
     for name in EXPORTED:
         if name not in ("pr_status_string", "pr_version", "pr_set_particles_per_thread",
                         "pr_set_tiles_per_cta", "pr_set_update_cluster", "pr_fine_adjoint_workspace",
@@ -341,10 +341,12 @@ def pr_restrict_weighted_workspace(n_slices: int, bins: int) -> int:
     return lib().pr_restrict_weighted_workspace(n_slices, bins)
 
 
-def pr_restrict_weighted(precision: int, x, w, n: int, n_slices: int, grid: Grid, cdf, workspace, stream=None):
+def pr_restrict_weighted(precision: int, x, broadcast_input: bool, w, n: int, n_slices: int, grid: Grid, cdf,
+                         workspace, stream=None):
     g = grid.c()
     wbytes = workspace.numel() * workspace.element_size()
-    _check("pr_restrict_weighted", lib().pr_restrict_weighted(precision, _ptr(x), _ptr(w), n, n_slices,
+    _check("pr_restrict_weighted", lib().pr_restrict_weighted(precision, _ptr(x), int(bool(broadcast_input)),
+                                                              _ptr(w), n, n_slices,
                                                               ctypes.byref(g), _ptr(cdf), _ptr(workspace), wbytes,
                                                               _stream(stream)))
 

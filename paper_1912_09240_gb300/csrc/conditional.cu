@@ -246,8 +246,9 @@ select_gather_kernel(const uint64_t* __restrict__ C, const uint64_t* __restrict_
 
 template <typename T>
 __global__ void __launch_bounds__(kCondThreads)
-restrict_weighted_kernel(const T* __restrict__ x, const double* __restrict__ w, int64_t n, GridDev g, float lo_f,
-                         float inv_h_f, unsigned long long* __restrict__ hist_g, int64_t per_block)
+restrict_weighted_kernel(const T* __restrict__ x, int64_t in_stride, const double* __restrict__ w, int64_t n,
+                         GridDev g, float lo_f, float inv_h_f, unsigned long long* __restrict__ hist_g,
+                         int64_t per_block)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int I = g.bins;
@@ -258,7 +259,7 @@ restrict_weighted_kernel(const T* __restrict__ x, const double* __restrict__ w, 
     if (sizeof(T) == 4) build_thresholds(g, thr);
     __syncthreads();
     const BinF32 bf = make_bin_f32(thr, I, lo_f, inv_h_f);
-    const T* xs = x + (int64_t)s * n;
+    const T* xs = x + (int64_t)s * in_stride;
     const double* ws = w + (int64_t)s * n;
     const int64_t b = (int64_t)blockIdx.x * per_block, e = min(n, b + per_block);
     for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
@@ -443,9 +444,9 @@ extern "C" size_t pr_restrict_weighted_workspace(int32_t n_slices, int32_t bins)
     return al256((size_t)n_slices * bins * sizeof(unsigned long long));
 }
 
-extern "C" pr_status pr_restrict_weighted(pr_precision precision, const void* x, const double* w, int64_t n,
-                                          int32_t n_slices, const pr_grid* grid, double* cdf, void* workspace,
-                                          size_t workspace_bytes, void* stream)
+extern "C" pr_status pr_restrict_weighted(pr_precision precision, const void* x, int32_t broadcast_input,
+                                          const double* w, int64_t n, int32_t n_slices, const pr_grid* grid,
+                                          double* cdf, void* workspace, size_t workspace_bytes, void* stream)
 {
     if (precision != PR_F32 && precision != PR_F64) return PR_ERR_INVALID_ARG;
     if (!x || !w || !cdf || !workspace || !grid_ok(grid) || n < 1 || n_slices < 1 || n_slices > 65535)
@@ -461,14 +462,15 @@ extern "C" pr_status pr_restrict_weighted(pr_precision precision, const void* x,
     const size_t smem = al16c((size_t)I * 8) + al16c((size_t)(I + 1) * 4);
     const int64_t per = cond_range(n, n_slices, 16384, 2);
     dim3 gr((unsigned)((n + per - 1) / per), (unsigned)n_slices);
+    const int64_t stride = broadcast_input ? 0 : n;
     if (precision == PR_F32) {
         PR_TRY_CUDA(cond_smem(restrict_weighted_kernel<float>, smem));
-        restrict_weighted_kernel<float><<<gr, kCondThreads, smem, st>>>(static_cast<const float*>(x), w, n, g, lo_f,
-                                                                        inv_h_f, hist, per);
+        restrict_weighted_kernel<float><<<gr, kCondThreads, smem, st>>>(static_cast<const float*>(x), stride, w, n, g,
+                                                                        lo_f, inv_h_f, hist, per);
     } else {
         PR_TRY_CUDA(cond_smem(restrict_weighted_kernel<double>, smem));
-        restrict_weighted_kernel<double><<<gr, kCondThreads, smem, st>>>(static_cast<const double*>(x), w, n, g, lo_f,
-                                                                         inv_h_f, hist, per);
+        restrict_weighted_kernel<double><<<gr, kCondThreads, smem, st>>>(static_cast<const double*>(x), stride, w, n,
+                                                                         g, lo_f, inv_h_f, hist, per);
     }
     PR_CHECK_LAUNCH();
     weighted_cdf_kernel<<<n_slices, 256, 0, st>>>(hist, I, cdf);

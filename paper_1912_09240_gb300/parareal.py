@@ -27,6 +27,13 @@ fine(k, c+1), which reads the slice fine(k+1, c) overwrites).  Results are
 bit for bit those of the sequential mode.  ``join()`` (called by every
 accessor) makes the caller's stream wait for the outstanding work.
 
+Matching (``matching``): "quantile" (Section 5.1, fused into the fine
+launch), "resample" / "resample_det" (Section 5.2: reweighting of the prior
+ensemble to the target histogram, stratified resampling with uniform or
+u~ = 1/2 points, gather of the start states, then the fine launch in place),
+"reweight" (Section 5.2 without resampling: positions kept, weights carried
+by the ensembles, every restriction weighted).
+
 Graph mode (``graph=True``): iterations k >= 1 are replayed as one CUDA graph
 each (two graphs, one per binding of the double buffers), which removes the
 per-launch host cost that dominates small workloads.  In pipelined graph mode
@@ -40,11 +47,17 @@ import torch
 from . import _lib as L
 
 
+MATCHINGS = ("quantile", "resample", "resample_det", "reweight")
+
+
 class PararealSolver:
     def __init__(self, model: L.Model, grid: L.Grid, n: int, K: int, steps: int, dt: float,
                  precision: int = L.PR_F32, rng: L.Rng = L.Rng(), iterator: int = L.PR_ITER_QUANTILE,
                  qmode: int = L.PR_QMODE_TWO_SIDED, device: str = "cuda", stream=None, chunk: int = 0,
-                 graph: bool = False):
+                 graph: bool = False, matching: str = "quantile"):
+        if matching not in MATCHINGS:
+            raise ValueError(f"matching must be one of {MATCHINGS}")
+        self.matching = matching
         self.model, self.grid, self.n, self.K, self.steps, self.dt = model, grid, n, K, steps, dt
         self.precision, self.rng, self.iterator, self.qmode = precision, rng, iterator, qmode
         self.device = torch.device(device)
@@ -69,6 +82,16 @@ class PararealSolver:
         self.counts_e = z(K, I, dtype=torch.int32)
         self.chunk = int(chunk) if chunk and chunk < K else 0
         nch = (K + self.chunk - 1) // self.chunk if self.chunk else 1
+        # Section 5.2 matchings: weights of the start states (and of the
+        # priors, which carry them in "reweight" mode), per-stream scratch
+        self._ws = {}
+        if matching != "quantile":
+            self.w = z(K, n, dtype=f64)
+            self.w_uni = torch.full((n,), 1.0 / n, dtype=f64, device=self.device)
+            if matching == "reweight":
+                self.w_prev = z(K, n, dtype=f64)
+                self.w[0].copy_(self.w_uni)
+                self.w_prev[0].copy_(self.w_uni)
         self._status = z(nch, dtype=torch.int32)
         self.coarse = L.pr_coarse_create(model, grid, steps * dt, stream=self._s())
         self.k = 0
@@ -131,7 +154,12 @@ class PararealSolver:
         s = self._s()
         self.x0.copy_(x0.reshape(self.n))
         self.y0.copy_(y0.reshape(self.model.fast_dim, self.n))
-        L.pr_restrict(self.precision, self.x0, self.n, 1, self.grid, self.counts0, self.cdf0, stream=s)
+        if self.matching == "reweight":   # every restriction carries the weights (here 1/N)
+            L.pr_restrict_weighted(self.precision, self.x0, False, self.w_uni, self.n, 1, self.grid, self.cdf0,
+                                   self._scratch("wr", 0, L.pr_restrict_weighted_workspace(1, self.grid.bins)),
+                                   stream=s)
+        else:
+            L.pr_restrict(self.precision, self.x0, self.n, 1, self.grid, self.counts0, self.cdf0, stream=s)
         self.prior0.copy_(self.cdf0.expand(self.K, -1))
         L.pr_parareal_update(self.coarse, L.PR_ITER_NONE, self.qmode, self.K, self.cdf0, None, None,
                              self._rho, self._status[0], stream=s)
@@ -141,32 +169,80 @@ class PararealSolver:
             self._ev_upd = [None] * len(self._ev_upd)
 
     # -- one generic iteration ---------------------------------------------------
-    def _fine(self, a: int, b: int, first: bool, stream):
-        """Fine launches for slices [a, b) of this iteration on `stream`."""
-        n = self.n
+    def _scratch(self, kind: str, role: int, nbytes: int) -> torch.Tensor:
+        """Device scratch of a library call, one per kind and per stream role
+        (0: sequential; chunk parity in the pipelined schedule), kept."""
+        t = self._ws.get((kind, role))
+        if t is None or t.numel() < nbytes:
+            t = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.device)
+            self._ws[(kind, role)] = t
+        return t
+
+    def _fine(self, a: int, b: int, first: bool, stream, role: int = 0):
+        """Matching and fine launches for slices [a, b) of this iteration on `stream`."""
+        n, grid, prec = self.n, self.grid, self.precision
+        weighted = self.matching == "reweight"
+        span = self.chunk or self.K
         if a == 0:
-            L.pr_fine_propagate(self.model, self.precision, self.rng, self.x0, self.y0, True,
-                                self.xb[0], self.yb[0], n, 0, 1, self.steps, self.dt, self.grid,
-                                None, None, self.counts_s[0], self.start[0], self.counts_e[0],
-                                self.f_star[0], stream=stream)
-            self.launches += 3
+            if weighted:   # X_0 with its uniform weights; restrictions with the weights
+                wr = self._scratch("wr", role, L.pr_restrict_weighted_workspace(span, grid.bins))
+                L.pr_restrict_weighted(prec, self.x0, False, self.w_uni, n, 1, grid, self.start[0], wr, stream=stream)
+                L.pr_fine_propagate(self.model, prec, self.rng, self.x0, self.y0, True, self.xb[0], self.yb[0], n,
+                                    0, 1, self.steps, self.dt, stream=stream)
+                L.pr_restrict_weighted(prec, self.xb[0], False, self.w_uni, n, 1, grid, self.f_star[0], wr,
+                                       stream=stream)
+                self.launches += 5
+            else:
+                L.pr_fine_propagate(self.model, prec, self.rng, self.x0, self.y0, True,
+                                    self.xb[0], self.yb[0], n, 0, 1, self.steps, self.dt, grid,
+                                    None, None, self.counts_s[0], self.start[0], self.counts_e[0],
+                                    self.f_star[0], stream=stream)
+                self.launches += 3
             a = 1
         if b <= a:
             return
         if first:   # X_0^n = M(rho_0^n, X_0)
             src_x, src_y, bcast, prior = self.x0, self.y0, True, self.prior0[a - 1:b - 1]
+            w_prior = None
         else:       # X_k^n = M(rho_k^n, Xbar_{k-1}^n)
             src_x, src_y, bcast = self.xa[a - 1:b - 1], self.ya[a - 1:b - 1], False
             prior = self.f_star_prev[a - 1:b - 1]
+            w_prior = self.w_prev[a - 1:b - 1] if weighted else None
         ev = None
         if self.fine_events is not None and not self.chunk:
             ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             ev[0].record(stream)
-        L.pr_fine_propagate(self.model, self.precision, self.rng, src_x, src_y, bcast,
-                            self.xb[a:b], self.yb[a:b], n, a, b - a, self.steps, self.dt, self.grid,
-                            prior, self._rho[a:b], self.counts_s[a:b], self.start[a:b], self.counts_e[a:b],
-                            self.f_star[a:b], stream=stream)
-        self.launches += 3
+        S = b - a
+        if self.matching == "quantile":
+            # Section 5.1: the matching is fused into the fine launch's prologue
+            L.pr_fine_propagate(self.model, prec, self.rng, src_x, src_y, bcast,
+                                self.xb[a:b], self.yb[a:b], n, a, S, self.steps, self.dt, grid,
+                                prior, self._rho[a:b], self.counts_s[a:b], self.start[a:b], self.counts_e[a:b],
+                                self.f_star[a:b], stream=stream)
+            self.launches += 3
+        elif weighted:
+            # Section 5.2, reweighting only: positions unchanged, weights carried
+            wr = self._scratch("wr", role, L.pr_restrict_weighted_workspace(span, grid.bins))
+            L.pr_reweight(prec, src_x, bcast, w_prior, n, S, grid, prior, self._rho[a:b], self.w[a:b],
+                          stream=stream)
+            L.pr_restrict_weighted(prec, src_x, bcast, self.w[a:b], n, S, grid, self.start[a:b], wr, stream=stream)
+            L.pr_fine_propagate(self.model, prec, self.rng, src_x, src_y, bcast, self.xb[a:b], self.yb[a:b], n, a,
+                                S, self.steps, self.dt, stream=stream)
+            L.pr_restrict_weighted(prec, self.xb[a:b], False, self.w[a:b], n, S, grid, self.f_star[a:b], wr,
+                                   stream=stream)
+            self.launches += 7
+        else:
+            # Section 5.2 with resampling: reweight, resample into the start
+            # states (gather of x and y), then the fine launch in place
+            mode = L.PR_RESAMPLE_STRATIFIED if self.matching == "resample" else L.PR_RESAMPLE_DETERMINISTIC
+            rs = self._scratch("rs", role, L.pr_resample_workspace(n, span))
+            L.pr_reweight(prec, src_x, bcast, None, n, S, grid, prior, self._rho[a:b], self.w[a:b], stream=stream)
+            L.pr_resample(prec, self.model.fast_dim, src_x, src_y, bcast, self.w[a:b], n, S, a, mode, self.rng, None,
+                          self.xb[a:b], self.yb[a:b], rs, stream=stream)
+            L.pr_fine_propagate(self.model, prec, self.rng, self.xb[a:b], self.yb[a:b], False, self.xb[a:b],
+                                self.yb[a:b], n, a, S, self.steps, self.dt, grid, None, None, self.counts_s[a:b],
+                                self.start[a:b], self.counts_e[a:b], self.f_star[a:b], stream=stream)
+            self.launches += 8
         if ev is not None:
             ev[1].record(stream)
             self.fine_events.append(ev)
@@ -184,6 +260,8 @@ class PararealSolver:
         self.ya, self.yb = self.yb, self.ya
         self.f_star, self.f_star_prev = self.f_star_prev, self.f_star
         self._rho, self._rho_next = self._rho_next, self._rho
+        if self.matching == "reweight":
+            self.w, self.w_prev = self.w_prev, self.w
         self._swaps += 1
         self.k += 1
 
@@ -211,7 +289,7 @@ class PararealSolver:
                 for ev in (self._ev_upd[c], self._ev_fine[c + 1] if c + 1 < nch else None):
                     if ev is not None:
                         sf.wait_event(ev)
-            self._fine(a, b, first, sf)
+            self._fine(a, b, first, sf, role=c % 2)
             ef = torch.cuda.Event()
             ef.record(sf)
             new_fine[c] = ef
@@ -274,7 +352,13 @@ class PararealSolver:
                                 n, m, 1, self.steps, self.dt, stream=s)
         counts = torch.empty(K + 1, self.grid.bins, dtype=torch.int32, device=self.device)
         rho = torch.empty(K + 1, self.grid.bins + 1, dtype=torch.float64, device=self.device)
-        L.pr_restrict(self.precision, xs, n, K + 1, self.grid, counts, rho, stream=s)
+        if self.matching == "reweight":
+            wu = self.w_uni.expand(K + 1, n).contiguous()
+            L.pr_restrict_weighted(self.precision, xs, False, wu, n, K + 1, self.grid, rho,
+                                   self._scratch("wr_ref", 0, L.pr_restrict_weighted_workspace(K + 1, self.grid.bins)),
+                                   stream=s)
+        else:
+            L.pr_restrict(self.precision, xs, n, K + 1, self.grid, counts, rho, stream=s)
         return xs, ys, rho
 
     def w1_to(self, rho_ref: torch.Tensor) -> torch.Tensor:
@@ -287,3 +371,11 @@ class PararealSolver:
         X_k^n is their matching against rho_k)."""
         self.join()
         return self.xa, self.ya, self._rho
+
+    def weights(self):
+        """Weights carried by the fine end states (matching "reweight"; slice 0
+        and the other matchings: uniform 1/N)."""
+        self.join()
+        if self.matching == "reweight":
+            return self.w_prev
+        return None

@@ -127,9 +127,13 @@ def test_restrict_weighted_bit_exact(L, orc, prec):
     cdf = torch.empty(S, bins + 1, dtype=torch.float64, device=DEV)
     ws = torch.empty(L.pr_restrict_weighted_workspace(S, bins), dtype=torch.uint8, device=DEV)
     dt = torch.float32 if prec == 0 else torch.float64
-    L.pr_restrict_weighted(prec, _t(x, dt), _t(w), n, S, L.Grid(bins, -3.0, 3.0), cdf, ws)
+    L.pr_restrict_weighted(prec, _t(x, dt), False, _t(w), n, S, L.Grid(bins, -3.0, 3.0), cdf, ws)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(cdf.cpu().numpy(), ref)
+    # one shared ensemble, per-slice weights
+    L.pr_restrict_weighted(prec, _t(x[2], dt), True, _t(w), n, S, L.Grid(bins, -3.0, 3.0), cdf, ws)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(cdf.cpu().numpy(), orc.restrict_weighted(np.repeat(x[2:3], S, axis=0), w, og))
 
 
 def test_full_size_reweight_resample(L, orc):
