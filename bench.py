@@ -314,6 +314,64 @@ def _plain_leg(L, dev, stream, rank):
     return out
 
 
+def _matching_leg(L, dev, stream, rank, chunk, iters=10):
+    """The matchings of Sections 5.1 and 5.2 on the double-well workload:
+    time per pipelined iteration and max_n W1(rho_k^n, R X_serial^n) per
+    iteration (same random numbers), and the standalone reweighting and
+    resampling passes over 49 slices."""
+    import torch
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    w = WORKLOAD
+    model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    grid = L.Grid(w.bins, w.lo, w.hi)
+    x0, y0 = workloads.initial_ensemble(w)
+    x0t = torch.tensor(x0, dtype=torch.float32, device=dev)
+    y0t = torch.tensor(y0, dtype=torch.float32, device=dev)
+    out = {}
+    for matching in ("quantile", "resample", "resample_det", "reweight"):
+        sv = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                            rng=L.Rng(w.seed, rank), device=str(dev), chunk=chunk, matching=matching)
+        sv.set_initial(x0t, y0t)
+        _, _, rser = sv.serial_reference()
+        sv.w1_to(rser).max().item()
+        sv.set_initial(x0t, y0t)
+        times, w1s = [], []
+        for _ in range(iters):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sv.iterate()
+            sv.join()
+            e1.record(stream)
+            w1s.append(float(sv.w1_to(rser).max().item()))
+            times.append(e0.elapsed_time(e1))
+        k_star = next((k + 1 for k, v in enumerate(w1s) if v <= 1e-3), None)
+        out[matching] = {"iteration_ms": statistics.median(times[1:]), "max_w1_per_iteration": w1s,
+                         "iterations_to_w1_1e-3": k_star, "status": int(sv.status.item())}
+        sv.close()
+        del sv
+    # standalone Section 5.2 passes over the 49 non-initial slices
+    S, n = w.K - 1, w.N
+    xs = torch.tensor(np.tile(x0.astype(np.float32), (S, 1)), device=dev)
+    cdfs = torch.empty(S, w.bins + 1, dtype=torch.float64, device=dev)
+    cnt = torch.empty(S, w.bins, dtype=torch.int32, device=dev)
+    L.pr_restrict(L.PR_F32, xs, n, S, grid, cnt, cdfs)
+    tgt = torch.empty_like(cdfs)
+    L.pr_restrict(L.PR_F32, xs + 0.05, n, S, grid, cnt, tgt)
+    wts = torch.empty(S, n, dtype=torch.float64, device=dev)
+    t_rw = _ev_time(lambda r: L.pr_reweight(L.PR_F32, xs, False, None, n, S, grid, cdfs, tgt, wts, stream=stream),
+                    stream, 10)
+    ws = torch.empty(L.pr_resample_workspace(n, S), dtype=torch.uint8, device=dev)
+    xo = torch.empty_like(xs)
+    yo = torch.empty_like(xs).reshape(S, 1, n)
+    ys = xs.reshape(S, 1, n)
+    t_rs = _ev_time(lambda r: L.pr_resample(L.PR_F32, 1, xs, ys, False, wts, n, S, 1, L.PR_RESAMPLE_STRATIFIED,
+                                            L.Rng(0), None, xo, yo, ws, stream=stream), stream, 10)
+    out["standalone"] = {"slices": S, "particles": n, "reweight_ms": t_rw, "resample_gather_ms": t_rs,
+                         "reweight_particles_per_s": S * n / (t_rw / 1e3),
+                         "resample_particles_per_s": S * n / (t_rs / 1e3)}
+    return out
+
+
 def _adjoint_leg(L, dev, stream, rank, n=None):
     """Pathwise gradients of the adjoint workload (2^20 particles, 20 slices x
     1000 steps, checkpoints every 256 steps): the forward alone, the gradient
@@ -609,6 +667,7 @@ def run_ours(args):
 
     unfused = None if args.no_unfused else _unfused_leg(L, solver, w, stream, _peaks().get("hbm_gbs"))
     plain = None if args.no_plain else _plain_leg(L, dev, stream, rank)
+    matchings = None if args.no_matchings else _matching_leg(L, dev, stream, rank, args.chunk)
     adjoint = None if args.no_adjoint else _adjoint_leg(L, dev, stream, rank, n=args.adjoint_n)
     large = None
     if not args.no_large:
@@ -662,6 +721,7 @@ def run_ours(args):
         "batched": batched,
         "unfused": unfused,
         "plain_ou": plain,
+        "matchings": matchings,
         "adjoint": adjoint,
         "fast16": large,
     }
@@ -686,6 +746,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=5, help="slices per pipelined chunk (0: sequential)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-serving leg")
     ap.add_argument("--no-unfused", action="store_true", help="skip standalone restriction/matching/coarse timing")
+    ap.add_argument("--no-matchings", action="store_true", help="skip the comparison of the matchings")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain OU workload legs")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--adjoint-n", type=int, default=None, help="particles of the adjoint leg")
