@@ -27,7 +27,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
 
-MODEL_OU, MODEL_DOUBLE_WELL, MODEL_DW_MULTI = 0, 1, 2
+MODEL_OU, MODEL_DOUBLE_WELL, MODEL_DW_MULTI, MODEL_ADVECTION = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -101,6 +101,8 @@ class Model:
     kind 0: d_x F = x - lambda*y           (linear OU family)
     kind 1: d_x F = x^3 - x + lambda*y     (double well)
     kind 2: d_x F = x^3 - x + lambda*mean(y), y in R^d
+    kind 3: no microscopic model; the coarse potential Fbar(x) = x/eps (the
+            linear advection test of Section 6), diffusion 1/beta
     fast:   d_y G = y - x per component, E = 1; slow diffusion D = 1/beta.
     """
     kind: int
@@ -328,6 +330,8 @@ def effective_potential(model: Model, x):
     """Fbar(x) with Fbar(0) = 0, by averaging d_x F over phi(y; x) = N(x, 1)
     (Eq. Fbar; the fast OU has E[y | x] = x in every component)."""
     x = np.asarray(x, dtype=np.float64)
+    if model.kind == MODEL_ADVECTION:     # given directly (Section 6, linear advection case)
+        return x / model.eps
     if model.kind == MODEL_OU:
         return 0.5 * (1.0 - model.lam) * x * x
     return 0.25 * x ** 4 - 0.5 * (1.0 - model.lam) * x * x
@@ -516,3 +520,44 @@ def parareal(model: Model, grid: Grid, seed: int, x0, y0, K: int, steps: int, dt
         res.rho.append(rho.copy())
         res.w.append(W.copy())
     return res
+
+
+# --------------------------------------------------------------------------
+# Parareal with the discretised Fokker-Planck equation as both propagators
+# (Section 6, linear advection case): restriction and matching are the
+# identity, the iterator is not.
+# --------------------------------------------------------------------------
+
+def fp_parareal(grid: Grid, fine: Model, coarse: Model, rho0: np.ndarray, K: int, dT: float, iters: int,
+                iterator: int = ITER_QUANTILE, qmode: int = QMODE_TWO_SIDED) -> list:
+    """rho[k] = CDFs [K+1][I+1] of iterations k = 0..iters, with
+    rho_0^{n+1} = C rho_0^n and rho_{k+1}^{n+1} = J(C rho_{k+1}^n, F rho_k^n, C rho_k^n),
+    F = exp(A_fine dT), C = exp(A_coarse dT)."""
+    PF = coarse_propagator(fine, grid, dT)
+    PC = coarse_propagator(coarse, grid, dT)
+    rho = np.empty((K + 1, grid.bins + 1))
+    rho[0] = rho0
+    for n in range(K):
+        rho[n + 1] = coarse_apply(PC, rho[n])[0]
+    out = [rho.copy()]
+    for _k in range(iters):
+        f_star = coarse_apply(PF, rho[:K])
+        c_star = coarse_apply(PC, rho[:K])
+        new = np.empty_like(rho)
+        new[0] = rho0
+        for n in range(K):
+            a = coarse_apply(PC, new[n])[0]
+            new[n + 1] = iterate(grid, a, f_star[n], c_star[n], iterator, qmode)
+        rho = new
+        out.append(rho.copy())
+    return out
+
+
+def fp_serial(grid: Grid, fine: Model, rho0: np.ndarray, K: int, dT: float) -> np.ndarray:
+    """rho^n = F^n rho0, n = 0..K (the reference the parareal iterates reach)."""
+    PF = coarse_propagator(fine, grid, dT)
+    rho = np.empty((K + 1, grid.bins + 1))
+    rho[0] = rho0
+    for n in range(K):
+        rho[n + 1] = coarse_apply(PF, rho[n])[0]
+    return rho
