@@ -56,8 +56,16 @@ typedef enum { PR_F32 = 0, PR_F64 = 1 } pr_precision;
  * component, E = 1:
  *   PR_MODEL_OU          d_x F = x - lambda*y             (fast_dim = 1)
  *   PR_MODEL_DOUBLE_WELL d_x F = x^3 - x + lambda*y       (fast_dim = 1)
- *   PR_MODEL_DW_MULTI    d_x F = x^3 - x + lambda*mean(y) (fast_dim 1..16) */
-typedef enum { PR_MODEL_OU = 0, PR_MODEL_DOUBLE_WELL = 1, PR_MODEL_DW_MULTI = 2 } pr_model_kind;
+ *   PR_MODEL_DW_MULTI    d_x F = x^3 - x + lambda*mean(y) (fast_dim 1..16)
+ *   PR_MODEL_ADVECTION   no microscopic model (pr_coarse_create only): the coarse
+ *                        potential Fbar(x) = x/eps, diffusion 1/beta -- the linear
+ *                        advection case of Section 6 */
+typedef enum {
+    PR_MODEL_OU = 0,
+    PR_MODEL_DOUBLE_WELL = 1,
+    PR_MODEL_DW_MULTI = 2,
+    PR_MODEL_ADVECTION = 3
+} pr_model_kind;
 
 /* Iterators of Section 4: quantile (4.4), additive (4.1), multiplicative
  * (4.2), rotation (4.3); PR_ITER_NONE keeps the coarse result (the serial

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpr.so")
 
 PR_OK, PR_ERR_INVALID_ARG, PR_ERR_CUDA, PR_ERR_TIMEOUT, PR_ERR_UNSUPPORTED, PR_ERR_NOMEM, PR_ERR_NUMERIC = range(7)
 PR_F32, PR_F64 = 0, 1
-PR_MODEL_OU, PR_MODEL_DOUBLE_WELL, PR_MODEL_DW_MULTI = 0, 1, 2
+PR_MODEL_OU, PR_MODEL_DOUBLE_WELL, PR_MODEL_DW_MULTI, PR_MODEL_ADVECTION = 0, 1, 2, 3
 PR_ITER_QUANTILE, PR_ITER_ADD, PR_ITER_MULT, PR_ITER_ROT, PR_ITER_NONE = 0, 1, 2, 3, 4
 PR_QMODE_TWO_SIDED, PR_QMODE_MIDPOINT = 0, 1
 PR_RESAMPLE_STRATIFIED, PR_RESAMPLE_DETERMINISTIC = 0, 1

@@ -30,7 +30,7 @@ struct CoarseHandle {
 // Kernels
 // ---------------------------------------------------------------------------
 
-__global__ void assemble_generator_kernel(GridDev g, int kind, double lam, double beta, double tau_x,
+__global__ void assemble_generator_kernel(GridDev g, int kind, double lam, double beta, double eps, double tau_x,
                                           double slice_dt, double* __restrict__ A)
 {
     const int I = g.bins;
@@ -39,6 +39,7 @@ __global__ void assemble_generator_kernel(GridDev g, int kind, double lam, doubl
     const double Dbar = 1.0 / beta;
     // log rho_inf(x) = log(1/Dbar) - Fbar(x)/Dbar, Fbar the averaged potential
     auto fbar = [&](double x) {
+        if (kind == PR_MODEL_ADVECTION) return x / eps;   // given directly (linear advection case)
         return kind == PR_MODEL_OU ? 0.5 * (1.0 - lam) * x * x
                                    : 0.25 * x * x * x * x - 0.5 * (1.0 - lam) * x * x;
     };
@@ -239,8 +240,9 @@ extern "C" pr_status pr_coarse_create(const pr_model* model, const pr_grid* grid
                                       void** handle, void* stream)
 {
     if (!model || !grid_ok(grid) || !handle || !(slice_dt > 0.0) || !std::isfinite(slice_dt)) return PR_ERR_INVALID_ARG;
-    if (model->kind < PR_MODEL_OU || model->kind > PR_MODEL_DW_MULTI) return PR_ERR_INVALID_ARG;
+    if (model->kind < PR_MODEL_OU || model->kind > PR_MODEL_ADVECTION) return PR_ERR_INVALID_ARG;
     if (!(model->beta > 0.0) || !(model->tau_x > 0.0) || !std::isfinite(model->lambda)) return PR_ERR_INVALID_ARG;
+    if (model->kind == PR_MODEL_ADVECTION && !(model->eps > 0.0)) return PR_ERR_INVALID_ARG;
     *handle = nullptr;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int I = grid->bins;
@@ -259,7 +261,7 @@ extern "C" pr_status pr_coarse_create(const pr_model* model, const pr_grid* grid
     }
     const GridDev g = make_grid(*grid);
     assemble_generator_kernel<<<(I + 127) / 128, 128, 0, st>>>(g, model->kind, model->lambda, model->beta,
-                                                               model->tau_x, slice_dt, B);
+                                                               model->eps, model->tau_x, slice_dt, B);
     norm1_kernel<<<1, 256, 0, st>>>(B, I, nrm);
     double norm = 0.0;
     if (cudaMemcpyAsync(&norm, nrm, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
