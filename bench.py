@@ -372,6 +372,47 @@ def _matching_leg(L, dev, stream, rank, chunk, iters=10):
     return out
 
 
+def _advection_leg(L, dev, stream, iters=4):
+    """The linear advection case of Section 6: parareal with the Fokker-Planck
+    equation (potential x/eps, diffusion 1/beta, eps = beta = 1) as the fine
+    propagator and a biased one as the coarse propagator, 288 bins on
+    [-12, 6], 10 slices of 0.2, Gaussian start N(1, 0.5^2): max_n W1 against
+    the serial fine solution per iteration, for every iterator."""
+    import math
+    import torch
+    from paper_1912_09240_gb300.fp_parareal import FPParareal
+    bins, lo, hi, K, dT = 288, -12.0, 6.0, 10, 0.2
+    edges = np.array([lo + i * (hi - lo) / bins for i in range(bins + 1)])
+    c = np.array([0.5 * (1 + math.erf((v - 1.0) / (0.5 * math.sqrt(2)))) for v in edges])
+    cdf0 = torch.tensor((c - c[0]) / (c[-1] - c[0]), dtype=torch.float64, device=dev)
+    grid = L.Grid(bins, lo, hi)
+    fine = L.Model(L.PR_MODEL_ADVECTION, 1, 0.0, 1.0, 1.0)
+    cases = {"underdiffusive (beta~ = 2)": (1.0, 2.0), "advection (eps~ = 0.5)": (0.5, 1.0),
+             "overdiffusive (beta~ = 0.5)": (1.0, 0.5)}
+    names = {L.PR_ITER_QUANTILE: "quantile", L.PR_ITER_ADD: "add", L.PR_ITER_MULT: "mult", L.PR_ITER_ROT: "rot"}
+    out = {}
+    for label, (eps_c, beta_c) in cases.items():
+        row = {}
+        for it, nm in names.items():
+            fp = FPParareal(grid, fine, L.Model(L.PR_MODEL_ADVECTION, 1, 0.0, beta_c, eps_c), K, dT, iterator=it,
+                            device=str(dev))
+            fp.set_initial(cdf0)
+            ref = fp.serial_reference()
+            w1 = [float(fp.w1_to(ref).max().item())]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms = []
+            for _ in range(iters):
+                e0.record(stream)
+                fp.iterate()
+                e1.record(stream)
+                w1.append(float(fp.w1_to(ref).max().item()))
+                ms.append(e0.elapsed_time(e1))
+            row[nm] = {"max_w1_per_iteration": w1, "iteration_ms": statistics.median(ms)}
+            fp.close()
+        out[label] = row
+    return out
+
+
 def _adjoint_leg(L, dev, stream, rank, n=None):
     """Pathwise gradients of the adjoint workload (2^20 particles, 20 slices x
     1000 steps, checkpoints every 256 steps): the forward alone, the gradient
@@ -668,6 +709,7 @@ def run_ours(args):
     unfused = None if args.no_unfused else _unfused_leg(L, solver, w, stream, _peaks().get("hbm_gbs"))
     plain = None if args.no_plain else _plain_leg(L, dev, stream, rank)
     matchings = None if args.no_matchings else _matching_leg(L, dev, stream, rank, args.chunk)
+    advection = None if args.no_advection else _advection_leg(L, dev, stream)
     adjoint = None if args.no_adjoint else _adjoint_leg(L, dev, stream, rank, n=args.adjoint_n)
     large = None
     if not args.no_large:
@@ -722,6 +764,7 @@ def run_ours(args):
         "unfused": unfused,
         "plain_ou": plain,
         "matchings": matchings,
+        "advection": advection,
         "adjoint": adjoint,
         "fast16": large,
     }
@@ -746,6 +789,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=5, help="slices per pipelined chunk (0: sequential)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-serving leg")
     ap.add_argument("--no-unfused", action="store_true", help="skip standalone restriction/matching/coarse timing")
+    ap.add_argument("--no-advection", action="store_true", help="skip the linear advection case")
     ap.add_argument("--no-matchings", action="store_true", help="skip the comparison of the matchings")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain OU workload legs")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
