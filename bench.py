@@ -644,6 +644,26 @@ def run_ours(args):
                 "note": "W1 between the parareal macroscopic states and the restriction of the serial fine "
                         "solution with the same random numbers, max over slices; time includes the per-"
                         "iteration W1 reduction"}
+        # wall time per iteration as CUDA graph replays (pipelined chunks inside
+        # each graph), median of 10 after two warm-up iterations
+        gs = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                            rng=L.Rng(w.seed, rank), device=str(dev), chunk=args.chunk, graph=True)
+        gs.set_initial(x0t, y0t)
+        for _ in range(3):
+            gs.iterate()
+        torch.cuda.synchronize()
+        gt = []
+        for _ in range(10):
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            gs.iterate()
+            g1.record(stream)
+            g1.synchronize()
+            gt.append(g0.elapsed_time(g1))
+        gs.close()
+        del gs
+        conv["graph_iteration_ms_median"] = statistics.median(gt)
+        conv["time_to_target_graph_ms"] = (k_star * statistics.median(gt)) if k_star else None
         # FP32 against the plain FP64 path on a paired smaller run (2^16 particles, 10 slices, 3 iterations)
         ws_ = w.scaled(N=1 << 16, K=10, T=w.slice_dt * 10, iters=3)
         x0s, y0s = workloads.initial_ensemble(ws_)
