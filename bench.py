@@ -413,6 +413,77 @@ def _advection_leg(L, dev, stream, iters=4):
     return out
 
 
+def _studies_leg(L, dev, stream, rank, n=1 << 18, iters=12):
+    """The convergence studies of Section 6 (varying the time-scale separation;
+    scaling with the number of intervals) on the double-well family, T = 5,
+    dt = 1e-4, 512 bins: the L2 error of the slow variable's histogram at T,
+    sqrt(sum_i (rho_i - rho_ref,i)^2 / h), against a serial fine solution with
+    ten times the particles, per parareal iteration."""
+    import torch
+    from paper_1912_09240_gb300.parareal import PararealSolver
+
+    def reference_cdfs(w):
+        """CDFs [K+1][bins+1] of the serial fine solution with 10 N particles."""
+        nr = 10 * w.N
+        wr = w.scaled(N=nr)
+        x0 = workloads.initial_slow(wr)
+        model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+        grid = L.Grid(w.bins, w.lo, w.hi)
+        x = torch.tensor(x0, dtype=torch.float32, device=dev).reshape(1, nr)
+        y = x.reshape(1, 1, nr).clone()
+        cnt = torch.empty(1, w.bins, dtype=torch.int32, device=dev)
+        cdf = torch.empty(w.K + 1, w.bins + 1, dtype=torch.float64, device=dev)
+        L.pr_restrict(L.PR_F32, x, nr, 1, grid, cnt, cdf[0:1], stream=stream)
+        for s_ in range(w.K):
+            L.pr_fine_propagate(model, L.PR_F32, L.Rng(w.seed, rank), x, y, False, x, y, nr, s_, 1, w.steps,
+                                w.step_dt, stream=stream)
+            L.pr_restrict(L.PR_F32, x, nr, 1, grid, cnt, cdf[s_ + 1:s_ + 2], stream=stream)
+        return cdf
+
+    def errors(w, iterator, matching, ref):
+        model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+        grid = L.Grid(w.bins, w.lo, w.hi)
+        sv = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                            rng=L.Rng(w.seed, rank), device=str(dev), iterator=iterator, matching=matching)
+        x0 = torch.tensor(workloads.initial_slow(w), dtype=torch.float32, device=dev)
+        sv.set_initial(x0, x0.reshape(1, -1))
+        h = (w.hi - w.lo) / w.bins
+        mref = torch.diff(ref, dim=1)
+        w1 = torch.empty(w.K + 1, dtype=torch.float64, device=dev)
+        out = {"l2_at_T": [], "l2_max_over_slices": [], "w1_max_over_slices": []}
+        for k in range(iters + 1):
+            if k:
+                sv.iterate()
+            m = torch.diff(sv.rho, dim=1)
+            l2 = torch.sqrt(((m - mref) ** 2).sum(dim=1) / h)
+            L.pr_w1(grid, w.K + 1, sv.rho, ref, w1, stream=stream)
+            out["l2_at_T"].append(float(l2[w.K].item()))
+            out["l2_max_over_slices"].append(float(l2.max().item()))
+            out["w1_max_over_slices"].append(float(w1.max().item()))
+        sv.close()
+        return out
+
+    base = workloads.DOUBLE_WELL.scaled(N=n, T=5.0, dt=1e-4)
+    res = {"particles": n, "reference_particles": 10 * n, "T": 5.0, "dt": 1e-4,
+           "errors": "L2 of the densities sqrt(sum (rho_i - rho_ref,i)^2 / h) at T and max over slices; W1 max over "
+                     "slices; the 10N reference's first N particles share the parareal ensemble's noise"}
+    e1 = {}
+    for eps in (1e-1, 1e-2, 1e-3):
+        w = base.scaled(eps=eps, K=20)
+        ref = reference_cdfs(w)
+        e1[f"eps={eps:g}"] = {f"{it_name}/{m}": errors(w, it, m, ref)
+                              for it_name, it in (("quantile", L.PR_ITER_QUANTILE), ("add", L.PR_ITER_ADD))
+                              for m in ("quantile", "resample")}
+    res["time_scale_separation"] = e1
+    e2 = {}
+    for K in (20, 50, 100):
+        w = base.scaled(K=K)
+        ref = reference_cdfs(w)
+        e2[f"slices={K}"] = {f"quantile/{m}": errors(w, L.PR_ITER_QUANTILE, m, ref) for m in ("quantile", "resample")}
+    res["number_of_intervals"] = e2
+    return res
+
+
 def _adjoint_leg(L, dev, stream, rank, n=None):
     """Pathwise gradients of the adjoint workload (2^20 particles, 20 slices x
     1000 steps, checkpoints every 256 steps): the forward alone, the gradient
@@ -730,6 +801,7 @@ def run_ours(args):
     plain = None if args.no_plain else _plain_leg(L, dev, stream, rank)
     matchings = None if args.no_matchings else _matching_leg(L, dev, stream, rank, args.chunk)
     advection = None if args.no_advection else _advection_leg(L, dev, stream)
+    studies = None if args.no_studies else _studies_leg(L, dev, stream, rank)
     adjoint = None if args.no_adjoint else _adjoint_leg(L, dev, stream, rank, n=args.adjoint_n)
     large = None
     if not args.no_large:
@@ -785,6 +857,7 @@ def run_ours(args):
         "plain_ou": plain,
         "matchings": matchings,
         "advection": advection,
+        "studies": studies,
         "adjoint": adjoint,
         "fast16": large,
     }
@@ -809,6 +882,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=5, help="slices per pipelined chunk (0: sequential)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-serving leg")
     ap.add_argument("--no-unfused", action="store_true", help="skip standalone restriction/matching/coarse timing")
+    ap.add_argument("--no-studies", action="store_true", help="skip the convergence studies")
     ap.add_argument("--no-advection", action="store_true", help="skip the linear advection case")
     ap.add_argument("--no-matchings", action="store_true", help="skip the comparison of the matchings")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain OU workload legs")
