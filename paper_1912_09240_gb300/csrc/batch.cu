@@ -78,7 +78,7 @@ __host__ __device__ inline size_t batch_fine_smem(int max_bins)
 {
     const size_t a = ((size_t)(max_bins + 1) * 4 + 15) & ~(size_t)15;
     const size_t b = ((size_t)max_bins * 4 + 15) & ~(size_t)15;
-    return a + 2 * b + match_smem_bytes(max_bins);
+    return a + 2 * b + match_smem_bytes_f32(max_bins);
 }
 
 template <int PPT>
@@ -122,8 +122,8 @@ batch_fine_kernel(BatchFineArgs a)
             yin = a.ya + P.x_off + (int64_t)(s - 1) * n;
             prior = a.fprev + P.c_off + (int64_t)(s - 1) * (bins + 1);
         }
-        MatchSmem ms = carve_match_smem(mbase, bins);
-        if (do_match) build_match_table(P.g, thr, prior, a.rho + P.r_off + (int64_t)s * (bins + 1), ms);
+        MatchSmem ms = carve_match_smem_f32(mbase, bins, prior, a.rho + P.r_off + (int64_t)s * (bins + 1));
+        if (do_match) build_match_table(P.g, thr, ms);
         __syncthreads();
         const BinF32 bf = make_bin_f32(thr, bins, P.lo_f, P.inv_h_f);
         float* xout = a.xb + P.x_off + (int64_t)s * n;

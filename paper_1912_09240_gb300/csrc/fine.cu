@@ -79,19 +79,31 @@ struct FineSmem {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-inline FineSmem fine_smem_layout(int bins, bool any_grid, bool match)
+// Binary32 with matching: thresholds, the matching table, then its build
+// scratch, which the two histograms reuse once the table is built.  Binary64
+// (or no matching): thresholds, histograms, then the full matching scratch.
+inline FineSmem fine_smem_layout(int bins, bool any_grid, bool match, bool f32)
 {
     FineSmem L{0, 0, 0, 0, 0};
     if (!any_grid) return L;
     size_t off = 0;
     L.thr = off;
     off += align16((size_t)(bins + 1) * sizeof(float));
-    L.hs = off;
-    off += align16((size_t)bins * sizeof(uint32_t));
-    L.he = off;
-    off += align16((size_t)bins * sizeof(uint32_t));
-    L.match = off;
-    if (match) off += match_smem_bytes(bins);
+    const size_t hb = align16((size_t)bins * sizeof(uint32_t));
+    if (match && f32) {
+        L.match = off;
+        off += match_table_bytes(bins);
+        L.hs = off;
+        L.he = off + hb;
+        off += std::max(match_build_bytes_f32(bins), 2 * hb);
+    } else {
+        L.hs = off;
+        off += hb;
+        L.he = off;
+        off += hb;
+        L.match = off;
+        if (match) off += match_smem_bytes(bins);
+    }
     L.total = off;
     return L;
 }
@@ -130,14 +142,14 @@ fine_f32_d1_kernel(FineArgs a, FineSmemOffsets so, int flags)
     MatchSmem ms;
     if (any_grid) {
         build_thresholds(a.g, thr);
+        if (do_match) {   // the histograms reuse the table's build scratch afterwards
+            ms = carve_match_smem_f32(smem + so.match, bins, a.cdf_prior + (size_t)s * (bins + 1),
+                                      a.cdf_target + (size_t)s * (bins + 1));
+            build_match_table(a.g, thr, ms);
+        }
         for (int i = threadIdx.x; i < bins; i += blockDim.x) {
             hist_s[i] = 0u;
             hist_e[i] = 0u;
-        }
-        if (do_match) {
-            ms = carve_match_smem(smem + so.match, bins);
-            build_match_table(a.g, thr, a.cdf_prior + (size_t)s * (bins + 1),
-                              a.cdf_target + (size_t)s * (bins + 1), ms);
         }
         __syncthreads();
     }
@@ -182,14 +194,14 @@ fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
     MatchSmem ms;
     if (any_grid) {
         build_thresholds(a.g, thr);
+        if (do_match) {   // the histograms reuse the table's build scratch afterwards
+            ms = carve_match_smem_f32(smem + so.match, bins, a.cdf_prior + (size_t)s * (bins + 1),
+                                      a.cdf_target + (size_t)s * (bins + 1));
+            build_match_table(a.g, thr, ms);
+        }
         for (int i = threadIdx.x; i < bins; i += blockDim.x) {
             hist_s[i] = 0u;
             hist_e[i] = 0u;
-        }
-        if (do_match) {
-            ms = carve_match_smem(smem + so.match, bins);
-            build_match_table(a.g, thr, a.cdf_prior + (size_t)s * (bins + 1),
-                              a.cdf_target + (size_t)s * (bins + 1), ms);
         }
         __syncthreads();
     }
@@ -463,10 +475,11 @@ match_f32_kernel(const float* __restrict__ xp, float* __restrict__ xo, int64_t n
     extern __shared__ __align__(16) unsigned char smem[];
     const int bins = g.bins;
     float* thr = reinterpret_cast<float*>(smem);
-    MatchSmem ms = carve_match_smem(smem + align16((size_t)(bins + 1) * sizeof(float)), bins);
     const int s = blockIdx.y;
+    MatchSmem ms = carve_match_smem_f32(smem + align16((size_t)(bins + 1) * sizeof(float)), bins,
+                                        cp + (size_t)s * (bins + 1), ct + (size_t)s * (bins + 1));
     build_thresholds(g, thr);
-    build_match_table(g, thr, cp + (size_t)s * (bins + 1), ct + (size_t)s * (bins + 1), ms);
+    build_match_table(g, thr, ms);
     const BinF32 bf = make_bin_f32(thr, bins, lo_f, inv_h_f);
     const int64_t b = (int64_t)blockIdx.x * per_block;
     const int64_t e = min(n, b + per_block);
@@ -692,7 +705,7 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
     if (counts_start) PR_TRY_CUDA(cudaMemsetAsync(counts_start, 0, (size_t)n_slices * bins * 4, st));
     if (counts_end) PR_TRY_CUDA(cudaMemsetAsync(counts_end, 0, (size_t)n_slices * bins * 4, st));
 
-    const FineSmem L = fine_smem_layout(bins, any_grid, do_match);
+    const FineSmem L = fine_smem_layout(bins, any_grid, do_match, precision == PR_F32);
     FineSmemOffsets so{(unsigned)L.thr, (unsigned)L.hs, (unsigned)L.he, (unsigned)L.match};
     const int flags = (any_grid ? 1 : 0) | (do_match ? 2 : 0) | (counts_start ? 4 : 0) | (counts_end ? 8 : 0);
     pr_status rc = PR_OK;
@@ -816,7 +829,7 @@ extern "C" pr_status pr_match(pr_precision precision, const void* x_prior, void*
     const int64_t blocks_per_slice = (n + per_block - 1) / per_block;
     dim3 gr((unsigned)blocks_per_slice, (unsigned)n_slices);
     if (precision == PR_F32) {
-        const size_t smem = align16((size_t)(bins + 1) * 4) + match_smem_bytes(bins);
+        const size_t smem = align16((size_t)(bins + 1) * 4) + match_smem_bytes_f32(bins);
         PR_TRY_CUDA(set_smem(match_f32_kernel, smem));
         match_f32_kernel<<<gr, 1024, smem, st>>>(static_cast<const float*>(x_prior), static_cast<float*>(x_out), n, g,
                                                 (float)grid->x_lo, (float)(1.0 / g.h), cdf_prior, cdf_target, per_block);

@@ -59,7 +59,40 @@ __host__ __device__ inline size_t match_build_bytes(int bins)
 
 __host__ __device__ inline size_t match_smem_bytes(int bins) { return match_table_bytes(bins) + match_build_bytes(bins); }
 
+// The binary32 table reads the CDFs from global memory while it is built, so
+// its scratch holds only the integer arrays (nzpre, nzlist, jfirst, pstart,
+// scan scratch); callers may reuse that scratch once the table is built.
+__host__ __device__ inline size_t match_build_bytes_f32(int bins)
+{
+    const size_t I = (size_t)bins;
+    return ((I + 1 + I + I + I + 1 + 64) * sizeof(int) + 15) & ~(size_t)15;
+}
+
+__host__ __device__ inline size_t match_smem_bytes_f32(int bins)
+{
+    return match_table_bytes(bins) + match_build_bytes_f32(bins);
+}
+
 // `base` 16-byte aligned; the build scratch starts match_table_bytes(bins) after it.
+// Binary32 layout: the table, then the integer scratch; Cp and Ct point to
+// the CDFs in global memory.
+__device__ inline MatchSmem carve_match_smem_f32(unsigned char* base, int bins, const double* cp_g, const double* ct_g)
+{
+    const int I = bins;
+    MatchSmem m;
+    m.piece = reinterpret_cast<float4*>(base);
+    m.pst = reinterpret_cast<int2*>(m.piece + (2 * I + 1));
+    m.Cp = const_cast<double*>(cp_g);
+    m.Ct = const_cast<double*>(ct_g);
+    int* ip = reinterpret_cast<int*>(base + match_table_bytes(bins));
+    m.nzpre = ip;
+    m.nzlist = m.nzpre + (I + 1);
+    m.jfirst = m.nzlist + I;
+    m.pstart = m.jfirst + I;
+    m.scratch = m.pstart + (I + 1);
+    return m;
+}
+
 __device__ inline MatchSmem carve_match_smem(unsigned char* base, int bins)
 {
     const int I = bins;
@@ -146,15 +179,11 @@ __device__ __forceinline__ int target_bin(const double* Ct, const int* nzpre, co
 // Build the binary32 table for one slice.  All threads of the block call it.
 // thr[] (the binary32 thresholds of the grid) must be written by the block
 // before the call; it is read after the first barrier inside.
-__device__ inline void build_match_table(const GridDev& g, const float* thr, const double* __restrict__ cp_g,
-                                         const double* __restrict__ ct_g, MatchSmem& m)
+// m from carve_match_smem_f32: the CDFs are read where they are (global
+// memory, through the read-only cache).
+__device__ inline void build_match_table(const GridDev& g, const float* thr, MatchSmem& m)
 {
     const int I = g.bins;
-    for (int i = threadIdx.x; i <= I; i += blockDim.x) {
-        m.Cp[i] = cp_g[i];
-        m.Ct[i] = ct_g[i];
-    }
-    __syncthreads();
     // non-empty target bins (jfirst used as a temporary flag array)
     for (int j = threadIdx.x; j < I; j += blockDim.x)
         m.jfirst[j] = dkey(m.Ct[j + 1]) > dkey(m.Ct[j]) ? 1 : 0;
