@@ -78,3 +78,48 @@ def test_python_binding_raises(L):
     with pytest.raises(L.PrError) as e:
         L._check("pr_x", L.PR_ERR_NUMERIC)
     assert "PR_ERR_NUMERIC" in str(e.value)
+
+
+def test_invalid_arguments_rejected_on_host_conditional_and_advection(L):
+    """Section 5.2 entry points, the advection model and the workspace sizes:
+    rejected before any CUDA call."""
+    lib = L.lib()
+    r = L.Rng().c()
+    g = L.Grid(16, -1.0, 1.0).c()
+    fake = ctypes.c_void_p(0x1000)
+    # reweight: n = 0, missing CDF, bad precision, bad grid
+    assert lib.pr_reweight(0, fake, 0, None, 0, 1, ctypes.byref(g), fake, fake, fake, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_reweight(0, fake, 0, None, 10, 1, ctypes.byref(g), None, fake, fake, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_reweight(5, fake, 0, None, 10, 1, ctypes.byref(g), fake, fake, fake, None) == L.PR_ERR_INVALID_ARG
+    bad = L.Grid(0, -1.0, 1.0).c()
+    assert lib.pr_reweight(0, fake, 0, None, 10, 1, ctypes.byref(bad), fake, fake, fake, None) == L.PR_ERR_INVALID_ARG
+    # resample: workspace sizes grow with n and slices; bad mode; small, misaligned
+    # workspace; gather in place; n too large for 32-bit indices; fast_dim out of range
+    n = 5000
+    need = lib.pr_resample_workspace(n, 3)
+    assert need >= 3 * n * 8 and lib.pr_resample_workspace(0, 1) == 0
+    ws = ctypes.c_void_p(0x10000)
+    args = lambda mode, x_in, x_out, nn, wsb, d=1, wsp=ws: (0, d, x_in, fake, 0, fake, nn, 3, 0, mode, ctypes.byref(r),
+                                                            None, x_out, None, wsp, wsb, None)
+    assert lib.pr_resample(*args(7, fake, None, n, need)) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_resample(*args(0, fake, None, n, need - 1)) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_resample(*args(0, fake, None, n, need, wsp=ctypes.c_void_p(0x10008))) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_resample(*args(0, fake, fake, n, need)) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_resample(*args(0, fake, None, 1 << 33, 1 << 60)) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_resample(0, 17, fake, fake, 0, fake, n, 3, 0, 0, ctypes.byref(r), None, None, fake, ws, need,
+                           None) == L.PR_ERR_INVALID_ARG
+    # weighted restriction: too small a workspace
+    wneed = lib.pr_restrict_weighted_workspace(3, 16)
+    assert wneed >= 3 * 16 * 8
+    assert lib.pr_restrict_weighted(0, fake, 0, fake, 10, 3, ctypes.byref(g), fake, ws, wneed - 8,
+                                    None) == L.PR_ERR_INVALID_ARG
+    # the advection model has no microscopic dynamics and needs eps > 0
+    adv = L.Model(L.PR_MODEL_ADVECTION, 1, 0.0, 1.0, 1.0).c()
+    assert lib.pr_fine_propagate(ctypes.byref(adv), 0, ctypes.byref(r), fake, fake, 0, fake, fake, 10, 0, 1, 1,
+                                 1e-3, None, None, None, None, None, None, None, None) == L.PR_ERR_INVALID_ARG
+    adv0 = L.Model(L.PR_MODEL_ADVECTION, 1, 0.0, 1.0, 0.0).c()
+    h = ctypes.c_void_p()
+    assert lib.pr_coarse_create(ctypes.byref(adv0), ctypes.byref(g), 0.1, ctypes.byref(h), None) == L.PR_ERR_INVALID_ARG
+    # the update cluster knob accepts any value (unknown ones select 8)
+    lib.pr_set_update_cluster(3)
+    lib.pr_set_update_cluster(8)

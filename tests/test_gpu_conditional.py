@@ -158,3 +158,59 @@ def test_full_size_reweight_resample(L, orc):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(w.cpu().numpy(), w_ref)
     np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), idx_ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_reweight_target_outside_prior_support(L, orc, prec):
+    """Target mass only left of, only right of, and on both sides of the
+    prior's support (the relocation of Section 5.2's reweighting), with the
+    ensemble's own restriction as prior: bit for bit against the oracle, and
+    all the weight inside the prior's support."""
+    rng = np.random.default_rng(40 + prec)
+    bins, lo, hi, n = 96, -4.0, 4.0, 12289
+    og = orc.Grid(bins, lo, hi)
+    x = rng.normal(0.0, 0.3, (3, n))
+    if prec == 0:
+        x = x.astype(np.float32).astype(np.float64)
+    _, cp = orc.restrict(x, og)
+    e = og.edges()
+    m = np.zeros((3, bins))
+    m[0, e[:-1] < -2.0] = 1.0                      # left of the support only
+    m[1, e[1:] > 2.5] = 1.0                        # right of it only
+    m[2, (e[:-1] < -2.0) | (e[1:] > 2.5)] = 1.0    # both sides
+    m /= m.sum(axis=1, keepdims=True)
+    ct = np.concatenate([np.zeros((3, 1)), np.cumsum(m, axis=1)], axis=1)
+    ct[:, -1] = 1.0
+    ref = orc.reweight(x, og, cp, ct)
+    dt = torch.float32 if prec == 0 else torch.float64
+    out = torch.empty(3, n, dtype=torch.float64, device=DEV)
+    L.pr_reweight(prec, _t(x, dt), False, None, n, 3, L.Grid(bins, lo, hi), _t(cp), _t(ct), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    np.testing.assert_array_equal(got, ref)
+    np.testing.assert_allclose(got.sum(axis=1), 1.0, rtol=0, atol=1e-12)
+    # slice 0: every weight sits in the leftmost occupied bin, slice 1 in the rightmost
+    b = np.array([[orc.lib().or_bin(v, bins, lo, hi) for v in row] for row in x[:2]])
+    assert np.all(got[0][b[0] != b[0].min()] == 0) and np.all(got[1][b[1] != b[1].max()] == 0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_resample_zero_weight_slice(L, orc, mode):
+    """A slice with no weight at all keeps its particles (index j -> j) while
+    the slices beside it resample as the oracle does."""
+    rng = np.random.default_rng(50 + mode)
+    S, n = 3, 7001
+    w = rng.gamma(0.5, 1.0, (S, n))
+    w /= w.sum(axis=1, keepdims=True)
+    w[1] = 0.0
+    ref = orc.resample(w, mode, seed=12, slice_begin=3, problem=2)
+    idx = torch.empty(S, n, dtype=torch.int32, device=DEV)
+    x = torch.randn(S, n, dtype=torch.float32, device=DEV)
+    xo = torch.empty_like(x)
+    ws = torch.empty(L.pr_resample_workspace(n, S), dtype=torch.uint8, device=DEV)
+    L.pr_resample(0, 1, x, None, False, _t(w), n, S, 3, mode, L.Rng(12, 2), idx, xo, None, ws)
+    torch.cuda.synchronize()
+    got = idx.cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(got, ref)
+    np.testing.assert_array_equal(got[1], np.arange(n))
+    assert torch.equal(xo[1], x[1])

@@ -202,3 +202,35 @@ def test_resampled_pairs_are_prior_pairs(orc, matching):
     # the conditional slope of y on x is the prior's 2.0, not the one a move of x alone would give
     slope = np.polyfit(xs[0], ys[0][0], 1)[0]
     assert abs(slope - 2.0) < 0.02
+
+
+def test_target_outside_the_prior_support(orc):
+    """All target mass left of the prior's support lands in the prior's first
+    supported bin, all of it right of the support in its last: the factors are
+    then 1/rhobar there and 0 elsewhere (dyadic masses, exact)."""
+    g = orc.Grid(8, 0.0, 8.0)
+    prior = [0.0, 0.0, 0.0, 0.25, 0.5, 0.25, 0.0, 0.0]
+    left = [0.5, 0.25, 0.25, 0.0, 0.0, 0.0, 0.0, 0.0]
+    right = [0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.5, 0.5]
+    np.testing.assert_array_equal(orc.reweight_factors(g, _cdf(prior), _cdf(left)),
+                                  [0, 0, 0, 4.0, 0, 0, 0, 0])
+    np.testing.assert_array_equal(orc.reweight_factors(g, _cdf(prior), _cdf(right)),
+                                  [0, 0, 0, 0, 0, 4.0, 0, 0])
+    # the reweighted ensemble puts all its weight into that one bin
+    x = np.array([3.5] * 4 + [4.5] * 8 + [5.5] * 4)
+    w = orc.reweight(x[None], g, _cdf(prior)[None], _cdf(left)[None])[0]
+    np.testing.assert_array_equal(w, [0.25] * 4 + [0.0] * 12)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_resample_without_weight_is_the_identity(orc, mode):
+    """A slice whose weights are all zero (T = 0) keeps its particles; the
+    other slices are unaffected."""
+    rng = np.random.default_rng(8)
+    w = rng.random((3, 257))
+    w /= w.sum(axis=1, keepdims=True)
+    w[1] = 0.0
+    idx = orc.resample(w, mode, seed=3, slice_begin=2)
+    np.testing.assert_array_equal(idx[1], np.arange(257))
+    ref = orc.resample(w[[0, 2]], mode, seed=3, slice_begin=2)
+    np.testing.assert_array_equal(idx[0], ref[0])
