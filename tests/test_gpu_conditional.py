@@ -189,9 +189,11 @@ def test_reweight_target_outside_prior_support(L, orc, prec):
     got = out.cpu().numpy()
     np.testing.assert_array_equal(got, ref)
     np.testing.assert_allclose(got.sum(axis=1), 1.0, rtol=0, atol=1e-12)
-    # slice 0: every weight sits in the leftmost occupied bin, slice 1 in the rightmost
+    # slice 0: the weight sits in the leftmost occupied bin, slice 1 in the
+    # rightmost (up to the ulp of mass that C_I = 1 leaves in the last bin)
     b = np.array([[orc.lib().or_bin(v, bins, lo, hi) for v in row] for row in x[:2]])
-    assert np.all(got[0][b[0] != b[0].min()] == 0) and np.all(got[1][b[1] != b[1].max()] == 0)
+    assert got[0][b[0] != b[0].min()].sum() < 1e-14 and got[1][b[1] != b[1].max()].sum() < 1e-14
+    assert abs(got[0][b[0] == b[0].min()].sum() - 1.0) < 1e-12
 
 
 @pytest.mark.parametrize("mode", [0, 1])
@@ -214,3 +216,86 @@ def test_resample_zero_weight_slice(L, orc, mode):
     np.testing.assert_array_equal(got, ref)
     np.testing.assert_array_equal(got[1], np.arange(n))
     assert torch.equal(xo[1], x[1])
+
+
+def test_weight_fixed_point_rounding(L, orc):
+    """The device's fixed point round(w 2^61) (integer arithmetic on the
+    binary64 encoding) on crafted weights -- exact ties, one ulp either side,
+    subnormals, signed zeros, negative values -- each alone in its bin of a
+    weighted restriction whose total stays small, so that every fixed value
+    shows in the CDF: bit for bit against the oracle, and the bin sums
+    recovered from the CDF equal the exact rational rounding."""
+    from _fixed_point import crafted_weights, fixed_exact
+    w = crafted_weights()
+    bins = len(w)
+    og = orc.Grid(bins, 0.0, float(bins))
+    x = np.arange(bins, dtype=np.float64) + 0.5
+    ref = orc.restrict_weighted(x[None], w[None], og)
+    fx = [fixed_exact(v) for v in w]
+    T = sum(fx)
+    assert T < 2 ** 52
+    cdf = torch.empty(1, bins + 1, dtype=torch.float64, device=DEV)
+    ws = torch.empty(L.pr_restrict_weighted_workspace(1, bins), dtype=torch.uint8, device=DEV)
+    for prec, dt in ((0, torch.float32), (1, torch.float64)):
+        L.pr_restrict_weighted(prec, _t(x[None], dt), False, _t(w[None]), bins, 1, L.Grid(bins, 0.0, float(bins)),
+                               cdf, ws)
+        torch.cuda.synchronize()
+        got = cdf.cpu().numpy()
+        np.testing.assert_array_equal(got, ref)
+        below = np.rint(got[0] * T).astype(np.int64)
+        np.testing.assert_array_equal(np.diff(below), fx)
+
+
+@pytest.mark.parametrize("bins", [1, 5, 600, 4096])
+def test_reweight_sparse_prior_support(L, orc, bins):
+    """A prior supported on a scattered third of the bins (runs of empty bins
+    of every length, empty bins at both ends) against a dense target: every
+    unsupported target bin is relocated; bit for bit against the oracle for
+    grids smaller and larger than the block."""
+    rng = np.random.default_rng(60 + bins)
+    lo, hi, n, S = -2.0, 2.0, 30011, 2
+    og = orc.Grid(bins, lo, hi)
+    e = og.edges()
+    keep = rng.random(bins) < 0.33
+    keep[rng.integers(bins)] = True
+    centres = 0.5 * (e[:-1] + e[1:])[keep]
+    x = rng.choice(centres, size=(S, n)) + (rng.random((S, n)) - 0.5) * 0.5 * (hi - lo) / bins
+    x = x.astype(np.float32).astype(np.float64)
+    _, cp = orc.restrict(x, og)
+    m = rng.random((S, bins)) + 0.01
+    m /= m.sum(axis=1, keepdims=True)
+    ct = np.concatenate([np.zeros((S, 1)), np.cumsum(m, axis=1)], axis=1)
+    ct[:, -1] = 1.0
+    ref = orc.reweight(x, og, cp, ct)
+    out = torch.empty(S, n, dtype=torch.float64, device=DEV)
+    L.pr_reweight(0, _t(x, torch.float32), False, None, n, S, L.Grid(bins, lo, hi), _t(cp), _t(ct), out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), ref)
+    np.testing.assert_allclose(out.cpu().numpy().sum(axis=1), 1.0, rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("pattern", ["sparse", "heavy", "runs"])
+def test_resample_concentrated_weights(L, orc, mode, pattern):
+    """Weights that stretch one block of outputs over many particles (weight on
+    every 37th particle only: ranges far beyond what a block stages), that
+    send most outputs to one particle, and long runs of zero weight between
+    dense stretches: every index bit for bit against the oracle."""
+    rng = np.random.default_rng({"sparse": 70, "heavy": 71, "runs": 72}[pattern] + 10 * mode)
+    S, n = 3, 100003
+    w = np.zeros((S, n))
+    if pattern == "sparse":
+        w[:, ::37] = rng.random((S, len(range(0, n, 37)))) + 0.1
+    elif pattern == "heavy":
+        w[:] = rng.random((S, n)) * 1e-3
+        w[np.arange(S), rng.integers(n, size=S)] = 50.0
+    else:
+        on = (np.arange(n) // 9001) % 3 == 1
+        w[:, on] = rng.random((S, on.sum()))
+    w /= w.sum(axis=1, keepdims=True)
+    ref = orc.resample(w, mode, seed=31, slice_begin=4, problem=3)
+    idx = torch.empty(S, n, dtype=torch.int32, device=DEV)
+    ws = torch.empty(L.pr_resample_workspace(n, S), dtype=torch.uint8, device=DEV)
+    L.pr_resample(0, 1, None, None, False, _t(w), n, S, 4, mode, L.Rng(31, 3), idx, None, None, ws)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), ref)

@@ -234,3 +234,11 @@ def test_resample_without_weight_is_the_identity(orc, mode):
     np.testing.assert_array_equal(idx[1], np.arange(257))
     ref = orc.resample(w[[0, 2]], mode, seed=3, slice_begin=2)
     np.testing.assert_array_equal(idx[0], ref[0])
+
+
+def test_weight_fixed_rounds_to_nearest_even(orc):
+    """The fixed point against exact rational arithmetic (ties to even)."""
+    from _fixed_point import crafted_weights, fixed_exact
+    for w in list(crafted_weights()) + [1.0, 0.5, 0.75, 1.0 / 3.0, 2.0 ** -61, 3.9]:
+        assert orc.weight_fixed(w) == fixed_exact(w), w
+    assert [orc.weight_fixed((2 * k + 1) * 2.0 ** -62) for k in range(4)] == [0, 2, 2, 4]
