@@ -329,10 +329,12 @@ pr_status pr_iterate(pr_iterator iterator, pr_quantile_mode qmode, const pr_grid
  * pass takes exactly the steps and random numbers of pr_fine_propagate over
  * slices slice_begin .. slice_begin + n_slices - 1 in sequence (slice s + 1
  * starting where slice s ended), storing (x, y) every ckpt_every steps in
- * the workspace; the backward pass replays each checkpoint segment (leaving
- * sub-checkpoints every 12 steps in the workspace), replays each 12-step
- * block once more into shared memory and runs the adjoint recursion over it,
- * accumulating in FP64.
+ * the workspace; the backward pass replays each checkpoint segment up to the
+ * start of its last 12-step block (leaving sub-checkpoints every 12 steps in
+ * the workspace), replays each 12-step block once more into shared memory and
+ * runs the adjoint recursion over it, accumulating in FP64.  ckpt_every = 12
+ * trades memory (8 n B per 12 steps) for one replay less: the backward pass
+ * is then a single replay.
  *   x0, y0      (device) [n] float start states
  *   x_T, y_T    (device) [n] float end states, or NULL
  *   xbar_T      (device) [n] double dL/dX_T per particle, or NULL

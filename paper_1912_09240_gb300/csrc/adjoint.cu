@@ -12,7 +12,10 @@
 // replayed once from its checkpoint to leave sub-checkpoints every 12 steps in
 // a scratch area of the workspace (16 B per particle per 12 steps); each
 // 12-step block is then replayed once more, keeping its states and noise
-// increments in shared memory, and the adjoint recursion
+// increments in shared memory (the first replay stops at the start of the
+// segment's last block, whose end state is never needed: with checkpoints
+// every 12 steps the backward pass is a single replay), and the adjoint
+// recursion
 //   lbar_t = J_t^T lbar_{t+1},  g += lbar_{t+1} . d(step_t)/d theta
 // runs backwards over the block.  Per-block partial sums are binary32; they
 // are added into binary64 accumulators per particle, and the ensemble sum is
@@ -218,6 +221,7 @@ adjoint_kernel(AdjArgs a)
             for (int j = 0; j < nsub; ++j) {
                 a.sub_buf[(int64_t)(2 * j) * a.n + p] = x;
                 a.sub_buf[(int64_t)(2 * j + 1) * a.n + p] = y;
+                if (j == nsub - 1) break;   // the last block's end state is not needed
                 const int len = min(kSub, L - j * kSub);
                 for (int i = 0; i < len; ++i) {
                     float q, cc, s;
@@ -311,6 +315,7 @@ adjoint_paired_kernel(AdjArgs a)
             for (int j = 0; j < nsub; ++j) {
                 a.sub_buf[(int64_t)(2 * j) * a.n + p] = x;
                 a.sub_buf[(int64_t)(2 * j + 1) * a.n + p] = y;
+                if (j == nsub - 1) break;   // the last block's end state is not needed
                 const int len = min(kSub, L - j * kSub);
                 for (int i = 0; i < len; i += 2) {
                     pair(slice, m, x, y);

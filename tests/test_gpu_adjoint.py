@@ -31,7 +31,8 @@ def _close(a, b, rel, abs_=0.0):
 
 
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("slices,steps,ckpt", [(3, 40, 32), (2, 125, 256), (1, 1, 256), (4, 7, 5)])
+@pytest.mark.parametrize("slices,steps,ckpt", [(3, 40, 32), (2, 125, 256), (1, 1, 256), (4, 7, 5), (3, 40, 12), (2, 31, 12),
+                                               (2, 50, 2), (1, 50, 3), (2, 48, 24)])
 def test_per_particle_against_tangent(L, orc, kind, slices, steps, ckpt):
     rng = np.random.default_rng(kind + steps)
     n, dt = 1000, 1e-3
