@@ -355,6 +355,26 @@ pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, const float*
                           void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * pr_fine_adjoint for an observable L = sum_p (seed_scale / 2 (X_T^p)^2 +
+ * seed_shift X_T^p), whose seed dL/dX_T^p = seed_scale X_T^p + seed_shift
+ * depends only on the particle's own end state (not in the paper; the second
+ * moment E[X_T^2] = (1/n) sum_p (X_T^p)^2 is seed_scale = 2/n, seed_shift = 0,
+ * the mean is seed_scale = 0, seed_shift = 1/n).  The seed is taken inside the
+ * adjoint after its forward pass, in binary64 and then rounded to binary32
+ * as pr_fine_adjoint rounds a given xbar_T: the gradient is bit for bit that
+ * of pr_fine_adjoint with xbar_T computed from the end states, without the
+ * separate forward pass that computing them would take.  dL/dY_T = 0.
+ *   seed_scale, seed_shift  finite (PR_ERR_INVALID_ARG otherwise)
+ *   grad        (device) [3] = dL/d(lambda, beta, eps), fixed summation order
+ *   other arguments as pr_fine_adjoint (same workspace size)
+ */
+pr_status pr_fine_adjoint_affine(const pr_model* model, const pr_rng* rng, const float* x0, const float* y0,
+                                 int64_t n, int32_t slice_begin, int32_t n_slices, int32_t steps, double dt,
+                                 int32_t ckpt_every, double seed_scale, double seed_shift, float* x_T,
+                                 float* y_T, double* grad, double* xbar_0, double* ybar_0, void* workspace,
+                                 size_t workspace_bytes, void* stream);
+
+/*
  * pr_fine_adjoint without any device allocation by the library or the
  * caller.  The paper has no counterpart: this serves callers that cannot
  * allocate device memory while they run -- a real-time control loop that

@@ -25,7 +25,7 @@ EXPORTED = (
     "pr_status_string", "pr_version", "pr_rng_words", "pr_fine_propagate", "pr_set_particles_per_thread",
     "pr_set_tiles_per_cta", "pr_set_update_cluster", "pr_restrict", "pr_counts_to_cdf", "pr_match", "pr_coarse_create", "pr_coarse_destroy",
     "pr_coarse_matrix", "pr_coarse_fp", "pr_parareal_update", "pr_iterate", "pr_w1",
-    "pr_fine_adjoint_workspace", "pr_fine_adjoint", "pr_order_statistics_workspace", "pr_order_statistics",
+    "pr_fine_adjoint_workspace", "pr_fine_adjoint", "pr_fine_adjoint_affine", "pr_order_statistics_workspace", "pr_order_statistics",
     "pr_fine_adjoint_noalloc_capacity", "pr_fine_adjoint_noalloc",
     "pr_batch_create", "pr_batch_destroy", "pr_batch_particle_steps", "pr_batch_set_initial", "pr_batch_iterate",
     "pr_batch_rho", "pr_batch_fine_state", "pr_batch_status", "pr_batch_set_config", "pr_batch_get_config",
@@ -145,6 +145,8 @@ def lib() -> ctypes.CDLL:
     L.pr_fine_adjoint_workspace.restype = ctypes.c_size_t
     L.pr_fine_adjoint.argtypes = [P(_Model), P(_Rng), vp, vp, i64, i32, i32, i32, d, i32, vp, vp, vp, vp, vp,
                                   vp, vp, vp, ctypes.c_size_t, vp]
+    L.pr_fine_adjoint_affine.argtypes = [P(_Model), P(_Rng), vp, vp, i64, i32, i32, i32, d, i32, d, d, vp, vp, vp,
+                                         vp, vp, vp, ctypes.c_size_t, vp]
     L.pr_order_statistics_workspace.argtypes = [i64]
     L.pr_order_statistics_workspace.restype = ctypes.c_size_t
     L.pr_order_statistics.argtypes = [vp, i64, vp, i32, vp, vp, ctypes.c_size_t, vp]
@@ -309,6 +311,18 @@ def pr_fine_adjoint(model: Model, rng: Rng, x0, y0, n: int, slice_begin: int, n_
                                                     _ptr(y_T), _ptr(xbar_T), _ptr(ybar_T), _ptr(grad),
                                                     _ptr(xbar_0), _ptr(ybar_0), _ptr(workspace), wbytes,
                                                     _stream(stream)))
+
+
+def pr_fine_adjoint_affine(model: Model, rng: Rng, x0, y0, n: int, slice_begin: int, n_slices: int, steps: int,
+                           dt: float, ckpt_every: int, seed_scale: float, seed_shift: float, x_T, y_T, grad, xbar_0,
+                           ybar_0, workspace, stream=None):
+    m, r = model.c(), rng.c()
+    wbytes = workspace.numel() * workspace.element_size()
+    _check("pr_fine_adjoint_affine",
+           lib().pr_fine_adjoint_affine(ctypes.byref(m), ctypes.byref(r), _ptr(x0), _ptr(y0), n, slice_begin, n_slices,
+                                        steps, dt, ckpt_every, float(seed_scale), float(seed_shift), _ptr(x_T),
+                                        _ptr(y_T), _ptr(grad), _ptr(xbar_0), _ptr(ybar_0), _ptr(workspace), wbytes,
+                                        _stream(stream)))
 
 
 def pr_order_statistics_workspace(n: int) -> int:

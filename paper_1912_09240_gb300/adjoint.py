@@ -68,22 +68,17 @@ def fine_em(theta, x0, y0, kind, tau_x, rng, slice_begin, n_slices, steps, dt, c
 
 def second_moment_gradient(model: L.Model, rng: L.Rng, x0, y0, slice_begin: int, n_slices: int, steps: int,
                            dt: float, ckpt_every: int = 256):
-    """E[X_T^2] = mean_p X_T^2 and its gradient with respect to (lambda, beta, eps), in one adjoint pass
-    (the forward pass of the adjoint gives X_T; the seeds 2 X_T / N need X_T first, so the
-    forward runs once on its own)."""
+    """E[X_T^2] = mean_p X_T^2 and its gradient with respect to (lambda, beta, eps), in one adjoint pass:
+    the seeds 2 X_T^p / N depend only on each particle's own end state, so the adjoint takes them
+    after its own forward pass (pr_fine_adjoint_affine)."""
     n = x0.numel()
     dev = x0.device
-    x = x0.reshape(1, n).to(torch.float32).clone()
-    y = y0.reshape(1, 1, n).to(torch.float32).clone()
-    for s in range(n_slices):
-        L.pr_fine_propagate(model, L.PR_F32, rng, x, y, False, x, y, n, slice_begin + s, 1, steps, dt)
-    xT = x.reshape(n)
-    seeds = (2.0 / n) * xT.to(torch.float64)
+    xT = torch.empty(n, dtype=torch.float32, device=dev)
     grad = torch.zeros(3, dtype=torch.float64, device=dev)
     ws = _workspace(L.pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every), dev)
-    L.pr_fine_adjoint(model, rng, x0.reshape(n).to(torch.float32).contiguous(),
-                      y0.reshape(n).to(torch.float32).contiguous(), n, slice_begin, n_slices, steps, dt,
-                      ckpt_every, None, None, seeds, None, grad, None, None, ws)
+    L.pr_fine_adjoint_affine(model, rng, x0.reshape(n).to(torch.float32).contiguous(),
+                             y0.reshape(n).to(torch.float32).contiguous(), n, slice_begin, n_slices, steps, dt,
+                             ckpt_every, 2.0 / n, 0.0, xT, None, grad, None, None, ws)
     value = (xT.to(torch.float64) ** 2).mean()
     return value, grad
 

@@ -60,7 +60,17 @@ struct AdjArgs {
     double* grad_pp;          // [n][3] in per-particle mode
     double* xbar0;
     double* ybar0;
+    int seed_affine;          // seeds dL/dX_T = seed_scale X_T + seed_shift from the particle's own end state
+    double seed_scale, seed_shift;
 };
+
+// dL/dX_T of particle p with end state xT: given per particle, affine in xT,
+// or 1 (per-particle mode)
+__device__ __forceinline__ float seed_of(const AdjArgs& a, int64_t p, float xT)
+{
+    if (a.seed_affine) return (float)__dadd_rn(__dmul_rn(a.seed_scale, (double)xT), a.seed_shift);
+    return a.xbar ? (float)a.xbar[p] : 1.0f;
+}
 
 // Walks the steps in order; step m of slice s uses words 2(m&1), 2(m&1)+1 of
 // the Philox block (m >> 1, p, slice_begin + s, problem << 8).
@@ -209,7 +219,7 @@ adjoint_kernel(AdjArgs a)
         if (a.yT) a.yT[p] = y;
 
         // ---- backward ----
-        lx = a.xbar ? (float)a.xbar[p] : 1.0f;
+        lx = seed_of(a, p, x);
         ly = a.ybar ? (float)a.ybar[p] : 0.0f;
         for (int64_t c = a.n_ckpt - 1; c >= 0; --c) {
             const int64_t t0 = c * a.ckpt;
@@ -303,7 +313,7 @@ adjoint_paired_kernel(AdjArgs a)
         if (a.yT) a.yT[p] = y;
 
         // ---- backward ----
-        lx = a.xbar ? (float)a.xbar[p] : 1.0f;
+        lx = seed_of(a, p, x);
         ly = a.ybar ? (float)a.ybar[p] : 0.0f;
         for (int64_t c = a.n_ckpt - 1; c >= 0; --c) {
             const int64_t t0 = c * a.ckpt;
@@ -473,7 +483,8 @@ static pr_status adjoint_launch(const pr_model* model, const pr_rng* rng, const 
                                 int64_t n, int32_t slice_begin, int32_t n_slices, int32_t steps, double dt,
                                 int32_t ckpt_every, float* x_T, float* y_T, const double* xbar_T,
                                 const double* ybar_T, double* grad, double* xbar_0, double* ybar_0, void* ws,
-                                cudaStream_t st)
+                                cudaStream_t st, int seed_affine = 0, double seed_scale = 0.0,
+                                double seed_shift = 0.0)
 {
     const AdjLayout l = adjoint_layout(n, n_slices, steps, ckpt_every);
     AdjArgs a{};
@@ -502,7 +513,10 @@ static pr_status adjoint_launch(const pr_model* model, const pr_rng* rng, const 
     char* base = static_cast<char*>(ws);
     a.ckpt_buf = reinterpret_cast<float*>(base);
     a.sub_buf = reinterpret_cast<float*>(base + l.ckpt_bytes);
-    const bool sum_mode = xbar_T != nullptr;
+    const bool sum_mode = xbar_T != nullptr || seed_affine;
+    a.seed_affine = seed_affine;
+    a.seed_scale = seed_scale;
+    a.seed_shift = seed_shift;
     a.partial = sum_mode ? reinterpret_cast<double*>(base + l.ckpt_bytes + l.sub_bytes) : nullptr;
     a.xT = x_T;
     a.yT = y_T;
@@ -552,6 +566,24 @@ extern "C" pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, c
     if (workspace_bytes < need || ((uintptr_t)workspace & 255)) return PR_ERR_INVALID_ARG;
     return adjoint_launch(model, rng, x0, y0, n, slice_begin, n_slices, steps, dt, ckpt_every, x_T, y_T, xbar_T,
                           ybar_T, grad, xbar_0, ybar_0, workspace, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pr_status pr_fine_adjoint_affine(const pr_model* model, const pr_rng* rng, const float* x0,
+                                            const float* y0, int64_t n, int32_t slice_begin, int32_t n_slices,
+                                            int32_t steps, double dt, int32_t ckpt_every, double seed_scale,
+                                            double seed_shift, float* x_T, float* y_T, double* grad,
+                                            double* xbar_0, double* ybar_0, void* workspace,
+                                            size_t workspace_bytes, void* stream)
+{
+    const pr_status chk = adjoint_check(model, rng, x0, y0, n, slice_begin, n_slices, steps, dt, ckpt_every,
+                                        nullptr, nullptr, grad);
+    if (chk != PR_OK) return chk;
+    if (!isfinite(seed_scale) || !isfinite(seed_shift) || !workspace) return PR_ERR_INVALID_ARG;
+    const size_t need = pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every);
+    if (workspace_bytes < need || ((uintptr_t)workspace & 255)) return PR_ERR_INVALID_ARG;
+    return adjoint_launch(model, rng, x0, y0, n, slice_begin, n_slices, steps, dt, ckpt_every, x_T, y_T, nullptr,
+                          nullptr, grad, xbar_0, ybar_0, workspace, static_cast<cudaStream_t>(stream), 1, seed_scale,
+                          seed_shift);
 }
 
 extern "C" size_t pr_order_statistics_workspace(int64_t n)

@@ -123,3 +123,19 @@ def test_invalid_arguments_rejected_on_host_conditional_and_advection(L):
     # the update cluster knob accepts any value (unknown ones select 8)
     lib.pr_set_update_cluster(3)
     lib.pr_set_update_cluster(8)
+
+
+def test_affine_adjoint_rejects_non_finite_seeds(L):
+    lib = L.lib()
+    m = L.Model(L.PR_MODEL_OU).c()
+    r = L.Rng().c()
+    fake = ctypes.c_void_p(0x1000)
+    ws = ctypes.c_void_p(0x100000)
+    need = lib.pr_fine_adjoint_workspace(100, 2, 10, 12)
+    for sc, sh in ((float("nan"), 0.0), (1.0, float("inf"))):
+        assert lib.pr_fine_adjoint_affine(ctypes.byref(m), ctypes.byref(r), fake, fake, 100, 0, 2, 10, 1e-3, 12, sc, sh,
+                                          None, None, fake, None, None, ws, need, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_fine_adjoint_affine(ctypes.byref(m), ctypes.byref(r), fake, fake, 100, 0, 2, 10, 1e-3, 12, 1.0, 0.0,
+                                      None, None, None, None, None, ws, need, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_fine_adjoint_affine(ctypes.byref(m), ctypes.byref(r), fake, fake, 100, 0, 2, 10, 1e-3, 12, 1.0, 0.0,
+                                      None, None, fake, None, None, ws, need - 1, None) == L.PR_ERR_INVALID_ARG

@@ -200,3 +200,37 @@ def test_adjoint_workload_sampled_at_full_size(L, orc):
             assert abs(Q[j] - X[i]) <= 2e-3 * max(abs(X[i]), 1.0)
             for k in range(3):
                 assert abs(dq[j, k] - dX[i, k]) <= 2e-3 * max(abs(dX[i, k]), rms[k]), (j, k, dq[j, k], dX[i, k])
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("steps,ckpt", [(40, 12), (31, 5), (100, 256)])
+@pytest.mark.parametrize("scale,shift", [(None, 0.0), (0.3, -0.7), (0.0, None)])
+def test_affine_seed_equals_given_seeds(L, kind, steps, ckpt, scale, shift):
+    """pr_fine_adjoint_affine against pr_fine_adjoint with the seeds
+    scale X_T + shift computed from the end states (scale = 2/n: the second
+    moment; scale = 0, shift = 1/n: the mean): the gradient, the end states
+    and the initial-state sensitivities bit for bit."""
+    n, slices, dt = 3001, 3, 1e-3
+    scale = 2.0 / n if scale is None else scale
+    shift = 1.0 / n if shift is None else shift
+    lam, beta, eps = (1.0, 1.0, 0.1) if kind == 0 else (0.5, 3.0, 0.05)
+    rng = np.random.default_rng(steps + kind)
+    x0 = torch.tensor(rng.normal(0.5, 0.4, n), dtype=torch.float32, device="cuda")
+    y0 = torch.tensor(rng.normal(0.0, 1.0, n), dtype=torch.float32, device="cuda")
+    m, r = L.Model(kind, 1, lam, beta, eps), L.Rng(21, 4)
+    ws = torch.empty(L.pr_fine_adjoint_workspace(n, slices, steps, ckpt), dtype=torch.uint8, device="cuda")
+    xT = torch.empty(n, dtype=torch.float32, device="cuda")
+    g1 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    xb1 = torch.empty(n, dtype=torch.float64, device="cuda")
+    yb1 = torch.empty(n, dtype=torch.float64, device="cuda")
+    L.pr_fine_adjoint_affine(m, r, x0, y0, n, 2, slices, steps, dt, ckpt, scale, shift, xT, None, g1, xb1, yb1, ws)
+    seeds = scale * xT.to(torch.float64) + shift
+    g0 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    xT0 = torch.empty(n, dtype=torch.float32, device="cuda")
+    xb0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    yb0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    L.pr_fine_adjoint(m, r, x0, y0, n, 2, slices, steps, dt, ckpt, xT0, None, seeds, None, g0, xb0, yb0, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(xT, xT0)
+    assert torch.equal(g1, g0), (g1, g0)
+    assert torch.equal(xb1, xb0) and torch.equal(yb1, yb0)
