@@ -43,7 +43,7 @@ INST_PER_PARTICLE_STEP = 41.42
 # particles, inputs larger than L2, scaled by particle-slices to the full
 # launch; profiles/fine_f32_d1_double_well.md); the algorithmic figure is
 # 16 B (x and y read once and written once, binary32).
-TRAFFIC_BYTES_PER_PARTICLE_SLICE = 13.77
+TRAFFIC_BYTES_PER_PARTICLE_SLICE = 13.73
 SMS = 152
 ISSUE_LANES_PER_SM_CLK = 4 * 32       # 4 sub-partitions x one 32-wide warp instruction per clock
 
