@@ -222,27 +222,37 @@ fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
     if (do_hs && ok) atomicAdd(&hist_s[bin_fast_f32(bf, thr, x)], 1u);
 
     const float lam = a.lam_f, ddt = a.drift_dt_f, rel = a.relax_f;
-    const float sx = a.sx_f, sy = a.sy_f;
+    const float sxk = a.sxk_f, syk = a.syk_f, omr = 1.0f - rel;
     const float invD = 1.0f / (float)D;
     constexpr int Q = 1 + D;
     constexpr int PAIRS = (Q + 1) / 2;
     constexpr int G = (PAIRS + 1) / 2;
     const uint32_t k0 = a.k0, k1 = a.k1, chi = a.ctr_hi, pid = (uint32_t)p;
     for (int m = 0; m < a.steps; ++m) {
-        float z[2 * PAIRS];
+        // normal 2i is sqrt(2 ln 2) q_i cos(theta_i), normal 2i + 1 the sine;
+        // sqrt(2 ln 2) is folded into the amplitudes sxk, syk
+        float q[PAIRS], c[PAIRS], sn[PAIRS];
 #pragma unroll
         for (int gi = 0; gi < G; ++gi) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)m, pid, slice, chi | (uint32_t)gi), k0, k1);
-            box_muller_f32(w.x, w.y, z[4 * gi], z[4 * gi + 1]);
-            if (2 * gi + 1 < PAIRS) box_muller_f32(w.z, w.w, z[4 * gi + 2], z[4 * gi + 3]);
+            box_muller_qcs(w.x, w.y, q[2 * gi], c[2 * gi], sn[2 * gi]);
+            if (2 * gi + 1 < PAIRS) box_muller_qcs(w.z, w.w, q[2 * gi + 1], c[2 * gi + 1], sn[2 * gi + 1]);
         }
         float ysum = 0.0f;
 #pragma unroll
         for (int j = 0; j < D; ++j) ysum += y[j];
         const float f = slow_force<KIND>(x, ysum * invD, lam);
-        const float xn = fmaf(sx, z[0], fmaf(-f, ddt, x));
+        const float xn = fmaf(sxk * q[0], c[0], fmaf(-f, ddt, x));
+        // y_j <- y_j + (x - y_j) rel + sy dV_j, as y_j (1 - rel) + x rel + sy dV_j
+        const float xr = x * rel;
+        float amp[PAIRS];
 #pragma unroll
-        for (int j = 0; j < D; ++j) y[j] = fmaf(sy, z[1 + j], fmaf(x - y[j], rel, y[j]));
+        for (int i = 0; i < PAIRS; ++i) amp[i] = syk * q[i];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const int k = 1 + j;   // the normal of component j
+            y[j] = fmaf(amp[k >> 1], (k & 1) ? sn[k >> 1] : c[k >> 1], fmaf(y[j], omr, xr));
+        }
         x = xn;
     }
     if (ok) {
