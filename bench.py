@@ -525,10 +525,12 @@ def _adjoint_leg(L, dev, stream, rank, n=None):
     # checkpoints every 12 steps (the replay block): more memory, one replay less
     t_g12, (val12, grad12) = timed(lambda: second_moment_gradient(model, rng, gx0, gy0, 0, w.K, w.steps, w.step_dt,
                                                                    ckpt_every=12))
+    t_q12, _ = timed(lambda: quantile_gradient(model, rng, gx0, gy0, 0, w.K, w.steps, w.step_dt, ckpt_every=12))
     ps = w.N * w.K * w.steps
     return {"workload": w.name, "particle_steps": ps,
             "forward_ms": t_f, "second_moment_grad_ms": t_g, "quantile_grad_ms": t_q,
             "second_moment_grad_ms_ckpt12": t_g12,
+            "quantile_grad_ms_ckpt12": t_q12,
             "ckpt12_workspace_bytes": L.pr_fine_adjoint_workspace(w.N, w.K, w.steps, 12),
             "ckpt12_grad_max_rel_diff": float(((grad12 - grad).abs() / grad.abs().clamp_min(1e-300)).max().item()),
             "forward_particle_steps_per_s": ps / (t_f / 1e3),
