@@ -503,9 +503,10 @@ __device__ __forceinline__ Idx sel_gallop(const V& v, Idx a, Idx hi, uint64_t u)
 
 __device__ __forceinline__ int sel_pad(int i) { return i + (i >> 5); }
 
-// A thread's kSelPer consecutive outputs from jj0 on: a search for the
-// first, then a gallop from the previous particle; the particles, relative
-// to `base`, go to sp.
+// A thread's kSelPer consecutive outputs from jj0 on: their strata points
+// first (independent Philox blocks, all in flight), then a search for the
+// first particle and a gallop from the previous one for the rest; the
+// particles, relative to `base`, go to sp.
 template <typename V, typename Idx>
 __device__ __forceinline__ void select_run(const V& v, Idx base, Idx hi, const StrataPoint& U, uint32_t j0,
                                            int jj0, int cnt, uint32_t* sp)
@@ -513,13 +514,36 @@ __device__ __forceinline__ void select_run(const V& v, Idx base, Idx hi, const S
     const uint32_t j = j0 + (uint32_t)jj0;
     uint32_t q2, r2;
     U.divmod_Rj(j, q2, r2);
-    Idx p = base;
-    for (int k = 0; k < kSelPer && jj0 + k < cnt; ++k) {
-        const uint64_t u = U.at(j + (uint32_t)k, q2, r2);
-        p = k == 0 ? sel_search(v, base, hi, u) : sel_gallop(v, p, hi, u);
-        sp[sel_pad(jj0 + k)] = (uint32_t)(p - base);
+    uint64_t u[kSelPer];
+#pragma unroll
+    for (int k = 0; k < kSelPer; ++k) {
+        u[k] = U.at(j + (uint32_t)k, q2, r2);   // past the end: unused
         U.step(q2, r2);
     }
+    const int m = min(kSelPer, cnt - jj0);
+    Idx p = sel_search(v, base, hi, u[0]);
+    sp[sel_pad(jj0)] = (uint32_t)(p - base);
+#pragma unroll
+    for (int k = 1; k < kSelPer; ++k) {
+        if (k < m) {
+            p = sel_gallop(v, p, hi, u[k]);
+            sp[sel_pad(jj0 + k)] = (uint32_t)(p - base);
+        }
+    }
+}
+
+// Copies rows[j] = src[p_j] for the kSelPer outputs of this thread, all loads
+// issued before the stores.
+template <typename T>
+__device__ __forceinline__ void gather_rows(const T* __restrict__ src, T* __restrict__ dst, const int64_t* pv,
+                                            const int64_t* jv, int valid)
+{
+    T v[kSelPer];
+#pragma unroll
+    for (int k = 0; k < kSelPer; ++k) v[k] = k < valid ? src[pv[k]] : T(0);
+#pragma unroll
+    for (int k = 0; k < kSelPer; ++k)
+        if (k < valid) dst[jv[k]] = v[k];
 }
 
 // One CTA takes kSelOut consecutive outputs, whose particles lie between
@@ -571,14 +595,26 @@ select_gather_kernel(const uint64_t* __restrict__ C, const uint64_t* __restrict_
         for (int jj = threadIdx.x; jj < cnt; jj += kSelThreads) sp[sel_pad(jj)] = (uint32_t)jj;
     }
     __syncthreads();
-    const int64_t si = broadcast ? 0 : s;   // the input slice (one shared by all with broadcast)
-    for (int jj = threadIdx.x; jj < cnt; jj += kSelThreads) {
-        const int64_t j = j0 + jj, p = lo + sp[sel_pad(jj)];
-        if (idx) idx[(int64_t)s * n + j] = (uint32_t)p;
-        if (x_out) x_out[(int64_t)s * n + j] = x_in[si * n + p];
-        if (y_out)
-            for (int c = 0; c < d; ++c) y_out[((int64_t)s * d + c) * n + j] = y_in[(si * d + c) * n + p];
+    // output jj = threadIdx.x + k kSelThreads of this CTA
+    const int valid = max(0, min(kSelPer, (cnt - (int)threadIdx.x + kSelThreads - 1) / kSelThreads));
+    int64_t pv[kSelPer], jv[kSelPer];
+#pragma unroll
+    for (int k = 0; k < kSelPer; ++k) {
+        const int jj = threadIdx.x + k * kSelThreads;
+        pv[k] = k < valid ? lo + sp[sel_pad(jj)] : 0;
+        jv[k] = j0 + jj;
     }
+    const int64_t si = broadcast ? 0 : s;   // the input slice (one shared by all with broadcast)
+    if (idx) {
+        uint32_t* o = idx + (int64_t)s * n;
+#pragma unroll
+        for (int k = 0; k < kSelPer; ++k)
+            if (k < valid) o[jv[k]] = (uint32_t)pv[k];
+    }
+    if (x_out) gather_rows(x_in + si * n, x_out + (int64_t)s * n, pv, jv, valid);
+    if (y_out)
+        for (int c = 0; c < d; ++c)
+            gather_rows(y_in + (si * d + c) * n, y_out + ((int64_t)s * d + c) * n, pv, jv, valid);
 }
 
 // ---------------------------------------------------------------------------
