@@ -39,15 +39,13 @@ constexpr int kCondThreads = 512;
 __device__ __forceinline__ uint64_t weight_fixed(double w)
 {
     const uint64_t b = (uint64_t)__double_as_longlong(w);
-    if ((int64_t)b <= 0) return 0ull;                       // +0, or the sign bit set
-    const int E = (int)(b >> 52);
-    if (E == 0) return 0ull;                                // subnormal: below 2^-961
-    if (E == 2047) return (b << 12) ? 0ull : ~0ull;         // NaN; +inf saturates
+    const uint32_t hi = (uint32_t)(b >> 32);
+    if ((int32_t)hi < 0) return 0ull;                       // the sign bit set (negative, -0, NaN with sign)
+    const int k = 1014 - (int)(hi >> 20);                    // w 2^61 = M 2^-k
+    if (k > 53) return 0ull;                                 // below 1/2, +0 and subnormals included
+    if (k < -11) return (b << 12) && (hi >> 20) == 2047 ? 0ull : ~0ull;   // w >= 8 saturates; NaN -> 0
     const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = E - 1014;
-    if (sh >= 0) return sh > 11 ? ~0ull : M << sh;          // exact below 2^64
-    const int k = -sh;
-    if (k > 53) return 0ull;                                // below 1/2
+    if (k <= 0) return M << -k;                              // exact below 2^64
     return (M + ((1ull << (k - 1)) - 1ull) + ((M >> k) & 1ull)) >> k;
 }
 
