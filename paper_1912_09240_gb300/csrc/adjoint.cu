@@ -110,12 +110,19 @@ struct NoiseWalker {
 // One block of the adjoint recursion, backwards over `len` steps whose states
 // and noise increments are in shared memory:
 //   lbar_t = J_t^T lbar_{t+1},  g += lbar_{t+1} . d(step_t)/d theta.
-template <int KIND>
+// LEN > 0: a full block of LEN steps, the loop unrolled (fixed shared-memory
+// offsets); LEN = 0: `len` steps.
+template <int KIND, int LEN = 0>
 __device__ __forceinline__ void backward_block(const AdjArgs& a, int len, int T, int tid, const float* bx,
                                                const float* by, const float* bnx, const float* bny, float& lx,
                                                float& ly, double& g0, double& g1, double& g2)
 {
+    if (LEN > 0) {
+        len = LEN;
+        T = kAdjThreads;
+    }
     float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
+#pragma unroll
     for (int i = len - 1; i >= 0; --i) {
         const float xi = bx[i * T + tid], yi = by[i * T + tid];
         const float nx = bnx[i * T + tid], ny = bny[i * T + tid];
@@ -340,27 +347,35 @@ adjoint_paired_kernel(AdjArgs a)
                 const int64_t tb = t0 + (int64_t)j * kSub;
                 slice = (int)(tb / S);
                 m = (int)(tb - (int64_t)slice * S);
-                for (int i = 0; i < len; i += 2) {
+                // steps i, i + 1 of the block: states and noise increments to shared memory
+                auto replay_pair = [&](int i, int Ts) {
                     const uint4 w = philox4x32_10(
                         make_uint4((uint32_t)(m >> 1), pid, (uint32_t)(a.slice_begin + slice), a.chi), a.k0, a.k1);
                     float q0, c0, s0, q1, c1, s1;
                     box_muller_qcs(w.x, w.y, q0, c0, s0);
                     box_muller_qcs(w.z, w.w, q1, c1, s1);
                     const float ax0 = q0 * sxk, ay0 = q0 * syk, ax1 = q1 * sxk, ay1 = q1 * syk;
-                    bx[i * T + tid] = x;
-                    by[i * T + tid] = y;
-                    bnx[i * T + tid] = ax0 * c0;
-                    bny[i * T + tid] = ay0 * s0;
+                    bx[i * Ts + tid] = x;
+                    by[i * Ts + tid] = y;
+                    bnx[i * Ts + tid] = ax0 * c0;
+                    bny[i * Ts + tid] = ay0 * s0;
                     em_step_f32<KIND>(x, y, ax0, c0, ay0, s0, lam, ddt, rel);
-                    bx[(i + 1) * T + tid] = x;
-                    by[(i + 1) * T + tid] = y;
-                    bnx[(i + 1) * T + tid] = ax1 * c1;
-                    bny[(i + 1) * T + tid] = ay1 * s1;
+                    bx[(i + 1) * Ts + tid] = x;
+                    by[(i + 1) * Ts + tid] = y;
+                    bnx[(i + 1) * Ts + tid] = ax1 * c1;
+                    bny[(i + 1) * Ts + tid] = ay1 * s1;
                     em_step_f32<KIND>(x, y, ax1, c1, ay1, s1, lam, ddt, rel);
                     m += 2;
                     if (m == S) { m = 0; ++slice; }
+                };
+                if (len == kSub) {
+#pragma unroll
+                    for (int i = 0; i < kSub; i += 2) replay_pair(i, kAdjThreads);
+                    backward_block<KIND, kSub>(a, len, T, tid, bx, by, bnx, bny, lx, ly, g0, g1, g2);
+                } else {
+                    for (int i = 0; i < len; i += 2) replay_pair(i, T);
+                    backward_block<KIND>(a, len, T, tid, bx, by, bnx, bny, lx, ly, g0, g1, g2);
                 }
-                backward_block<KIND>(a, len, T, tid, bx, by, bnx, bny, lx, ly, g0, g1, g2);
             }
         }
         store_outputs(a, p, lx, ly, g0, g1, g2);
