@@ -36,12 +36,12 @@ WORKLOAD = workloads.DOUBLE_WELL
 # Thread-instructions issued per particle-step by the binary32 fine kernel
 # (d = 1, 4 particles per thread): ncu smsp__inst_issued.sum x 32 over the
 # particle-steps of the launch, double-well workload at 2^16 particles x 9
-# slices x 1000 steps (profiles/fine_f32_d1_double_well.md).
+# slices x 1000 steps.
 INST_PER_PARTICLE_STEP = 41.42
 # DRAM bytes per particle per slice of that kernel, read + write (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of the 9-slice launch at 2^21
 # particles, inputs larger than L2, scaled by particle-slices to the full
-# launch; profiles/fine_f32_d1_double_well.md); the algorithmic figure is
+# launch); the algorithmic figure is
 # 16 B (x and y read once and written once, binary32).
 TRAFFIC_BYTES_PER_PARTICLE_SLICE = 13.73
 SMS = 152

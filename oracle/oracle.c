@@ -10,8 +10,8 @@
  * separation: a numerical study", arXiv:1912.09240) in its own order and
  * notation, in double precision, with no blocking, fusion or reordering.
  *
- * Readings of passages that are silent or garbled are listed in the design doc
- * ("Readings of the paper") and repeated at the function they affect.
+ * Where the paper is silent or garbled, the reading taken is stated at the
+ * function it affects.
  *
  * Compile with -ffp-contract=off so that no multiply-add is fused: every
  * operation below is one IEEE-754 double operation, identical on x86-64 and
