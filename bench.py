@@ -183,7 +183,7 @@ def run_reference(args):
     orc.build()
     om = orc.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
     x0, y0 = workloads.initial_ensemble(w)
-    n = 1 << 15
+    n = min(1 << 15, w.N)
     for _ in range(args.warmup):
         orc.fine_propagate(om, w.seed, x0[None, :n], y0[None, :, :n], 1, 20, w.step_dt)
     times = []
