@@ -231,29 +231,32 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPer = 8;                              // elements per thread
 constexpr int kScanBlock = kScanThreads * kScanPer;      // elements per block
 
-// Sum of the fixed weights of each block of kScanBlock elements.
+// Sum of the fixed weights of each block of kScanBlock elements, one warp
+// per block (kScanWarps blocks per CTA, no block-wide synchronisation).
+constexpr int kScanWarps = kScanThreads / 32;
+
 __global__ void __launch_bounds__(kScanThreads)
 fixed_blocksum_kernel(const double* __restrict__ w, int64_t n, int64_t nblk, uint64_t* __restrict__ bsum)
 {
-    __shared__ uint64_t wsum[kScanThreads / 32];
-    const int s = blockIdx.y;
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    const int s = blockIdx.y, lane = threadIdx.x & 31;
+    const int64_t blk = (int64_t)blockIdx.x * kScanWarps + (threadIdx.x >> 5);
+    if (blk >= nblk) return;
     const double* ws = w + (int64_t)s * n;
+    const int64_t b0 = blk * kScanBlock;
     uint64_t loc = 0;
+    for (int c = 0; c < kScanBlock; c += 8 * 32) {
+        double v[8];
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        const int64_t p = base + (int64_t)k * kScanThreads;
-        if (p < n) loc += weight_fixed(__ldcs(ws + p));
+        for (int k = 0; k < 8; ++k) {
+            const int64_t p = b0 + c + k * 32 + lane;
+            v[k] = p < n ? __ldcs(ws + p) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) loc += weight_fixed(v[k]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = loc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t t = 0;
-        for (int k = 0; k < kScanThreads / 32; ++k) t += wsum[k];
-        bsum[(int64_t)s * nblk + blockIdx.x] = t;
-    }
+    if (lane == 0) bsum[(int64_t)s * nblk + blk] = loc;
 }
 
 // Exclusive scan of the block sums of each slice (one CTA per slice); the
@@ -289,58 +292,63 @@ scan_blocks_kernel(uint64_t* __restrict__ bsum, int64_t nblk, uint64_t* __restri
     if (threadIdx.x == T - 1) total[s] = run;
 }
 
-// C_p: the weights are read again and the block's inclusive scan is added to
-// its offset.  Thread t of a block takes the kScanPer consecutive elements
-// t * kScanPer ..; loads and stores are staged through shared memory (one pad
-// word per kScanPer, so that a thread's run and its neighbours' sit in
-// distinct banks) and stay coalesced.
-__device__ __forceinline__ int scan_pad(int i) { return i + i / kScanPer; }
+// C_p: the weights are read again and each block's inclusive scan is added
+// to its offset, one warp per block in chunks of 256 elements.  In a chunk,
+// lane l scans the 8 consecutive elements 8l .. 8l+7; loads and stores stay
+// coalesced through a warp-private stage in shared memory (one pad word per 8,
+// so that a lane's run and its neighbours' sit in distinct banks).
+constexpr int kScanChunk = 8 * 32;
+
+__device__ __forceinline__ int scan_pad(int i) { return i + i / 8; }
 
 __global__ void __launch_bounds__(kScanThreads)
 scan_within_kernel(const double* __restrict__ w, uint64_t* __restrict__ C, int64_t n, int64_t nblk,
                    const uint64_t* __restrict__ boff)
 {
-    __shared__ uint64_t stage[kScanBlock + kScanBlock / kScanPer];
-    __shared__ uint64_t wtot[kScanThreads / 32];
-    const int s = blockIdx.y;
-    const int64_t b0 = (int64_t)blockIdx.x * kScanBlock;
+    __shared__ uint64_t stage_all[kScanWarps][kScanChunk + kScanChunk / 8];
+    const int s = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t blk = (int64_t)blockIdx.x * kScanWarps + warp;
+    if (blk >= nblk) return;
+    uint64_t* stage = stage_all[warp];
     const double* ws = w + (int64_t)s * n;
     uint64_t* Cs = C + (int64_t)s * n;
+    uint64_t carry = boff[(int64_t)s * nblk + blk];
+    for (int64_t c0 = blk * kScanBlock; c0 < min(n, (blk + 1) * kScanBlock); c0 += kScanChunk) {
+        double v[8];
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        const int i = threadIdx.x + k * kScanThreads;
-        stage[scan_pad(i)] = b0 + i < n ? weight_fixed(__ldcs(ws + b0 + i)) : 0ull;
-    }
-    __syncthreads();
-    uint64_t v[kScanPer];
-    uint64_t loc = 0;
-    const int own = threadIdx.x * (kScanPer + 1);
+        for (int k = 0; k < 8; ++k) {
+            const int64_t p = c0 + k * 32 + lane;
+            v[k] = p < n ? __ldcs(ws + p) : 0.0;
+        }
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        v[k] = stage[own + k];
-        loc += v[k];
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t incl = loc;
+        for (int k = 0; k < 8; ++k) stage[scan_pad(k * 32 + lane)] = weight_fixed(v[k]);
+        __syncwarp();
+        uint64_t r[8], loc = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) wtot[warp] = incl;
-    __syncthreads();
-    uint64_t run = boff[(int64_t)s * nblk + blockIdx.x] + incl - loc;
-    for (int k = 0; k < warp; ++k) run += wtot[k];
+        for (int k = 0; k < 8; ++k) {
+            r[k] = stage[lane * 9 + k];
+            loc += r[k];
+        }
+        uint64_t incl = loc;
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        run += v[k];
-        stage[own + k] = run;
-    }
-    __syncthreads();
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        uint64_t run = carry + incl - loc;
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        const int i = threadIdx.x + k * kScanThreads;
-        if (b0 + i < n) Cs[b0 + i] = stage[scan_pad(i)];
+        for (int k = 0; k < 8; ++k) {
+            run += r[k];
+            stage[lane * 9 + k] = run;
+        }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t p = c0 + k * 32 + lane;
+            if (p < n) Cs[p] = stage[scan_pad(k * 32 + lane)];
+        }
+        __syncwarp();
     }
 }
 
@@ -819,7 +827,7 @@ extern "C" pr_status pr_resample(pr_precision precision, int32_t fast_dim, const
     uint64_t* bsum = reinterpret_cast<uint64_t*>(base + l.c_bytes);
     uint64_t* total = reinterpret_cast<uint64_t*>(base + l.c_bytes + l.b_bytes);
     int64_t* bounds = reinterpret_cast<int64_t*>(base + l.c_bytes + l.b_bytes + l.t_bytes);
-    dim3 gb((unsigned)l.nblk, (unsigned)n_slices);
+    dim3 gb((unsigned)((l.nblk + kScanWarps - 1) / kScanWarps), (unsigned)n_slices);
     fixed_blocksum_kernel<<<gb, kScanThreads, 0, st>>>(w, n, l.nblk, bsum);
     PR_CHECK_LAUNCH();
     scan_blocks_kernel<<<n_slices, 1024, 0, st>>>(bsum, l.nblk, total);
