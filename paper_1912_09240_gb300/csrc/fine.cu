@@ -40,6 +40,22 @@ int num_sms()
     return cache[dev];
 }
 
+int smem_optin_max()
+{
+    static std::mutex mu;
+    static std::vector<int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 48 * 1024;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1, 0);
+    if (cache[dev] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cache[dev] = v > 0 ? v : 48 * 1024;
+    }
+    return cache[dev];
+}
+
 // Arguments of one fine launch, after host-side validation.
 struct FineArgs {
     const void* x_in;
@@ -716,6 +732,7 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
     if (counts_end) PR_TRY_CUDA(cudaMemsetAsync(counts_end, 0, (size_t)n_slices * bins * 4, st));
 
     const FineSmem L = fine_smem_layout(bins, any_grid, do_match, precision == PR_F32);
+    if (L.total > (size_t)smem_optin_max()) return PR_ERR_UNSUPPORTED;   // the fused matching table
     FineSmemOffsets so{(unsigned)L.thr, (unsigned)L.hs, (unsigned)L.he, (unsigned)L.match};
     const int flags = (any_grid ? 1 : 0) | (do_match ? 2 : 0) | (counts_start ? 4 : 0) | (counts_end ? 8 : 0);
     pr_status rc = PR_OK;
@@ -834,17 +851,20 @@ extern "C" pr_status pr_match(pr_precision precision, const void* x_prior, void*
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int bins = grid->bins;
     const GridDev g = make_grid(*grid);
-    // one 1024-thread CTA per SM: the table is built once per SM (FP64 work)
-    const int64_t per_block = stream_range(n, n_slices, 16384, 1);
+    // two 1024-thread CTAs per SM, each building its table once (a few
+    // microseconds of FP64 work) and streaming its share of the particles
+    const int64_t per_block = stream_range(n, n_slices, 16384, 2);
     const int64_t blocks_per_slice = (n + per_block - 1) / per_block;
     dim3 gr((unsigned)blocks_per_slice, (unsigned)n_slices);
+    // the per-CTA table must fit in shared memory (PR_ERR_UNSUPPORTED beyond)
+    const size_t smem = precision == PR_F32 ? align16((size_t)(bins + 1) * 4) + match_smem_bytes_f32(bins)
+                                            : match_smem_bytes(bins);
+    if (smem > (size_t)smem_optin_max()) return PR_ERR_UNSUPPORTED;
     if (precision == PR_F32) {
-        const size_t smem = align16((size_t)(bins + 1) * 4) + match_smem_bytes_f32(bins);
         PR_TRY_CUDA(set_smem(match_f32_kernel, smem));
         match_f32_kernel<<<gr, 1024, smem, st>>>(static_cast<const float*>(x_prior), static_cast<float*>(x_out), n, g,
                                                 (float)grid->x_lo, (float)(1.0 / g.h), cdf_prior, cdf_target, per_block);
     } else {
-        const size_t smem = match_smem_bytes(bins);
         PR_TRY_CUDA(set_smem(match_f64_kernel, smem));
         match_f64_kernel<<<gr, 256, smem, st>>>(static_cast<const double*>(x_prior), static_cast<double*>(x_out), n, g,
                                                 cdf_prior, cdf_target, per_block);

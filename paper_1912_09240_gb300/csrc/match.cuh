@@ -19,10 +19,15 @@
 namespace pr {
 
 // Shared-memory layout (bins = I).  The table, live while particles are mapped:
-//   piece  : float4 [2I+1]  (f_end, alpha, beta, target bin j as int bits):
+//   piece  : float4 [2I+1]  (alpha, beta, thr[j], thr[j+1]) of target bin j:
 //            on prior bin i the map is X = clamp(alpha + beta f, thr[j], thr[j+1])
 //            for the first piece of the bin whose f_end >= f (or its last piece)
-//   pst    : int2   [I]     pieces [pst.x, pst.y) of prior bin i (pst.x == pst.y: identity)
+//   pst    : uint2  [I]     pieces [start, end) of prior bin i as start | end << 16
+//            (start == end: identity; at most 2I+1 <= 8193 pieces) and the
+//            bin's left threshold thr[i] (float bits)
+//   fend   : float  [2I+1]  f_end of each piece (read only where a bin has more
+//            than one piece)
+// so that a particle on a bin with one piece reads an 8-byte and a 16-byte record.
 // Build scratch, dead once the table is built:
 //   Cp, Ct : double [I+1]   prior / target CDF
 //   nzpre  : int    [I+1]   number of non-empty target bins below j
@@ -32,7 +37,8 @@ namespace pr {
 // The binary64 path keeps using Cp, Ct, nzpre and nzlist while it maps.
 struct MatchSmem {
     float4* piece;
-    int2* pst;
+    uint2* pst;
+    float* fend;
     double* Cp;
     double* Ct;
     int* nzpre;
@@ -45,7 +51,7 @@ struct MatchSmem {
 __host__ __device__ inline size_t match_table_bytes(int bins)
 {
     const size_t I = (size_t)bins;
-    return (((2 * I + 1) * 16 + I * 8) + 15) & ~(size_t)15;
+    return (((2 * I + 1) * 16 + I * 8 + (2 * I + 1) * 4) + 15) & ~(size_t)15;
 }
 
 __host__ __device__ inline size_t match_build_bytes(int bins)
@@ -81,7 +87,8 @@ __device__ inline MatchSmem carve_match_smem_f32(unsigned char* base, int bins, 
     const int I = bins;
     MatchSmem m;
     m.piece = reinterpret_cast<float4*>(base);
-    m.pst = reinterpret_cast<int2*>(m.piece + (2 * I + 1));
+    m.pst = reinterpret_cast<uint2*>(m.piece + (2 * I + 1));
+    m.fend = reinterpret_cast<float*>(m.pst + I);
     m.Cp = const_cast<double*>(cp_g);
     m.Ct = const_cast<double*>(ct_g);
     int* ip = reinterpret_cast<int*>(base + match_table_bytes(bins));
@@ -98,7 +105,8 @@ __device__ inline MatchSmem carve_match_smem(unsigned char* base, int bins)
     const int I = bins;
     MatchSmem m;
     m.piece = reinterpret_cast<float4*>(base);
-    m.pst = reinterpret_cast<int2*>(m.piece + (2 * I + 1));
+    m.pst = reinterpret_cast<uint2*>(m.piece + (2 * I + 1));
+    m.fend = reinterpret_cast<float*>(m.pst + I);
     m.Cp = reinterpret_cast<double*>(base + match_table_bytes(bins));
     m.Ct = m.Cp + (I + 1);
     int* ip = reinterpret_cast<int*>(m.Ct + (I + 1));
@@ -219,7 +227,8 @@ __device__ inline void build_match_table(const GridDev& g, const float* thr, Mat
     }
     const int npieces = m.pstart[I];
     const float h_f = (float)g.h;
-    for (int i = threadIdx.x; i < I; i += blockDim.x) m.pst[i] = make_int2(m.pstart[i], m.pstart[i + 1]);
+    for (int i = threadIdx.x; i < I; i += blockDim.x)
+        m.pst[i] = make_uint2((uint32_t)m.pstart[i] | ((uint32_t)m.pstart[i + 1] << 16), __float_as_uint(thr[i]));
     // one thread per piece: its prior bin by binary search over pstart.  CDF
     // values are subtracted in FP64 (they cancel); the quotients, which end
     // up rounded to binary32 anyway, are taken in binary32, and the target
@@ -245,7 +254,8 @@ __device__ inline void build_match_table(const GridDev& g, const float* thr, Mat
             fe = __fdiv_rn((float)__dsub_rn(m.Ct[j + 1], m.Cp[i]), rbf);
         // a target bin of negligible mass makes the slope huge; saturate so
         // that the clamp into the bin below never sees inf - inf
-        m.piece[k] = make_float4(fe, fmaxf(fminf(a, 1e30f), -1e30f), fminf(b, 1e30f), __int_as_float(j));
+        m.piece[k] = make_float4(fmaxf(fminf(a, 1e30f), -1e30f), fminf(b, 1e30f), thr[j], thr[j + 1]);
+        m.fend[k] = fe;
     }
     __syncthreads();
 }
@@ -255,19 +265,19 @@ __device__ __forceinline__ float match_one_f32(const MatchSmem& m, const float* 
                                                float x)
 {
     const int i = bin_fast_f32(bf, thr, x);
-    const int2 kk = m.pst[i];
-    if (kk.x == kk.y) return x;   // identity on this bin
+    const uint2 kk = m.pst[i];
+    const int k0 = (int)(kk.x & 0xFFFFu), k1 = (int)(kk.x >> 16);
+    if (k0 == k1) return x;   // identity on this bin
     const bool below = !(x >= bf.thr0);
     const bool above = x >= bf.thrI;
-    float f = (x - thr[i]) * bf.inv_h;
+    float f = (x - __uint_as_float(kk.y)) * bf.inv_h;
     f = fminf(fmaxf(f, 0.0f), 1.0f);
     if (below) f = 0.0f;
     if (above) f = 1.0f;
-    int k = kk.x;
-    float4 pc = m.piece[k];
-    while (k < kk.y - 1 && f > pc.x) pc = m.piece[++k];
-    const int j = __float_as_int(pc.w);
-    const float xn = fminf(fmaxf(fmaf(pc.z, f, pc.y), thr[j]), thr[j + 1]);
+    int k = k0;
+    while (k < k1 - 1 && f > m.fend[k]) ++k;
+    const float4 pc = m.piece[k];
+    const float xn = fminf(fmaxf(fmaf(pc.y, f, pc.x), pc.z), pc.w);
     if (below) return x + (xn - bf.thr0);
     if (above) return x + (xn - bf.thrI);
     return xn;

@@ -36,6 +36,7 @@ inline bool grid_ok(const pr_grid* g)
 }
 
 int num_sms();   // of the current device, cached per device
+int smem_optin_max();   // shared memory one CTA may opt in to, current device, cached per device
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the

@@ -177,7 +177,7 @@ def _cdf_pair(orc, og, rng, n):
     return prior_x, cp[0], ct[0]
 
 
-@pytest.mark.parametrize("bins,lo,hi", [(64, -3.0, 3.0), (512, -3.0, 3.0), (37, -2.2, 4.1)])
+@pytest.mark.parametrize("bins,lo,hi", [(64, -3.0, 3.0), (512, -3.0, 3.0), (37, -2.2, 4.1), (2400, -3.0, 3.0)])
 def test_match_f64_bit_exact(L, orc, bins, lo, hi):
     og = orc.Grid(bins, lo, hi)
     rng = np.random.default_rng(3)
@@ -196,7 +196,7 @@ def test_match_f64_bit_exact(L, orc, bins, lo, hi):
     np.testing.assert_array_equal(out.cpu().numpy(), orc.match(x, og, cp, ct))
 
 
-@pytest.mark.parametrize("bins,lo,hi", [(64, -3.0, 3.0), (512, -3.0, 3.0), (1024, -3.0, 3.0)])
+@pytest.mark.parametrize("bins,lo,hi", [(64, -3.0, 3.0), (512, -3.0, 3.0), (1024, -3.0, 3.0), (2900, -3.0, 3.0)])
 def test_match_f32_close(L, orc, bins, lo, hi):
     og = orc.Grid(bins, lo, hi)
     rng = np.random.default_rng(4)
@@ -467,3 +467,30 @@ def test_update_cluster_sizes_agree(L, bins):
     finally:
         L.pr_set_update_cluster(8)
         L.pr_coarse_destroy(h)
+
+
+def test_matching_table_beyond_shared_memory_is_unsupported(L):
+    """A grid whose matching table does not fit one CTA's shared memory
+    (4096 bins) is refused with PR_ERR_UNSUPPORTED, standalone and fused into
+    the fine propagator, in both precisions; the restriction alone still
+    runs at 4096 bins."""
+    bins, n = 4096, 1000
+    grid = L.Grid(bins, -3.0, 3.0)
+    cdf = torch.linspace(0.0, 1.0, bins + 1, dtype=torch.float64, device=DEV).reshape(1, -1)
+    for prec, dt in ((L.PR_F32, torch.float32), (L.PR_F64, torch.float64)):
+        x = torch.zeros(1, n, dtype=dt, device=DEV)
+        y = torch.zeros(1, 1, n, dtype=dt, device=DEV)
+        out = torch.empty_like(x)
+        with pytest.raises(L.PrError) as e:
+            L.pr_match(prec, x, out, n, 1, grid, cdf, cdf)
+        assert e.value.code == L.PR_ERR_UNSUPPORTED
+        m = L.Model(L.PR_MODEL_OU, 1, 1.0, 1.0, 0.1)
+        with pytest.raises(L.PrError) as e:
+            L.pr_fine_propagate(m, prec, L.Rng(0), x, y, False, out, y.clone(), n, 0, 1, 4, 1e-3, grid=grid,
+                                cdf_prior=cdf, cdf_target=cdf)
+        assert e.value.code == L.PR_ERR_UNSUPPORTED
+        counts = torch.empty(1, bins, dtype=torch.int32, device=DEV)
+        L.pr_fine_propagate(m, prec, L.Rng(0), x, y, False, out, y.clone(), n, 0, 1, 4, 1e-3, grid=grid,
+                            counts_end=counts)
+        torch.cuda.synchronize()
+        assert int(counts.sum().item()) == n
