@@ -151,6 +151,11 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int n, const double* __restr
     }
 }
 
+// C_dT on n_vec states, one state per cluster of CL CTAs (the rows of P @ m
+// split between them; the bits do not depend on CL): on GB300's narrow FP64
+// pipe one CTA takes ~60 us for 512^2 FMAs, so a few states fill the GPU only
+// when each is spread over several SMs.
+template <int CL>
 __global__ void __launch_bounds__(kCoarseThreads)
 coarse_fp_kernel(const double* __restrict__ P, int I, const double* __restrict__ cin, double* __restrict__ cout)
 {
@@ -160,12 +165,19 @@ coarse_fp_kernel(const double* __restrict__ P, int I, const double* __restrict__
     double* mass = out + (I + 1);
     double* mp = mass + I;
     double* wsum = mp + I;
-    const double* src = cin + (size_t)blockIdx.x * (I + 1);
+    const Dist<CL> d = Dist<CL>::make();
+    const size_t v = blockIdx.x / CL;
+    const double* src = cin + v * (I + 1);
     for (int i = threadIdx.x; i <= I; i += blockDim.x) in[i] = src[i];
     __syncthreads();
-    coarse_apply_block(P, I, in, out, mass, mp, wsum);
-    double* dst = cout + (size_t)blockIdx.x * (I + 1);
-    for (int i = threadIdx.x; i <= I; i += blockDim.x) dst[i] = out[i];
+    coarse_apply_block<CL>(P, I, in, out, mass, mp, wsum, d);
+    double* dst = cout + v * (I + 1);
+    const int q0 = d.lo(I - 1), q1 = d.hi(I - 1);
+    for (int r = q0 + (int)threadIdx.x; r < q1; r += blockDim.x) dst[r + 1] = out[r + 1];
+    if (d.rank == 0 && threadIdx.x == 0) {
+        dst[0] = out[0];
+        dst[I] = out[I];
+    }
 }
 
 // The serial sweep of Section 3.2.3 on one CTA (CL = 1) or on a cluster of
@@ -327,8 +339,45 @@ extern "C" pr_status pr_coarse_fp(void* handle, const double* cdf_in, double* cd
     auto* h = static_cast<CoarseHandle*>(handle);
     const int I = h->g.bins;
     const size_t smem = coarse_apply_smem(I);
-    PR_TRY_CUDA(allow_smem(coarse_fp_kernel, smem));
-    coarse_fp_kernel<<<n_vec, kCoarseThreads, smem, static_cast<cudaStream_t>(stream)>>>(h->P, I, cdf_in, cdf_out);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the largest cluster that keeps the launch within two CTAs per SM
+    int cl = 1;
+    if (I >= 64)
+        for (int c : {8, 4, 2})
+            if ((int64_t)n_vec * c <= 2 * (int64_t)num_sms()) {
+                cl = c;
+                break;
+            }
+    if (cl == 1) {
+        PR_TRY_CUDA(allow_smem(coarse_fp_kernel<1>, smem));
+        coarse_fp_kernel<1><<<n_vec, kCoarseThreads, smem, st>>>(h->P, I, cdf_in, cdf_out);
+        PR_CHECK_LAUNCH();
+        return PR_OK;
+    }
+    auto launch = [&](auto kernel) -> cudaError_t {
+        cudaError_t e = allow_smem(kernel, smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)(n_vec * cl));
+        cfg.blockDim = dim3(kCoarseThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kernel, (const double*)h->P, I, cdf_in, cdf_out);
+    };
+    cudaError_t e;
+    switch (cl) {
+    case 2: e = launch(coarse_fp_kernel<2>); break;
+    case 4: e = launch(coarse_fp_kernel<4>); break;
+    default: e = launch(coarse_fp_kernel<8>); break;
+    }
+    if (e != cudaSuccess) return PR_ERR_CUDA;
     PR_CHECK_LAUNCH();
     return PR_OK;
 }
