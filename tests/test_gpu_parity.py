@@ -494,3 +494,41 @@ def test_matching_table_beyond_shared_memory_is_unsupported(L):
                             counts_end=counts)
         torch.cuda.synchronize()
         assert int(counts.sum().item()) == n
+
+
+@pytest.mark.parametrize("prec,bins,kind,d", [(0, 64, 1, 1), (0, 512, 1, 1), (0, 2900, 0, 1), (0, 512, 2, 3),
+                                              (1, 64, 0, 1), (1, 2400, 1, 1), (1, 256, 2, 3)])
+def test_fused_matching_equals_standalone(L, orc, prec, bins, kind, d):
+    """pr_fine_propagate with the matching fused into its prologue equals
+    pr_match followed by pr_fine_propagate without it, bit for bit, and the
+    fused restriction of the start states equals pr_restrict of the matched
+    states: binary32 and binary64, d = 1 and d = 3, grids up to the
+    shared-memory limit of the matching table."""
+    rng = np.random.default_rng(bins + d + prec)
+    og = orc.Grid(bins, -3.0, 3.0)
+    n, S, steps, dt = 5003, 2, 20, 1e-3
+    px = rng.normal(-0.3, 0.8, (S, n))
+    _, cp = orc.restrict(px, og)
+    _, ct = orc.restrict(rng.normal(0.4, 0.6, (S, 4 * n)), og)
+    dt_t = torch.float32 if prec == 0 else torch.float64
+    if prec == 0:
+        px = px.astype(np.float32).astype(np.float64)
+        _, cp = orc.restrict(px, og)
+    x = torch.tensor(px, dtype=dt_t, device=DEV)
+    y = torch.tensor(rng.normal(0.0, 1.0, (S, d, n)), dtype=dt_t, device=DEV)
+    g = L.Grid(bins, -3.0, 3.0)
+    m = L.Model(kind, d, 0.5, 3.0, 0.05) if kind != 0 else L.Model(0, 1, 1.0, 1.0, 0.1)
+    cpt, ctt = torch.tensor(cp, device=DEV), torch.tensor(ct, device=DEV)
+    xf, yf = torch.empty_like(x), torch.empty_like(y)
+    cs = torch.empty(S, bins, dtype=torch.int32, device=DEV)
+    L.pr_fine_propagate(m, prec, L.Rng(5, 1), x, y, False, xf, yf, n, 3, S, steps, dt, grid=g, cdf_prior=cpt,
+                        cdf_target=ctt, counts_start=cs)
+    xm = torch.empty_like(x)
+    L.pr_match(prec, x, xm, n, S, g, cpt, ctt)
+    cs_ref = torch.empty(S, bins, dtype=torch.int32, device=DEV)
+    L.pr_restrict(prec, xm, n, S, g, cs_ref, None)
+    xs, ys = torch.empty_like(x), torch.empty_like(y)
+    L.pr_fine_propagate(m, prec, L.Rng(5, 1), xm, y, False, xs, ys, n, 3, S, steps, dt)
+    torch.cuda.synchronize()
+    assert torch.equal(xf, xs) and torch.equal(yf, ys)
+    assert torch.equal(cs, cs_ref)
