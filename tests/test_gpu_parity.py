@@ -501,9 +501,10 @@ def test_matching_table_beyond_shared_memory_is_unsupported(L):
 def test_fused_matching_equals_standalone(L, orc, prec, bins, kind, d):
     """pr_fine_propagate with the matching fused into its prologue equals
     pr_match followed by pr_fine_propagate without it, bit for bit, and the
-    fused restriction of the start states equals pr_restrict of the matched
-    states: binary32 and binary64, d = 1 and d = 3, grids up to the
-    shared-memory limit of the matching table."""
+    fused restrictions (counts and CDFs) of the start and end states equal
+    pr_restrict of the matched and propagated states: binary32 and binary64,
+    d = 1 and d = 3, grids up to the shared-memory limit of the matching
+    table."""
     rng = np.random.default_rng(bins + d + prec)
     og = orc.Grid(bins, -3.0, 3.0)
     n, S, steps, dt = 5003, 2, 20, 1e-3
@@ -520,15 +521,19 @@ def test_fused_matching_equals_standalone(L, orc, prec, bins, kind, d):
     m = L.Model(kind, d, 0.5, 3.0, 0.05) if kind != 0 else L.Model(0, 1, 1.0, 1.0, 0.1)
     cpt, ctt = torch.tensor(cp, device=DEV), torch.tensor(ct, device=DEV)
     xf, yf = torch.empty_like(x), torch.empty_like(y)
-    cs = torch.empty(S, bins, dtype=torch.int32, device=DEV)
+    cs, ce = (torch.empty(S, bins, dtype=torch.int32, device=DEV) for _ in range(2))
+    cds, cde = (torch.empty(S, bins + 1, dtype=torch.float64, device=DEV) for _ in range(2))
     L.pr_fine_propagate(m, prec, L.Rng(5, 1), x, y, False, xf, yf, n, 3, S, steps, dt, grid=g, cdf_prior=cpt,
-                        cdf_target=ctt, counts_start=cs)
+                        cdf_target=ctt, counts_start=cs, cdf_start=cds, counts_end=ce, cdf_end=cde)
     xm = torch.empty_like(x)
     L.pr_match(prec, x, xm, n, S, g, cpt, ctt)
-    cs_ref = torch.empty(S, bins, dtype=torch.int32, device=DEV)
-    L.pr_restrict(prec, xm, n, S, g, cs_ref, None)
+    cs_ref, ce_ref = (torch.empty(S, bins, dtype=torch.int32, device=DEV) for _ in range(2))
+    cds_ref, cde_ref = (torch.empty(S, bins + 1, dtype=torch.float64, device=DEV) for _ in range(2))
+    L.pr_restrict(prec, xm, n, S, g, cs_ref, cds_ref)
     xs, ys = torch.empty_like(x), torch.empty_like(y)
     L.pr_fine_propagate(m, prec, L.Rng(5, 1), xm, y, False, xs, ys, n, 3, S, steps, dt)
+    L.pr_restrict(prec, xs, n, S, g, ce_ref, cde_ref)
     torch.cuda.synchronize()
     assert torch.equal(xf, xs) and torch.equal(yf, ys)
-    assert torch.equal(cs, cs_ref)
+    assert torch.equal(cs, cs_ref) and torch.equal(cds, cds_ref)
+    assert torch.equal(ce, ce_ref) and torch.equal(cde, cde_ref)
