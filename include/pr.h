@@ -288,8 +288,10 @@ pr_status pr_coarse_matrix(void* handle, double* out, void* stream);
  * Apply C_dT to n_vec macroscopic states: masses = diff(cdf_in), P @ masses
  * with masses <= 1e-10 set to 0 (below that level they are rounding noise of
  * the matrix exponential, and negative round-off goes with them), cumulative
- * sum normalised to unit mass.
- *   cdf_in, cdf_out (device) [n_vec][bins+1]; may not alias.
+ * sum normalised to unit mass.  With few states each one is spread over a
+ * thread-block cluster of up to 8 CTAs (rows of P split between them); the
+ * result does not depend on that split.
+ *   cdf_in, cdf_out (device) [n_vec][bins+1]; must not overlap.
  */
 pr_status pr_coarse_fp(void* handle, const double* cdf_in, double* cdf_out, int32_t n_vec,
                        void* stream);
