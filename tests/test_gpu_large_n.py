@@ -1,0 +1,118 @@
+"""Ensembles beyond 2^31 particles: every kernel's particle index must be
+64-bit wide (a 32-bit product or sum would wrap past 2^31).  Inputs are
+built on the device in chunks; expected values come from closed forms and
+from the oracle run on sampled particles (with their own indices as Philox
+particle ids), among them the ones just below and above 2^31."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+N_BIG = (1 << 31) + 77
+BINS, LO, HI = 512, -3.0, 3.0          # h = 3/256: bin centres are exact in binary32
+SAMPLE = np.array([0, 1, 511, 512, (1 << 31) - 1, 1 << 31, (1 << 31) + 1, N_BIG - 1, 123456789, 1500000001])
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1912_09240_gb300 import build as b
+    b.build()
+    from paper_1912_09240_gb300 import _lib
+    yield _lib
+    torch.cuda.empty_cache()   # these tests hold tens of GB; give them back to the device
+
+
+def _centres(n):
+    """x_p = centre of bin (p mod BINS), filled in chunks."""
+    h = (HI - LO) / BINS
+    x = torch.empty(n, dtype=torch.float32, device=DEV)
+    step = 1 << 27
+    for a in range(0, n, step):
+        b = min(n, a + step)
+        i = torch.arange(a, b, dtype=torch.int64, device=DEV) % BINS
+        x[a:b] = (LO + (i.to(torch.float64) + 0.5) * h).to(torch.float32)
+    return x
+
+
+def _expected_counts(n):
+    i = np.arange(BINS)
+    return (n - i + BINS - 1) // BINS
+
+
+def _cdf_of(counts):
+    c = np.concatenate([[0], np.cumsum(counts)]).astype(np.float64)
+    return c / c[-1]
+
+
+def test_restrict_beyond_2_31(L):
+    x = _centres(N_BIG)
+    counts = torch.empty(1, BINS, dtype=torch.int32, device=DEV)
+    cdf = torch.empty(1, BINS + 1, dtype=torch.float64, device=DEV)
+    L.pr_restrict(L.PR_F32, x, N_BIG, 1, L.Grid(BINS, LO, HI), counts, cdf)
+    torch.cuda.synchronize()
+    exp = _expected_counts(N_BIG)
+    np.testing.assert_array_equal(counts.cpu().numpy()[0].astype(np.int64), exp)
+    np.testing.assert_array_equal(cdf.cpu().numpy()[0], np.concatenate([[0], np.cumsum(exp)]) / N_BIG)
+
+
+def test_match_beyond_2_31(L, orc):
+    """Target = the prior moved up by one bin (bin 0 left empty, the last
+    bin keeping its own mass too): a map that moves every particle, sampled
+    particles against the oracle's matching of the same values."""
+    x = _centres(N_BIG)
+    exp = _expected_counts(N_BIG).astype(np.float64)
+    cp = _cdf_of(exp)
+    tgt = np.concatenate([[0.0], exp[:-1]])
+    tgt[-1] += exp[-1]
+    ct = _cdf_of(tgt)
+    out = torch.empty_like(x)
+    L.pr_match(L.PR_F32, x, out, N_BIG, 1, L.Grid(BINS, LO, HI), torch.tensor(cp[None], device=DEV),
+               torch.tensor(ct[None], device=DEV))
+    torch.cuda.synchronize()
+    og = orc.Grid(BINS, LO, HI)
+    xs = x[torch.tensor(SAMPLE, device=DEV)].cpu().numpy().astype(np.float64)
+    ref = orc.match(xs[None], og, cp[None], ct[None])[0]
+    got = out[torch.tensor(SAMPLE, device=DEV)].cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ref) <= 2e-3 * np.maximum(np.abs(ref), 1.0)), (got, ref)
+    assert np.all(np.abs(got - xs) > 1e-3)   # every sampled particle moved
+
+
+def test_fine_propagate_beyond_2_31(L, orc):
+    """Two EM steps of the OU system over 2^31 + 77 particles in place, with
+    the end-state restriction fused: sampled particles against the oracle
+    with their own particle ids, and the counts sum to n."""
+    x = _centres(N_BIG).reshape(1, -1)
+    y = torch.zeros(1, 1, N_BIG, dtype=torch.float32, device=DEV)
+    x0 = x[0, torch.tensor(SAMPLE, device=DEV)].cpu().numpy().astype(np.float64)
+    counts = torch.empty(1, BINS, dtype=torch.int32, device=DEV)
+    m = L.Model(L.PR_MODEL_OU, 1, 0.7, 2.0, 0.1)
+    L.pr_fine_propagate(m, L.PR_F32, L.Rng(11, 3), x, y, False, x, y, N_BIG, 4, 1, 2, 1e-3,
+                        grid=L.Grid(BINS, LO, HI), counts_end=counts)
+    torch.cuda.synchronize()
+    assert int(counts.to(torch.int64).sum().item()) == N_BIG
+    idx = torch.tensor(SAMPLE, device=DEV)
+    gx = x[0, idx].cpu().numpy().astype(np.float64)
+    gy = y[0, 0, idx].cpu().numpy().astype(np.float64)
+    rx, ry = orc.fine_propagate(orc.Model(kind=0, fast_dim=1, lam=0.7, beta=2.0, eps=0.1), 11, x0[None],
+                                np.zeros((1, 1, len(SAMPLE))), 4, 2, 1e-3, problem=3, ids=SAMPLE.astype(np.uint32))
+    assert np.all(np.abs(gx - rx[0]) <= 2e-3 * np.maximum(np.abs(rx[0]), 1.0)), (gx, rx[0])
+    assert np.all(np.abs(gy - ry[0, 0]) <= 2e-3 * np.maximum(np.abs(ry[0, 0]), 1.0)), (gy, ry[0, 0])
+
+
+def test_resample_equal_weights_beyond_2_31(L):
+    """Equal weights over 2^31 + 77 particles: both resampling modes give
+    the identity (strong projection), checked on every index in chunks."""
+    n = N_BIG
+    w = torch.full((1, n), 1.0 / n, dtype=torch.float64, device=DEV)
+    idx = torch.empty(1, n, dtype=torch.int32, device=DEV)
+    ws = torch.empty(L.pr_resample_workspace(n, 1), dtype=torch.uint8, device=DEV)
+    for mode in (L.PR_RESAMPLE_STRATIFIED, L.PR_RESAMPLE_DETERMINISTIC):
+        L.pr_resample(0, 1, None, None, False, w, n, 1, 2, mode, L.Rng(4, 0), idx, None, None, ws)
+        torch.cuda.synchronize()
+        step = 1 << 27
+        for a in range(0, n, step):
+            b = min(n, a + step)
+            got = idx[0, a:b].to(torch.int64) & 0xFFFFFFFF
+            assert torch.equal(got, torch.arange(a, b, dtype=torch.int64, device=DEV)), (mode, a)
