@@ -116,3 +116,29 @@ def test_resample_equal_weights_beyond_2_31(L):
             b = min(n, a + step)
             got = idx[0, a:b].to(torch.int64) & 0xFFFFFFFF
             assert torch.equal(got, torch.arange(a, b, dtype=torch.int64, device=DEV)), (mode, a)
+
+
+def test_reweight_and_weighted_restriction_beyond_2_31(L):
+    """Reweighting to a target that doubles the mass of the even bins (the
+    factors are exact: 4/3 on even bins, 2/3 on odd ones up to the rounding
+    of the CDF differences, checked on sampled particles against the same
+    arithmetic), then the weighted restriction of those weights, whose CDF
+    must be the target's within the rounding of the fixed point."""
+    x = _centres(N_BIG)
+    exp = _expected_counts(N_BIG).astype(np.float64)
+    cp = _cdf_of(exp)
+    tgt = exp * np.where(np.arange(BINS) % 2 == 0, 2.0, 1.0)
+    ct = _cdf_of(tgt)
+    w = torch.empty(1, N_BIG, dtype=torch.float64, device=DEV)
+    g = L.Grid(BINS, LO, HI)
+    L.pr_reweight(L.PR_F32, x, False, None, N_BIG, 1, g, torch.tensor(cp[None], device=DEV),
+                  torch.tensor(ct[None], device=DEV), w)
+    torch.cuda.synchronize()
+    bins_s = SAMPLE % BINS
+    r = (ct[bins_s + 1] - ct[bins_s]) / (cp[bins_s + 1] - cp[bins_s])
+    np.testing.assert_allclose(w[0, torch.tensor(SAMPLE, device=DEV)].cpu().numpy(), r / N_BIG, rtol=1e-14)
+    cdf = torch.empty(1, BINS + 1, dtype=torch.float64, device=DEV)
+    ws = torch.empty(L.pr_restrict_weighted_workspace(1, BINS), dtype=torch.uint8, device=DEV)
+    L.pr_restrict_weighted(L.PR_F32, x, False, w, N_BIG, 1, g, cdf, ws)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(cdf.cpu().numpy()[0], ct, rtol=0, atol=1e-12)
