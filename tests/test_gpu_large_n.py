@@ -142,3 +142,37 @@ def test_reweight_and_weighted_restriction_beyond_2_31(L):
     L.pr_restrict_weighted(L.PR_F32, x, False, w, N_BIG, 1, g, cdf, ws)
     torch.cuda.synchronize()
     np.testing.assert_allclose(cdf.cpu().numpy()[0], ct, rtol=0, atol=1e-12)
+
+
+def test_slice_count_at_its_limit(L, orc):
+    """65535 slices (the largest count the entry points accept) of 7
+    particles: restriction counts against their closed form, the fine
+    propagator on the first and last slices against the oracle, and
+    equal-weight resampling (the identity) on every slice."""
+    S, n = 65535, 7
+    h = (HI - LO) / BINS
+    i = (torch.arange(S * n, dtype=torch.int64, device=DEV) * 37) % BINS
+    x = (LO + (i.to(torch.float64) + 0.5) * h).to(torch.float32).reshape(S, n)
+    g = L.Grid(BINS, LO, HI)
+    counts = torch.empty(S, BINS, dtype=torch.int32, device=DEV)
+    L.pr_restrict(L.PR_F32, x, n, S, g, counts, None)
+    ref = torch.zeros(S, BINS, dtype=torch.int32, device=DEV)
+    ref.scatter_add_(1, i.reshape(S, n), torch.ones(S, n, dtype=torch.int32, device=DEV))
+    torch.cuda.synchronize()
+    assert torch.equal(counts, ref)
+    y = torch.zeros(S, 1, n, dtype=torch.float32, device=DEV)
+    xo, yo = torch.empty_like(x), torch.empty_like(y)
+    m = L.Model(L.PR_MODEL_DOUBLE_WELL, 1, 0.5, 3.0, 0.1)
+    L.pr_fine_propagate(m, L.PR_F32, L.Rng(2, 0), x, y, False, xo, yo, n, 9, S, 4, 1e-3)
+    torch.cuda.synchronize()
+    om = orc.Model(kind=1, fast_dim=1, lam=0.5, beta=3.0, eps=0.1)
+    for s in (0, S - 1):
+        rx, _ = orc.fine_propagate(om, 2, x[s:s + 1].cpu().numpy(), np.zeros((1, 1, n)), 9 + s, 4, 1e-3)
+        got = xo[s].cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(got - rx[0]) <= 2e-3 * np.maximum(np.abs(rx[0]), 1.0)), (s, got, rx[0])
+    w = torch.full((S, n), 1.0 / n, dtype=torch.float64, device=DEV)
+    idx = torch.empty(S, n, dtype=torch.int32, device=DEV)
+    ws = torch.empty(L.pr_resample_workspace(n, S), dtype=torch.uint8, device=DEV)
+    L.pr_resample(0, 1, None, None, False, w, n, S, 0, L.PR_RESAMPLE_STRATIFIED, L.Rng(1, 0), idx, None, None, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(idx, torch.arange(n, dtype=torch.int32, device=DEV).expand(S, n))
