@@ -569,7 +569,10 @@ static void or_cdf_from_mass(int I, const double* m, double* out)
 
 /* kind 1: additive (Section 4.1), negatives to zero then rescale.
  * kind 2: multiplicative (Section 4.2), unsupported bins to zero then rescale.
- * kind 3: rotation on the L2 sphere (Section 4.3). */
+ * kind 3: rotation on the L2 sphere (Section 4.3).
+ * Reading: when the corrected masses sum to zero (the multiplicative
+ * iterator when the supports of a b and c do not meet) there is nothing to
+ * rescale; the correction is dropped and the result is b, the fine result. */
 void or_iterator_mass(int kind, int I, const double* A, const double* B, const double* C, double* out)
 {
     double* a = (double*)malloc(sizeof(double) * I);
@@ -602,7 +605,13 @@ void or_iterator_mass(int kind, int I, const double* A, const double* B, const d
             r[i] = s * s;
         }
     }
-    or_cdf_from_mass(I, r, out);
+    double total = 0.0;
+    for (int i = 0; i < I; ++i) total += r[i];
+    if (total > 0.0) {
+        or_cdf_from_mass(I, r, out);
+    } else {
+        for (int i = 0; i <= I; ++i) out[i] = B[i];
+    }
     free(a); free(b); free(c); free(r);
 }
 

@@ -570,8 +570,15 @@ __device__ inline void mass_iterate_block(int kind, int I, const double* A, cons
     __syncthreads();
     block_scan_f64(r, r, I, wsum);
     const double total = r[I - 1];
+    if (!(total > 0.0)) {   // no mass to normalise (the multiplicative iterator
+        // when the supports of a b and c do not meet): the correction is
+        // dropped and the update keeps the fine result b
+        for (int i = threadIdx.x; i <= I; i += blockDim.x) out[i] = B[i];
+        __syncthreads();
+        return;
+    }
     for (int i = threadIdx.x; i < I - 1; i += blockDim.x) {
-        const double v = total > 0.0 ? __ddiv_rn(r[i], total) : 0.0;
+        const double v = __ddiv_rn(r[i], total);
         out[i + 1] = v < 1.0 ? v : 1.0;
     }
     if (threadIdx.x == 0) {

@@ -335,7 +335,7 @@ def _rand_cdf(rng, bins, empty=0.3, n=4096):
 
 
 @pytest.mark.parametrize("qmode", [0, 1])
-@pytest.mark.parametrize("bins", [3, 64, 512, 1024])
+@pytest.mark.parametrize("bins", [1, 2, 3, 64, 512, 1024])
 def test_quantile_iterator_bit_exact(L, orc, qmode, bins):
     og = orc.Grid(bins, -3.0, 3.0)
     rng = np.random.default_rng(bins + qmode)
@@ -537,3 +537,20 @@ def test_fused_matching_equals_standalone(L, orc, prec, bins, kind, d):
     assert torch.equal(xf, xs) and torch.equal(yf, ys)
     assert torch.equal(cs, cs_ref) and torch.equal(cds, cds_ref)
     assert torch.equal(ce, ce_ref) and torch.equal(cde, cde_ref)
+
+
+@pytest.mark.parametrize("bins", [1, 2, 3])
+@pytest.mark.parametrize("it", [1, 2, 3])
+def test_mass_iterators_tiny_grids(L, orc, it, bins):
+    """The additive, multiplicative and rotation iterators on grids of 1, 2
+    and 3 bins with empty bins, against the oracle."""
+    og = orc.Grid(bins, 0.0, 1.0)
+    rng = np.random.default_rng(10 * it + bins)
+    V = 8
+    a, b, c = (np.stack([_rand_cdf(rng, bins) for _ in range(V)]) for _ in range(3))
+    out = torch.empty(V, bins + 1, dtype=torch.float64, device=DEV)
+    L.pr_iterate(it, 0, L.Grid(bins, 0.0, 1.0), V, _t(a), _t(b), _t(c), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for v in range(V):
+        np.testing.assert_allclose(got[v], orc.iterate(og, a[v], b[v], c[v], it, 0), rtol=0, atol=1e-13)

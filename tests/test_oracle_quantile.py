@@ -137,6 +137,19 @@ def test_additive_hand_computed(orc):
     np.testing.assert_allclose(out, [0, 0.4, 1.0, 1.0], atol=1e-15)
 
 
+def test_multiplicative_without_common_support_keeps_b(orc):
+    """a b / c vanishes on every bin when b's mass sits where a or c has
+    none: there is no mass to rescale and the update keeps b (the
+    correction is dropped), bit for bit."""
+    g = orc.Grid(4, 0.0, 4.0)
+    cdf = lambda m: np.concatenate([[0.0], np.cumsum(m)])
+    a, b, c = cdf([0.5, 0.5, 0.0, 0.0]), cdf([0.0, 0.0, 0.25, 0.75]), cdf([0.25, 0.25, 0.25, 0.25])
+    np.testing.assert_array_equal(orc.iterate(g, a, b, c, orc.ITER_MULT), b)
+    # a single common bin is enough to normalise: all mass goes there
+    b2 = cdf([0.0, 0.5, 0.5, 0.0])
+    np.testing.assert_allclose(orc.iterate(g, a, b2, c, orc.ITER_MULT), cdf([0.0, 1.0, 0.0, 0.0]), atol=0)
+
+
 def test_rotation_is_a_rotation(orc):
     """sqrt of the result has unit L2 norm and the map sends sqrt(c) to sqrt(a)
     (Section 4.3): the inner product with sqrt(a) equals that of b with c."""
