@@ -300,7 +300,10 @@ def test_match_strong_projection_exact(L, orc, prec):
 
 @pytest.mark.parametrize("kind,lam,beta,bins,lo,hi,dT", [(0, 1.0, 1.0, 256, -4.0, 4.0, 0.125),
                                                         (1, 0.5, 3.0, 512, -3.0, 3.0, 0.1),
-                                                        (0, 0.3, 2.0, 100, -5.0, 5.0, 0.7)])
+                                                        (0, 0.3, 2.0, 100, -5.0, 5.0, 0.7),
+                                                        (1, 0.5, 3.0, 1, -3.0, 3.0, 0.1),
+                                                        (1, 0.5, 3.0, 2, -3.0, 3.0, 0.1),
+                                                        (0, 1.0, 1.0, 1024, -4.0, 4.0, 2.0)])
 def test_coarse_matches_oracle(L, orc, kind, lam, beta, bins, lo, hi, dT):
     gm = L.Model(kind, 1, lam, beta, 0.1)
     om = orc.Model(kind, 1, lam, beta, 0.1)
