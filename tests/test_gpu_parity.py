@@ -557,3 +557,45 @@ def test_mass_iterators_tiny_grids(L, orc, it, bins):
     got = out.cpu().numpy()
     for v in range(V):
         np.testing.assert_allclose(got[v], orc.iterate(og, a[v], b[v], c[v], it, 0), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", ["foreign_prior", "point_masses", "prior_in_target_gap"])
+def test_match_degenerate_cdfs(L, orc, prec, case):
+    """Matching with CDFs that are not the ensemble's own: a prior from
+    another sample (particles in bins the prior calls empty), prior and
+    target each concentrated in a single bin, and a prior whose support lies
+    in a gap of the target.  Binary64 bit for bit, binary32 within its
+    tolerance, both against the oracle."""
+    bins, lo, hi, n = 96, -3.0, 3.0, 20011
+    og = orc.Grid(bins, lo, hi)
+    rng = np.random.default_rng({"foreign_prior": 1, "point_masses": 2, "prior_in_target_gap": 3}[case] + 10 * prec)
+    x = rng.normal(0.0, 1.0, (1, n))
+    cdf = lambda m: np.concatenate([[0.0], np.cumsum(m / m.sum())])
+    if case == "foreign_prior":
+        _, cp = orc.restrict(rng.normal(0.8, 0.3, (1, n)), og)
+        _, ct = orc.restrict(rng.normal(-0.5, 0.7, (1, n)), og)
+    elif case == "point_masses":
+        mp, mt = np.zeros(bins), np.zeros(bins)
+        mp[40], mt[70] = 1.0, 1.0
+        cp, ct = cdf(mp)[None], cdf(mt)[None]
+    else:
+        mt = np.ones(bins)
+        mt[30:60] = 0.0
+        mp = np.zeros(bins)
+        mp[35:55] = 1.0
+        cp, ct = cdf(mp)[None], cdf(mt)[None]
+    cp[:, -1] = 1.0
+    ct[:, -1] = 1.0
+    if prec == 0:
+        x = x.astype(np.float32).astype(np.float64)
+    dt = torch.float32 if prec == 0 else torch.float64
+    out = torch.empty(1, n, dtype=dt, device=DEV)
+    L.pr_match(prec, torch.tensor(x, dtype=dt, device=DEV), out, n, 1, L.Grid(bins, lo, hi), _t(cp), _t(ct))
+    torch.cuda.synchronize()
+    ref = orc.match(x, og, cp, ct)
+    got = out.cpu().numpy().astype(np.float64)
+    if prec == 1:
+        np.testing.assert_array_equal(got, ref)
+    else:
+        assert np.all(np.abs(got - ref) <= 2e-3 * np.maximum(np.abs(ref), 1.0))
