@@ -311,7 +311,9 @@ pr_status pr_coarse_fp(void* handle, const double* cdf_in, double* cdf_out, int3
  *   cdf_c_star (device) [n_slices][bins+1], C(R X_k^n)   (NULL for PR_ITER_NONE)
  *   cdf_next   (device) [n_slices+1][bins+1], receives rho_{k+1}^0 .. rho_{k+1}^{n_slices}
  *   status     (device) int32 or NULL: 0 on success, PR_ERR_NUMERIC if a
- *              non-finite value or an empty state appeared.
+ *              non-finite value or an empty state appeared, or if an input
+ *              of the quantile iterator was not a CDF (a value outside
+ *              [0, 1], or decreasing); the results are then unspecified.
  */
 pr_status pr_parareal_update(void* coarse, pr_iterator iterator, pr_quantile_mode qmode,
                              int32_t n_slices, const double* cdf0, const double* cdf_f_star,

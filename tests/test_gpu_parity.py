@@ -599,3 +599,34 @@ def test_match_degenerate_cdfs(L, orc, prec, case):
         np.testing.assert_array_equal(got, ref)
     else:
         assert np.all(np.abs(got - ref) <= 2e-3 * np.maximum(np.abs(ref), 1.0))
+
+
+@pytest.mark.parametrize("qmode", [0, 1])
+def test_quantile_iterator_degenerate_cdfs(L, orc, qmode):
+    """The quantile iterator on point masses in different bins, disjoint
+    supports, mass only in the two end bins, and a = b = c: bit for bit
+    against the oracle, unit mass and monotone."""
+    bins = 48
+    og = orc.Grid(bins, -3.0, 3.0)
+    def cdf(m):   # a valid CDF: non-decreasing, C_0 = 0, C_I = 1 exactly
+        c = np.minimum(np.concatenate([[0.0], np.cumsum(np.asarray(m, float) / np.sum(m))]), 1.0)
+        c[-1] = 1.0
+        return c
+    pm = lambda *idx: np.bincount(idx, minlength=bins).astype(float)
+    ends = np.zeros(bins)
+    ends[[0, -1]] = [0.3, 0.7]
+    cases = [(pm(5), pm(20), pm(40)), (pm(0), pm(47), pm(47)), (pm(3, 4), pm(30, 31, 32), pm(10)),
+             (ends, pm(24), ends), (ends, ends, ends), (pm(12), pm(12), pm(12)),
+             (np.ones(bins), pm(7), np.ones(bins))]
+    a, b, c = (np.stack([cdf(t[k]) for t in cases]) for k in range(3))
+    V = len(cases)
+    out = torch.empty(V, bins + 1, dtype=torch.float64, device=DEV)
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    L.pr_iterate(L.PR_ITER_QUANTILE, qmode, L.Grid(bins, -3.0, 3.0), V, _t(a), _t(b), _t(c), out, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    got = out.cpu().numpy()
+    for v in range(V):
+        ref = orc.iterate(og, a[v], b[v], c[v], 0, qmode)
+        np.testing.assert_array_equal(got[v], ref, err_msg=f"case {v}")
+        assert got[v][0] == 0.0 and got[v][-1] == 1.0 and np.all(np.diff(got[v]) >= 0)
