@@ -299,3 +299,26 @@ def test_resample_concentrated_weights(L, orc, mode, pattern):
     L.pr_resample(0, 1, None, None, False, _t(w), n, S, 4, mode, L.Rng(31, 3), idx, None, None, ws)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(idx.cpu().numpy().view(np.uint32), ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_reweight_foreign_prior(L, orc, prec):
+    """A prior CDF restricted from another sample than the particles: the
+    particles in bins the prior calls empty get weight 0, the others the
+    relocated target's factors; bit for bit against the oracle."""
+    rng = np.random.default_rng(80 + prec)
+    bins, lo, hi, n, S = 128, -3.0, 3.0, 30011, 2
+    og = orc.Grid(bins, lo, hi)
+    x = rng.normal(0.0, 1.0, (S, n))
+    if prec == 0:
+        x = x.astype(np.float32).astype(np.float64)
+    _, cp = orc.restrict(rng.normal(0.6, 0.4, (S, 5000)), og)
+    _, ct = orc.restrict(rng.normal(-0.3, 0.8, (S, 5000)), og)
+    ref = orc.reweight(x, og, cp, ct)
+    dt = torch.float32 if prec == 0 else torch.float64
+    out = torch.empty(S, n, dtype=torch.float64, device=DEV)
+    L.pr_reweight(prec, _t(x, dt), False, None, n, S, L.Grid(bins, lo, hi), _t(cp), _t(ct), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    np.testing.assert_array_equal(got, ref)
+    assert np.any(got == 0.0) and np.any(got > 0.0)
