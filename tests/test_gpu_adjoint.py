@@ -234,3 +234,49 @@ def test_affine_seed_equals_given_seeds(L, kind, steps, ckpt, scale, shift):
     assert torch.equal(xT, xT0)
     assert torch.equal(g1, g0), (g1, g0)
     assert torch.equal(xb1, xb0) and torch.equal(yb1, yb0)
+
+
+@pytest.mark.parametrize("n", [1, 37])
+def test_adjoint_without_steps(L, n):
+    """No steps at all (steps = 0): X_T = X_0, every parameter derivative is
+    0 and dX_T/dX_0 = 1, dX_T/dY_0 = 0, per particle and seeded."""
+    rng = np.random.default_rng(n)
+    x0 = torch.tensor(rng.normal(size=n), dtype=torch.float32, device="cuda")
+    y0 = torch.tensor(rng.normal(size=n), dtype=torch.float32, device="cuda")
+    m = L.Model(L.PR_MODEL_DOUBLE_WELL, 1, 0.5, 3.0, 0.05)
+    ws = torch.empty(L.pr_fine_adjoint_workspace(n, 2, 0, 12), dtype=torch.uint8, device="cuda")
+    xT = torch.empty(n, dtype=torch.float32, device="cuda")
+    grads = torch.empty(n, 3, dtype=torch.float64, device="cuda")
+    xb0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    yb0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    L.pr_fine_adjoint(m, L.Rng(1, 0), x0, y0, n, 0, 2, 0, 1e-3, 12, xT, None, None, None, grads, xb0, yb0, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(xT, x0)
+    assert torch.all(grads == 0.0) and torch.all(xb0 == 1.0) and torch.all(yb0 == 0.0)
+    g = torch.full((3,), 7.0, dtype=torch.float64, device="cuda")
+    L.pr_fine_adjoint_affine(m, L.Rng(1, 0), x0, y0, n, 0, 2, 0, 1e-3, 12, 2.0 / n, 0.0, xT, None, g, None, None,
+                             ws)
+    torch.cuda.synchronize()
+    assert torch.all(g == 0.0)
+
+
+def test_adjoint_single_particle_against_tangent(L, orc):
+    """One particle, the paired and the step-by-step kernels (even and odd
+    steps per slice): against the oracle's tangent-linear derivatives."""
+    for steps in (40, 41):
+        x0 = np.array([0.7], dtype=np.float32)
+        y0 = np.array([-0.2], dtype=np.float32)
+        gm = L.Model(L.PR_MODEL_OU, 1, 0.8, 1.5, 0.1)
+        om = orc.Model(0, 1, 0.8, 1.5, 0.1)
+        ws = torch.empty(L.pr_fine_adjoint_workspace(1, 3, steps, 16), dtype=torch.uint8, device="cuda")
+        xT = torch.empty(1, dtype=torch.float32, device="cuda")
+        grads = torch.empty(1, 3, dtype=torch.float64, device="cuda")
+        L.pr_fine_adjoint(gm, L.Rng(4, 1), torch.tensor(x0, device="cuda"), torch.tensor(y0, device="cuda"), 1, 2, 3,
+                          steps, 1e-3, 16, xT, None, None, None, grads, None, None, ws)
+        torch.cuda.synchronize()
+        rx, _, dx, _ = orc.fine_tangent(om, 4, x0.astype(np.float64), y0.astype(np.float64), 2, 3, steps, 1e-3,
+                                        problem=1)
+        g = grads.cpu().numpy()[0]
+        ref = dx[0, :3]
+        assert np.all(np.abs(g - ref) <= 2e-3 * np.maximum(np.abs(ref), 1e-3)), (steps, g, ref)
+        assert abs(float(xT.item()) - rx[0]) <= 2e-3 * max(abs(rx[0]), 1.0)
