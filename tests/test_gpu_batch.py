@@ -128,3 +128,29 @@ def test_batched_workload_shape(L):
         ref, _ = _single(L, probs[i], i, xs[i], ys[i], 2)
         np.testing.assert_array_equal(b.rho(i).cpu().numpy(), ref[2])
     b.close()
+
+
+def test_batch_with_tiny_problems(L):
+    """Problems at the small end beside an ordinary one: one particle, one
+    slice, a single bin, an odd number of steps; each equals its
+    single-problem run bit for bit over three iterations."""
+    from paper_1912_09240_gb300.batch import BatchSolver
+    probs = [
+        L.Problem(L.Model(0, 1, 1.0, 1.0, 0.1), L.Grid(64, -4.0, 4.0), 1, 3, 11, 1e-3, 5),
+        L.Problem(L.Model(1, 1, 0.5, 3.0, 0.05), L.Grid(48, -3.0, 3.0), 777, 1, 20, 1e-3, 5),
+        L.Problem(L.Model(0, 1, 0.5, 2.0, 0.1), L.Grid(1, -4.0, 4.0), 300, 3, 9, 1e-3, 6),
+        L.Problem(L.Model(1, 1, 0.2, 1.0, 0.1), L.Grid(128, -2.5, 3.5), 4099, 4, 13, 5e-4, 3),
+    ]
+    xs, ys = _inits(probs)
+    iters = 3
+    b = BatchSolver(probs)
+    ref = [_single(L, p, i, xs[i], ys[i], iters) for i, p in enumerate(probs)]
+    b.set_initial(xs, ys)
+    for k in range(1, iters + 1):
+        b.iterate()
+        for i in range(len(probs)):
+            np.testing.assert_array_equal(b.rho(i).cpu().numpy(), ref[i][0][k], err_msg=f"k {k} p {i}")
+    for i in range(len(probs)):
+        np.testing.assert_array_equal(b.fine_state(i)[0].cpu().numpy(), ref[i][1])
+    assert b.status() == 0
+    b.close()
