@@ -263,3 +263,38 @@ def test_graph_mode_equals_eager(L, chunk):
     assert all(g is not None for g in s._graphs)
     assert int(s.status.item()) == 0
     s.close()
+
+
+@pytest.mark.parametrize("K", [1, 2])
+@pytest.mark.parametrize("chunk,graph", [(0, False), (1, False), (5, False), (0, True), (5, True)])
+def test_driver_with_one_or_two_slices(L, K, chunk, graph):
+    """One and two slices, chunks larger than the horizon, eager and graph
+    replay: every schedule equals the sequential one bit for bit, and after
+    iteration k the slices n <= k equal the serial fine solution (the
+    exactness theorem), so iteration K is the serial solution itself."""
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    w = workloads.DOUBLE_WELL.scaled(N=2049, K=K, T=0.02 * K, dt=1e-3, bins=64)
+    model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    x0, y0 = workloads.initial_ensemble(w)
+    gx, gy = (torch.tensor(v, dtype=torch.float32, device="cuda") for v in (x0, y0))
+
+    def run(ch, gr):
+        s = PararealSolver(model, L.Grid(w.bins, w.lo, w.hi), w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                           rng=L.Rng(w.seed, 0), chunk=ch, graph=gr)
+        s.set_initial(gx, gy)
+        rho = []
+        for _ in range(K + 2):
+            s.iterate()
+            rho.append(s.rho.cpu().numpy().copy())
+        _, _, rser = s.serial_reference()
+        assert int(s.status.item()) == 0
+        s.close()
+        return rho, rser.cpu().numpy()
+
+    ref, rser = run(0, False)
+    got, _ = run(chunk, graph)
+    for k in range(K + 2):
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=f"k={k}")
+    for j in range(K + 2):             # got[j] is iterate k = j + 1
+        for n in range(min(j + 1, K) + 1):
+            np.testing.assert_array_equal(got[j][n], rser[n], err_msg=f"k={j + 1} n={n}")
