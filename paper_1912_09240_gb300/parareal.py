@@ -366,6 +366,28 @@ class PararealSolver:
         L.pr_w1(self.grid, self.K + 1, self.rho, rho_ref, out, stream=self._s())
         return out
 
+    def increment(self) -> torch.Tensor:
+        """W1(rho_k^n, rho_{k-1}^n) for n = 0..K on the device: the change of
+        the macroscopic states in the latest iteration (k >= 1).  It needs no
+        serial solution, and by the exactness theorem it is 0 from iteration
+        K + 1 on."""
+        if self.k < 1:
+            raise RuntimeError("increment() needs at least one iteration after set_initial()")
+        out = torch.empty(self.K + 1, dtype=torch.float64, device=self.device)
+        L.pr_w1(self.grid, self.K + 1, self.rho, self._rho_next, out, stream=self._s())
+        return out
+
+    def run(self, tol: float, max_iters: int | None = None) -> int:
+        """Iterate until max_n increment() <= tol, or until iteration
+        max_iters (default K + 1, where the increment is 0); returns the
+        number of iterations taken.  One host synchronisation per iteration."""
+        limit = self.K + 1 if max_iters is None else max_iters
+        while self.k < limit:
+            self.iterate()
+            if float(self.increment().max().item()) <= tol:
+                break
+        return self.k
+
     def state(self):
         """The fine end states Xbar_{k-1}^{n}, n = 1..K, and rho_k (the iterate
         X_k^n is their matching against rho_k)."""

@@ -298,3 +298,36 @@ def test_driver_with_one_or_two_slices(L, K, chunk, graph):
     for j in range(K + 2):             # got[j] is iterate k = j + 1
         for n in range(min(j + 1, K) + 1):
             np.testing.assert_array_equal(got[j][n], rser[n], err_msg=f"k={j + 1} n={n}")
+
+
+@pytest.mark.parametrize("chunk,graph", [(0, False), (3, False), (3, True)])
+def test_increment_and_run(L, orc, chunk, graph):
+    """increment() is W1 between consecutive macroscopic iterates (checked
+    against the oracle's W1 on the host), it vanishes from iteration K + 1
+    on (the exactness theorem), and run(tol) stops at the first iteration
+    whose increment is within tol."""
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    w = workloads.DOUBLE_WELL.scaled(N=4099, K=6, T=0.06, dt=1e-3, bins=96)
+    model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    x0, y0 = workloads.initial_ensemble(w)
+    gx, gy = (torch.tensor(v, dtype=torch.float32, device="cuda") for v in (x0, y0))
+    og = orc.Grid(w.bins, w.lo, w.hi)
+    s = PararealSolver(model, L.Grid(w.bins, w.lo, w.hi), w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                       rng=L.Rng(w.seed, 0), chunk=chunk, graph=graph)
+    s.set_initial(gx, gy)
+    prev = s.rho.cpu().numpy().copy()
+    incs = []
+    for k in range(1, w.K + 2):
+        s.iterate()
+        cur = s.rho.cpu().numpy().copy()
+        inc = s.increment().cpu().numpy()
+        ref = np.array([orc.w1(og, cur[n], prev[n]) for n in range(w.K + 1)])
+        np.testing.assert_allclose(inc, ref, rtol=1e-12, atol=1e-15)
+        incs.append(inc.max())
+        prev = cur
+    assert incs[-1] == 0.0 and incs[0] > 0.0
+    tol = sorted(incs)[len(incs) // 2]
+    s.set_initial(gx, gy)
+    k = s.run(tol)
+    assert k == next(i + 1 for i, v in enumerate(incs) if v <= tol)
+    s.close()
