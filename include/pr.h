@@ -230,8 +230,8 @@ pr_status pr_reweight(pr_precision precision, const void* x_prior, int32_t broad
  * particle p with C_{p-1} <= U_j < C_p, where C_p are the cumulative weights
  * in fixed point (round(W 2^61) as 64-bit integers: exact in any summation
  * order), T = C_{n-1} and U_j = floor(T (j 2^24 + a_j) / (n 2^24)): a_j the
- * odd 24-bit integer of the uniform of word 0 of Philox block
- * (j, 0xFFFFFFFF, slice, problem_id << 8 | 0xFE) for PR_RESAMPLE_STRATIFIED,
+ * odd 24-bit integer of the uniform of word j mod 4 of Philox block
+ * (floor(j/4), 0xFFFFFFFF, slice, problem_id << 8 | 0xFE) for PR_RESAMPLE_STRATIFIED,
  * 2^23 (u~ = 1/2) for PR_RESAMPLE_DETERMINISTIC; slice = slice_begin + s.
  * Equal weights give output j = particle j (strong projection).  T = 0 (no
  * weight) gives the identity as well.  Weights are probability weights: their

@@ -713,9 +713,10 @@ uint64_t or_weight_fixed(double w)
  * u_j = (j + u~_j) / N, the points scaled by the total weight T.
  * Readings: the cumulative weights are taken in the fixed point above, so
  * that the selection is exact and independent of the order of summation;
- * u~_j = a_j / 2^24 with a_j the odd 24-bit integer of the uniform of word 0
- * of Philox block (j, 0xFFFFFFFF, slice, problem << 8 | 0xFE) (stratified,
- * mode 0) or a_j = 2^23 (u~ = 1/2, deterministic, mode 1); the point is
+ * u~_j = a_j / 2^24 with a_j the odd 24-bit integer of the uniform of word
+ * j mod 4 of Philox block (floor(j / 4), 0xFFFFFFFF, slice, problem << 8 |
+ * 0xFE) (stratified, mode 0: one block serves four consecutive outputs) or
+ * a_j = 2^23 (u~ = 1/2, deterministic, mode 1); the point is
  * U_j = floor(T (j 2^24 + a_j) / (N 2^24)); a point on a boundary goes to the
  * particle on its right (the paper's strict inequalities leave it to none).
  * With T = 0 (no weight at all) output j takes particle j.
@@ -739,10 +740,11 @@ void or_resample(const double* w, int64_t N, int n_slices, int mode, uint64_t se
             if (T == 0) { is[j] = (uint32_t)j; continue; }
             uint64_t a = (uint64_t)1 << 23;
             if (mode == 0) {
-                const uint32_t ctr[4] = {(uint32_t)j, 0xFFFFFFFFu, slice_begin + (uint32_t)s, (problem << 8) | 0xFEu};
+                const uint32_t ctr[4] = {(uint32_t)(j >> 2), 0xFFFFFFFFu, slice_begin + (uint32_t)s,
+                                         (problem << 8) | 0xFEu};
                 uint32_t out[4];
                 or_philox4x32_10(ctr, key, out);
-                a = 2 * (uint64_t)(out[0] >> 9) + 1;
+                a = 2 * (uint64_t)(out[j & 3] >> 9) + 1;
             }
             const unsigned __int128 num = (unsigned __int128)T * (((uint64_t)j << 24) + a);
             const uint64_t U = (uint64_t)(num / ((unsigned __int128)N << 24));

@@ -367,23 +367,38 @@ struct StrataPoint {
     int mode;
     uint32_t k0, k1, chi, slice;
 
+    // a_j of the stratified mode is the odd 24-bit integer of the uniform of
+    // word j mod 4 of Philox block floor(j / 4): one block serves four
+    // consecutive outputs.
+    __device__ __forceinline__ uint4 block_of(uint32_t jq) const
+    {
+        return philox4x32_10(make_uint4(jq, 0xFFFFFFFFu, slice, chi | 0xFEu), k0, k1);
+    }
+
+    __device__ __forceinline__ static uint32_t odd24(uint32_t w) { return 2u * (w >> 9) + 1u; }
+
     __device__ __forceinline__ uint32_t a_of(uint32_t j) const
     {
         if (mode != PR_RESAMPLE_STRATIFIED) return 1u << 23;
-        const uint4 wd = philox4x32_10(make_uint4(j, 0xFFFFFFFFu, slice, chi | 0xFEu), k0, k1);
-        return 2u * (wd.x >> 9) + 1u;
+        const uint4 wd = block_of(j >> 2);
+        const uint32_t r = j & 3u;
+        return odd24(r == 0 ? wd.x : r == 1 ? wd.y : r == 2 ? wd.z : wd.w);
     }
 
-    // U_j given q2 = floor(R j / n) and r2 = R j - q2 n
-    __device__ __forceinline__ uint64_t at(uint32_t j, uint32_t q2, uint32_t r2) const
+    // U_j given a_j, q2 = floor(R j / n) and r2 = R j - q2 n
+    __device__ __forceinline__ uint64_t at_a(uint32_t j, uint32_t q2, uint32_t r2, uint32_t a) const
     {
-        const uint32_t a = a_of(j);
         const uint64_t la = (uint64_t)Ql * a;                          // below 2^56
         const uint64_t P1 = (((uint64_t)Qh * a) << 8) + (la >> 24);   // floor(Q a / 2^24)
         const uint32_t m1 = (uint32_t)la & 0xFFFFFFu;
         const uint64_t W = (uint64_t)m1 * n + ((uint64_t)r2 << 24) + (uint64_t)R * a;
         const uint64_t f = W < D ? 0ull : (W < 2 * D ? 1ull : 2ull);
         return Q * (uint64_t)j + P1 + (uint64_t)q2 + f;
+    }
+
+    __device__ __forceinline__ uint64_t at(uint32_t j, uint32_t q2, uint32_t r2) const
+    {
+        return at_a(j, q2, r2, a_of(j));
     }
 
     __device__ __forceinline__ void divmod_Rj(uint32_t j, uint32_t& q2, uint32_t& r2) const
@@ -444,6 +459,7 @@ __device__ __forceinline__ int64_t first_above(const uint64_t* __restrict__ C, i
 constexpr int kSelThreads = 256;
 constexpr int kSelPer = 8;
 constexpr int kSelOut = kSelThreads * kSelPer;   // consecutive outputs per CTA
+static_assert(kSelPer % 4 == 0, "a thread's outputs start on a Philox block of the strata draws");
 constexpr int kSelStage = 4096;                  // cumulative weights staged per CTA
 
 // The particles of the first and last output of every selection CTA: one
@@ -509,8 +525,9 @@ __device__ __forceinline__ Idx sel_gallop(const V& v, Idx a, Idx hi, uint64_t u)
 
 __device__ __forceinline__ int sel_pad(int i) { return i + (i >> 5); }
 
-// A thread's kSelPer consecutive outputs from jj0 on: their strata points
-// first (independent Philox blocks, all in flight), then a search for the
+// A thread's kSelPer consecutive outputs from jj0 on (j0 + jj0 a multiple of
+// kSelPer, so they take whole Philox blocks of four draws): their strata
+// points first (independent blocks, all in flight), then a search for the
 // first particle and a gallop from the previous one for the rest; the
 // particles, relative to `base`, go to sp.
 template <typename V, typename Idx>
@@ -520,10 +537,24 @@ __device__ __forceinline__ void select_run(const V& v, Idx base, Idx hi, const S
     const uint32_t j = j0 + (uint32_t)jj0;
     uint32_t q2, r2;
     U.divmod_Rj(j, q2, r2);
+    uint32_t a[kSelPer];
+    if (U.mode == PR_RESAMPLE_STRATIFIED) {
+#pragma unroll
+        for (int b = 0; b < kSelPer / 4; ++b) {
+            const uint4 wd = U.block_of((j >> 2) + (uint32_t)b);
+            a[4 * b] = StrataPoint::odd24(wd.x);
+            a[4 * b + 1] = StrataPoint::odd24(wd.y);
+            a[4 * b + 2] = StrataPoint::odd24(wd.z);
+            a[4 * b + 3] = StrataPoint::odd24(wd.w);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kSelPer; ++k) a[k] = 1u << 23;
+    }
     uint64_t u[kSelPer];
 #pragma unroll
     for (int k = 0; k < kSelPer; ++k) {
-        u[k] = U.at(j + (uint32_t)k, q2, r2);   // past the end: unused
+        u[k] = U.at_a(j + (uint32_t)k, q2, r2, a[k]);   // past the end: unused
         U.step(q2, r2);
     }
     const int m = min(kSelPer, cnt - jj0);
@@ -538,18 +569,19 @@ __device__ __forceinline__ void select_run(const V& v, Idx base, Idx hi, const S
     }
 }
 
-// Copies rows[j] = src[p_j] for the kSelPer outputs of this thread, all loads
-// issued before the stores.
+// Copies dst[k kSelThreads] = src[pr[k]] for the kSelPer outputs of this
+// thread (src starting at the CTA's first particle, dst at the thread's first
+// output), all loads issued before the stores.
 template <typename T>
-__device__ __forceinline__ void gather_rows(const T* __restrict__ src, T* __restrict__ dst, const int64_t* pv,
-                                            const int64_t* jv, int valid)
+__device__ __forceinline__ void gather_rows(const T* __restrict__ src, T* __restrict__ dst, const uint32_t* pr,
+                                            int valid)
 {
     T v[kSelPer];
 #pragma unroll
-    for (int k = 0; k < kSelPer; ++k) v[k] = k < valid ? src[pv[k]] : T(0);
+    for (int k = 0; k < kSelPer; ++k) v[k] = k < valid ? src[pr[k]] : T(0);
 #pragma unroll
     for (int k = 0; k < kSelPer; ++k)
-        if (k < valid) dst[jv[k]] = v[k];
+        if (k < valid) dst[k * kSelThreads] = v[k];
 }
 
 // One CTA takes kSelOut consecutive outputs, whose particles lie between
@@ -602,25 +634,24 @@ select_gather_kernel(const uint64_t* __restrict__ C, const uint64_t* __restrict_
     }
     __syncthreads();
     // output jj = threadIdx.x + k kSelThreads of this CTA
+    // particles relative to lo (below 2^32: p < n <= 2^32 - 1), outputs at
+    // j0 + threadIdx.x + k kSelThreads
     const int valid = max(0, min(kSelPer, (cnt - (int)threadIdx.x + kSelThreads - 1) / kSelThreads));
-    int64_t pv[kSelPer], jv[kSelPer];
+    uint32_t pr[kSelPer];
 #pragma unroll
-    for (int k = 0; k < kSelPer; ++k) {
-        const int jj = threadIdx.x + k * kSelThreads;
-        pv[k] = k < valid ? lo + sp[sel_pad(jj)] : 0;
-        jv[k] = j0 + jj;
-    }
+    for (int k = 0; k < kSelPer; ++k) pr[k] = k < valid ? sp[sel_pad(threadIdx.x + k * kSelThreads)] : 0u;
     const int64_t si = broadcast ? 0 : s;   // the input slice (one shared by all with broadcast)
+    const int64_t jt = j0 + threadIdx.x;
     if (idx) {
-        uint32_t* o = idx + (int64_t)s * n;
+        uint32_t* o = idx + (int64_t)s * n + jt;
 #pragma unroll
         for (int k = 0; k < kSelPer; ++k)
-            if (k < valid) o[jv[k]] = (uint32_t)pv[k];
+            if (k < valid) o[k * kSelThreads] = (uint32_t)lo + pr[k];
     }
-    if (x_out) gather_rows(x_in + si * n, x_out + (int64_t)s * n, pv, jv, valid);
+    if (x_out) gather_rows(x_in + si * n + lo, x_out + (int64_t)s * n + jt, pr, valid);
     if (y_out)
         for (int c = 0; c < d; ++c)
-            gather_rows(y_in + (si * d + c) * n, y_out + ((int64_t)s * d + c) * n, pv, jv, valid);
+            gather_rows(y_in + (si * d + c) * n + lo, y_out + ((int64_t)s * d + c) * n + jt, pr, valid);
 }
 
 // ---------------------------------------------------------------------------
