@@ -39,6 +39,19 @@ each (two graphs, one per binding of the double buffers), which removes the
 per-launch host cost that dominates small workloads.  In pipelined graph mode
 the chunks still overlap within an iteration; consecutive iterations are
 ordered by the graph launches themselves.
+
+Skipping converged slices (``skip_converged=True``, exactness property of
+Section 3.2.4): iterate k is the serial fine solution on slices n <= k, so
+iteration k >= 1 need not propagate slices n < k again -- their start states
+are those of iteration k - 1, and so are their fine results.  Iteration k
+launches the fine work of slices k..K-1 only (K(K-1)/2 slice propagations
+fewer over K iterations) and takes slice k - 1's results, the last ones not
+yet in both halves of the double buffers, from the previous iteration's
+half.  The results are those of the full iteration bit for bit wherever the
+iterator meets J(a, b, a) = b bit for bit (the quantile iterator); with the
+other iterators the skipped slices keep the serial fine result exactly,
+where recomputing them would reproduce it within rounding.  Not combined
+with graph mode (the work changes from one iteration to the next).
 """
 from __future__ import annotations
 
@@ -54,10 +67,13 @@ class PararealSolver:
     def __init__(self, model: L.Model, grid: L.Grid, n: int, K: int, steps: int, dt: float,
                  precision: int = L.PR_F32, rng: L.Rng = L.Rng(), iterator: int = L.PR_ITER_QUANTILE,
                  qmode: int = L.PR_QMODE_TWO_SIDED, device: str = "cuda", stream=None, chunk: int = 0,
-                 graph: bool = False, matching: str = "quantile"):
+                 graph: bool = False, matching: str = "quantile", skip_converged: bool = False):
         if matching not in MATCHINGS:
             raise ValueError(f"matching must be one of {MATCHINGS}")
+        if skip_converged and graph:
+            raise ValueError("skip_converged changes the work of every iteration: it cannot be graph-replayed")
         self.matching = matching
+        self.skip_converged = bool(skip_converged)
         self.model, self.grid, self.n, self.K, self.steps, self.dt = model, grid, n, K, steps, dt
         self.precision, self.rng, self.iterator, self.qmode = precision, rng, iterator, qmode
         self.device = torch.device(device)
@@ -265,11 +281,27 @@ class PararealSolver:
         self._swaps += 1
         self.k += 1
 
+    def _carry(self, stream):
+        """Slice k - 1 of this iteration's outputs, taken from the previous
+        iteration's (the start state of slice k - 1 is exact in both)."""
+        m = self.k - 1
+        with torch.cuda.stream(stream):
+            self.xb[m].copy_(self.xa[m])
+            self.yb[m].copy_(self.ya[m])
+            self.f_star[m].copy_(self.f_star_prev[m])
+            if self.matching == "reweight":
+                self.w[m].copy_(self.w_prev[m])
+
     def _enqueue(self, s, first: bool, in_graph: bool):
         """Enqueue one iteration behind the work already on stream `s`."""
         K = self.K
+        # with skip_converged, slices n < k keep the previous iteration's results
+        lo = self.k if self.skip_converged else 0
+        carry = self.skip_converged and 1 <= self.k <= K
         if not self.chunk:
-            self._fine(0, K, first, s)
+            if carry:
+                self._carry(s)
+            self._fine(lo, K, first, s)
             L.pr_coarse_fp(self.coarse, self.start, self.c_star, K, stream=s)
             L.pr_parareal_update(self.coarse, self.iterator, self.qmode, K, self.cdf0, self.f_star, self.c_star,
                                  self._rho_next, self._status[0], stream=s)
@@ -289,7 +321,9 @@ class PararealSolver:
                 for ev in (self._ev_upd[c], self._ev_fine[c + 1] if c + 1 < nch else None):
                     if ev is not None:
                         sf.wait_event(ev)
-            self._fine(a, b, first, sf, role=c % 2)
+            if carry and a <= self.k - 1 < b:
+                self._carry(sf)
+            self._fine(max(a, lo), b, first, sf, role=c % 2)
             ef = torch.cuda.Event()
             ef.record(sf)
             new_fine[c] = ef
