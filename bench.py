@@ -240,9 +240,18 @@ def _unfused_leg(L, solver, w, stream, hbm_peak):
     t_u = _ev_time(lambda r: L.pr_parareal_update(solver.coarse, L.PR_ITER_QUANTILE, L.PR_QMODE_TWO_SIDED, K,
                                                   solver.cdf0, solver.f_star, solver.c_star, solver._rho_next,
                                                   solver._status[0], stream=stream), stream, 20)
+    # Monte Carlo estimator (Eq. MCestimator): mean and second moment of x per slice
+    import torch
+    mom = torch.empty(S, 2, dtype=torch.float64, device=solver.x0.device)
+    mws = torch.empty(L.pr_moments_workspace(n, S, 2), dtype=torch.uint8, device=solver.x0.device)
+    t_e = _ev_time(lambda r: L.pr_moments(L.PR_F32, bufs[r % 2], n, None, n, S, 2, mom, mws, stream=stream),
+                   stream, 10)
     rb, mb = 4.0 * n * S, 8.0 * n * S
     out = {"restrict": {"ms": t_r, "algorithmic_bytes": rb, "gbs": rb / t_r / 1e6},
            "match": {"ms": t_m, "algorithmic_bytes": mb, "gbs": mb / t_m / 1e6},
+           "moments_q2": {"ms": t_e, "algorithmic_bytes": rb, "gbs": rb / t_e / 1e6,
+                          "fp64_ops_per_particle": 2,
+                          "fp64_ops_per_s": 2.0 * n * S / t_e / 1e-3},
            "coarse_fp_us": 1e3 * t_c, "serial_sweep_us": 1e3 * t_u,
            "note": f"{S} slices x {n} binary32 particles; coarse step on {K} states of {w.bins} bins; "
                    f"sweep over {K} slices"}

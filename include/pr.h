@@ -267,6 +267,31 @@ pr_status pr_restrict_weighted(pr_precision precision, const void* x, int32_t br
                                size_t workspace_bytes, void* stream);
 
 /*
+ * Monte Carlo estimator (Section 2.1.3, Eq. MCestimator) of the power
+ * observables M = v^q, q = 1..max_order (max_order <= 4), of one coordinate v
+ * of each slice's ensemble (the slow variable, or one fast component):
+ *   out[s][q-1] = sum_p W^p (v^p)^q,
+ * W^p = w[s][p] when w is given, else 1/n (taken as the sum divided by n).
+ * Binary64 accumulation (each term added by one fused multiply-add) in a
+ * fixed order that depends only on n and n_slices, so repeated calls return
+ * the same bits.
+ *   v (device) precision as given; slice s starts slice_stride elements after
+ *     slice s-1 (n for x[n_slices][n]; fast_dim * n for component c of
+ *     y[n_slices][fast_dim][n], passing y + c * n); slice_stride >= n when
+ *     n_slices > 1
+ *   w (device) [n_slices][n] double, or NULL for uniform weights
+ *   out (device) [n_slices][max_order] double
+ *   workspace (device) >= pr_moments_workspace(n, n_slices, max_order) bytes,
+ *     8-byte aligned
+ * PR_ERR_INVALID_ARG for max_order outside 1..4, a short or misaligned
+ * workspace, or a stride that makes slices overlap.
+ */
+size_t pr_moments_workspace(int64_t n, int32_t n_slices, int32_t max_order);
+pr_status pr_moments(pr_precision precision, const void* v, int64_t slice_stride, const double* w, int64_t n,
+                     int32_t n_slices, int32_t max_order, double* out, void* workspace, size_t workspace_bytes,
+                     void* stream);
+
+/*
  * Coarse propagator C_dT (Section 2.2.2): finite volumes on the detailed-
  * balance form of the averaged Fokker-Planck equation (Eq. FPz_rewritten),
  * central differences for the fluxes, zero flux at x_lo and x_hi, and an

@@ -784,3 +784,24 @@ void or_restrict_weighted(const double* x, const double* w, int64_t N, int n_sli
     }
     free(h);
 }
+
+/* Monte Carlo estimator (Section 2.1.3, Eq. MCestimator) of the observables
+ * M = v^q, q = 1..Q: out[s][q-1] = sum over p, in order, of W^p (v^p)^q, the
+ * term built as W^p multiplied by v^p q times.  Without weights (w NULL)
+ * W^p = 1/n, read as the sum of (v^p)^q divided by n.
+ * v: slice s at v + s * stride; w: [n_slices][n]; out: [n_slices][Q]. */
+void or_moments(const double* v, int64_t stride, const double* w, int64_t n, int n_slices, int Q, double* out)
+{
+    for (int s = 0; s < n_slices; ++s) {
+        for (int q = 1; q <= Q; ++q) {
+            double sum = 0.0;
+            for (int64_t p = 0; p < n; ++p) {
+                const double x = v[(int64_t)s * stride + p];
+                double t = w ? w[(int64_t)s * n + p] : 1.0;
+                for (int r = 0; r < q; ++r) t = t * x;
+                sum = sum + t;
+            }
+            out[s * Q + q - 1] = w ? sum : sum / (double)n;
+        }
+    }
+}

@@ -82,6 +82,7 @@ def lib():
         _lib.or_weight_fixed.restype = u64
         _lib.or_resample.argtypes = [vp, i64, i32, i32, u64, u32, u32, vp]
         _lib.or_restrict_weighted.argtypes = [vp, vp, i64, i32, i32, d, d, vp]
+        _lib.or_moments.argtypes = [vp, i64, vp, i64, i32, i32, vp]
     return _lib
 
 
@@ -297,6 +298,19 @@ def restrict_weighted(x: np.ndarray, w: np.ndarray, grid: Grid) -> np.ndarray:
     cdf = np.empty((n_slices, grid.bins + 1))
     lib().or_restrict_weighted(_p(x), _p(w), N, n_slices, grid.bins, grid.lo, grid.hi, _p(cdf))
     return cdf
+
+
+def moments(v: np.ndarray, Q: int, w: np.ndarray | None = None) -> np.ndarray:
+    """Monte Carlo estimator (Eq. MCestimator) of v^q, q = 1..Q, per slice:
+    [n_slices][Q], weights w [n_slices][n] or uniform 1/n."""
+    v = np.ascontiguousarray(np.atleast_2d(v), dtype=np.float64)
+    n_slices, n = v.shape
+    if w is not None:
+        w = np.ascontiguousarray(np.atleast_2d(w), dtype=np.float64)
+        assert w.shape == v.shape
+    out = np.empty((n_slices, Q))
+    lib().or_moments(_p(v), n, None if w is None else _p(w), n, n_slices, Q, _p(out))
+    return out
 
 
 QMODE_TWO_SIDED, QMODE_MIDPOINT = 0, 1

@@ -30,7 +30,7 @@ EXPORTED = (
     "pr_batch_create", "pr_batch_destroy", "pr_batch_particle_steps", "pr_batch_set_initial", "pr_batch_iterate",
     "pr_batch_rho", "pr_batch_fine_state", "pr_batch_status", "pr_batch_set_config", "pr_batch_get_config",
     "pr_batch_tune", "pr_reweight", "pr_resample_workspace", "pr_resample", "pr_restrict_weighted_workspace",
-    "pr_restrict_weighted",
+    "pr_restrict_weighted", "pr_moments_workspace", "pr_moments",
 )
 
 
@@ -174,11 +174,15 @@ def lib() -> ctypes.CDLL:
     L.pr_restrict_weighted_workspace.argtypes = [i32, i32]
     L.pr_restrict_weighted_workspace.restype = ctypes.c_size_t
     L.pr_restrict_weighted.argtypes = [i32, vp, i32, vp, i64, i32, P(_Grid), vp, vp, ctypes.c_size_t, vp]
+    L.pr_moments_workspace.argtypes = [i64, i32, i32]
+    L.pr_moments_workspace.restype = ctypes.c_size_t
+    L.pr_moments.argtypes = [i32, vp, i64, vp, i64, i32, i32, vp, vp, ctypes.c_size_t, vp]
     for name in EXPORTED:
         if name not in ("pr_status_string", "pr_version", "pr_set_particles_per_thread",
                         "pr_set_tiles_per_cta", "pr_set_update_cluster", "pr_fine_adjoint_workspace",
                         "pr_order_statistics_workspace", "pr_fine_adjoint_noalloc_capacity",
-                        "pr_batch_particle_steps", "pr_resample_workspace", "pr_restrict_weighted_workspace"):
+                        "pr_batch_particle_steps", "pr_resample_workspace", "pr_restrict_weighted_workspace",
+                        "pr_moments_workspace"):
             getattr(L, name).restype = i32
     _lib = L
     return L
@@ -363,6 +367,17 @@ def pr_restrict_weighted(precision: int, x, broadcast_input: bool, w, n: int, n_
                                                               _ptr(w), n, n_slices,
                                                               ctypes.byref(g), _ptr(cdf), _ptr(workspace), wbytes,
                                                               _stream(stream)))
+
+
+def pr_moments_workspace(n: int, n_slices: int, max_order: int) -> int:
+    return lib().pr_moments_workspace(n, n_slices, max_order)
+
+
+def pr_moments(precision: int, v, slice_stride: int, w, n: int, n_slices: int, max_order: int, out, workspace,
+               stream=None):
+    wbytes = workspace.numel() * workspace.element_size()
+    _check("pr_moments", lib().pr_moments(precision, _ptr(v), slice_stride, _ptr(w), n, n_slices, max_order,
+                                          _ptr(out), _ptr(workspace), wbytes, _stream(stream)))
 
 
 def pr_order_statistics(x, n: int, ranks, n_ranks: int, index_out, workspace, stream=None):

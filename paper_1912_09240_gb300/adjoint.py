@@ -79,8 +79,9 @@ def second_moment_gradient(model: L.Model, rng: L.Rng, x0, y0, slice_begin: int,
     L.pr_fine_adjoint_affine(model, rng, x0.reshape(n).to(torch.float32).contiguous(),
                              y0.reshape(n).to(torch.float32).contiguous(), n, slice_begin, n_slices, steps, dt,
                              ckpt_every, 2.0 / n, 0.0, xT, None, grad, None, None, ws)
-    value = (xT.to(torch.float64) ** 2).mean()
-    return value, grad
+    moments = torch.empty(2, dtype=torch.float64, device=dev)   # E[X_T], E[X_T^2] (Eq. MCestimator)
+    L.pr_moments(L.PR_F32, xT, n, None, n, 1, 2, moments, _workspace(L.pr_moments_workspace(n, 1, 2), dev))
+    return moments[1], grad
 
 
 def quantile_gradient(model: L.Model, rng: L.Rng, x0, y0, slice_begin: int, n_slices: int, steps: int, dt: float,

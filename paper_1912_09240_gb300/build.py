@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fine.cu", "coarse.cu", "adjoint.cu", "batch.cu", "conditional.cu"]
+SOURCES = ["fine.cu", "coarse.cu", "adjoint.cu", "batch.cu", "conditional.cu", "estimator.cu"]
 
 
 def nvcc() -> str:

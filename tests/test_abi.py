@@ -139,3 +139,25 @@ def test_affine_adjoint_rejects_non_finite_seeds(L):
                                       None, None, None, None, None, ws, need, None) == L.PR_ERR_INVALID_ARG
     assert lib.pr_fine_adjoint_affine(ctypes.byref(m), ctypes.byref(r), fake, fake, 100, 0, 2, 10, 1e-3, 12, 1.0, 0.0,
                                       None, None, fake, None, None, ws, need - 1, None) == L.PR_ERR_INVALID_ARG
+
+
+def test_moments_rejects_bad_arguments(L):
+    lib = L.lib()
+    fake = ctypes.c_void_p(0x10000)
+    need = lib.pr_moments_workspace(1000, 2, 3)
+    assert need >= 2 * 3 * 8
+    assert lib.pr_moments_workspace(1000, 2, 0) == 0 and lib.pr_moments_workspace(1000, 2, 5) == 0
+    ok = dict(prec=0, v=fake, stride=1000, w=None, n=1000, s=2, q=3, out=fake, ws=fake, nb=need)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return lib.pr_moments(a["prec"], a["v"], a["stride"], a["w"], a["n"], a["s"], a["q"], a["out"], a["ws"],
+                              a["nb"], None)
+    assert call(prec=3) == L.PR_ERR_INVALID_ARG
+    assert call(q=0) == L.PR_ERR_INVALID_ARG
+    assert call(q=5) == L.PR_ERR_INVALID_ARG
+    assert call(stride=999) == L.PR_ERR_INVALID_ARG          # slices would overlap
+    assert call(nb=need - 1) == L.PR_ERR_INVALID_ARG
+    assert call(ws=ctypes.c_void_p(0x10004)) == L.PR_ERR_INVALID_ARG
+    assert call(v=None) == L.PR_ERR_INVALID_ARG
+    assert call(n=0) == L.PR_ERR_INVALID_ARG
