@@ -438,25 +438,23 @@ restrict_kernel(const T* __restrict__ x, int64_t n, GridDev g, float lo_f, float
                 uint32_t* __restrict__ counts, int64_t per_block)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ float s_thr[2];
     const int bins = g.bins;
     uint32_t* hist = reinterpret_cast<uint32_t*>(smem);
+    float* thr = reinterpret_cast<float*>(hist + bins);   // binary32 thresholds, bins + 1
     const int s = blockIdx.y;
-    if (threadIdx.x == 0) {
-        s_thr[0] = __double2float_ru(edge(g, 0));
-        s_thr[1] = __double2float_ru(edge(g, bins));
-    }
+    if (sizeof(T) == 4) build_thresholds(g, thr);
     for (int i = threadIdx.x; i < bins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
     const T* xs = x + (int64_t)s * n;
     const int64_t b = (int64_t)blockIdx.x * per_block;
     const int64_t e = min(n, b + per_block);
     if (sizeof(T) == 4) {
-        // thresholds are computed only for the few particles near an edge,
-        // decided once per group of values so that the common case has no
-        // divergent branch
-        const BinF32 bf = make_bin_f32(s_thr[0], s_thr[1], bins, lo_f, inv_h_f);
-        const auto thr_of = [g](int k) { return __double2float_ru(edge(g, k)); };
+        // the thresholds (built once per CTA, binary64 edges rounded up to
+        // binary32) are read only for the few particles near an edge, decided
+        // once per group of values so that the common case has no divergent
+        // branch and no binary64 arithmetic
+        const BinF32 bf = make_bin_f32(thr, bins, lo_f, inv_h_f);
+        const auto thr_of = [thr](int k) { return thr[k]; };
         auto group4 = [&](float4 u, int m) {
             int i0 = bin_try_f32(bf, u.x);
             int i1 = m > 1 ? bin_try_f32(bf, u.y) : 0;
@@ -826,7 +824,7 @@ extern "C" pr_status pr_restrict(pr_precision precision, const void* x, int64_t 
     // one wave of 512-thread CTAs (4 per SM), each a contiguous range of one slice
     const int64_t per_block = stream_range(n, n_slices, 4096, 4);
     const int64_t blocks_per_slice = (n + per_block - 1) / per_block;
-    const size_t smem = align16((size_t)bins * 4);
+    const size_t smem = align16((size_t)bins * 4 + (size_t)(bins + 1) * 4);
     dim3 gr((unsigned)blocks_per_slice, (unsigned)n_slices);
     if (precision == PR_F32) {
         restrict_kernel<float><<<gr, 512, smem, st>>>(static_cast<const float*>(x), n, g, lo_f, inv_h_f, counts, per_block);
