@@ -428,6 +428,25 @@ class PararealSolver:
         self.join()
         return self.xa, self.ya, self._rho
 
+    def moments(self, max_order: int = 2, component: int = -1) -> torch.Tensor:
+        """Monte Carlo estimates (Eq. MCestimator) of v^q, q = 1..max_order, over
+        the fine end states Xbar_{k-1}^{n}, n = 1..K: [K][max_order], v the
+        slow variable (component -1) or fast component `component`, with the
+        weights those states carry (matching "reweight") or 1/N."""
+        self.join()
+        K, n, d = self.K, self.n, self.model.fast_dim
+        if component >= 0:
+            if component >= d:
+                raise ValueError("component out of range")
+            v, stride = self.ya.reshape(-1)[component * n:], d * n
+        else:
+            v, stride = self.xa, n
+        w = self.w_prev if self.matching == "reweight" else None
+        out = torch.empty(K, max_order, dtype=torch.float64, device=self.device)
+        ws = self._scratch("mom", 0, L.pr_moments_workspace(n, K, max_order))
+        L.pr_moments(self.precision, v, stride, w, n, K, max_order, out, ws, stream=self._s())
+        return out
+
     def weights(self):
         """Weights carried by the fine end states (matching "reweight"; slice 0
         and the other matchings: uniform 1/N)."""

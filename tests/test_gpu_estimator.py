@@ -110,3 +110,32 @@ def test_second_moment_helper_uses_the_estimator(L, orc):
     torch.cuda.synchronize()
     ref = orc.moments(x.double().cpu().numpy(), 2)[0, 1]
     assert abs(float(val) - ref) <= 1e-13 * ref
+
+
+@pytest.mark.parametrize("matching", ["quantile", "reweight"])
+def test_solver_moments(L, orc, matching):
+    """PararealSolver.moments(): the estimator over the fine end states of the
+    latest iteration, slow variable and a fast component, with the weights
+    those states carry."""
+    import workloads
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    w = workloads.LARGE_FAST.scaled(N=3001, K=5, T=0.05, dt=1e-3, bins=64, fast_dim=3, eps=0.1)
+    model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    s = PararealSolver(model, L.Grid(w.bins, w.lo, w.hi), w.N, w.K, w.steps, w.step_dt, rng=L.Rng(w.seed, 0),
+                       matching=matching)
+    x0, y0 = workloads.initial_ensemble(w)
+    s.set_initial(torch.tensor(x0, dtype=torch.float32, device=DEV), torch.tensor(y0, dtype=torch.float32, device=DEV))
+    for _ in range(2):
+        s.iterate()
+    xa, ya, _ = s.state()
+    wts = s.weights()
+    wn = wts.cpu().numpy() if wts is not None else None
+    got_x = s.moments(3).cpu().numpy()
+    got_y = s.moments(2, component=1).cpu().numpy()
+    v64 = xa.double().cpu().numpy()
+    _check(got_x, orc.moments(v64, 3, wn), v64, wn, 3)
+    y64 = ya[:, 1, :].double().cpu().numpy()
+    _check(got_y, orc.moments(y64, 2, wn), y64, wn, 2)
+    with pytest.raises(ValueError):
+        s.moments(2, component=3)
+    s.close()
