@@ -35,24 +35,6 @@ static int64_t moments_blocks(int64_t n, int32_t n_slices)
     return std::min<int64_t>(cap, std::max<int64_t>(1, (n + kMomPerBlock - 1) / kMomPerBlock));
 }
 
-// The binary64 value of a binary32 number, built from its encoding on the
-// integer units (exponent rebiased by 1023 - 127, mantissa moved up by 29
-// bits) for normal numbers and zeros; subnormals, infinities and NaNs take
-// the conversion instruction.  Exact either way.
-__device__ __forceinline__ double widen(float f)
-{
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xFFu;
-    if (e - 1u < 254u) {
-        const uint32_t hi = (u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + 0x38000000u);
-        return __hiloint2double((int)hi, (int)(u << 29));
-    }
-    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-    return (double)f;
-}
-
-__device__ __forceinline__ double widen(double d) { return d; }
-
 template <typename T, int Q, bool W>
 __global__ void __launch_bounds__(kMomThreads)
 moments_kernel(const T* __restrict__ v, int64_t stride, const double* __restrict__ w, int64_t n, int64_t per_block,

@@ -286,6 +286,25 @@ __device__ __forceinline__ void build_thresholds(const GridDev& g, float* thr)
     for (int i = threadIdx.x; i <= g.bins; i += blockDim.x) thr[i] = __double2float_ru(edge(g, i));
 }
 
+// The binary64 value of a binary32 number, built from its encoding on the
+// integer units (exponent rebiased by 1023 - 127, mantissa moved up by 29
+// bits) for normal numbers and zeros; subnormals, infinities and NaNs take
+// the conversion instruction.  Exact either way.  On GB300 the conversion
+// instruction occupies the narrow binary64 pipe.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    if (e - 1u < 254u) {
+        const uint32_t hi = (u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + 0x38000000u);
+        return __hiloint2double((int)hi, (int)(u << 29));
+    }
+    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+}
+
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // Equality of two non-NaN doubles by their bits (+0 and -0 equal), on the
 // integer units.
 __device__ __forceinline__ bool deq(double a, double b)
