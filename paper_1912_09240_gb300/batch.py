@@ -74,6 +74,33 @@ class BatchSolver:
     def status(self) -> int:
         return L.pr_batch_status(self.plan, stream=self._s())
 
+    def _w1(self, problem: int, a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+        p = self.problems[problem]
+        out = torch.empty(p.n_slices + 1, dtype=torch.float64, device=self.device)
+        L.pr_w1(p.grid, p.n_slices + 1, a, b, out, stream=self._s())
+        return out
+
+    def run(self, tol: float, max_iters: int | None = None) -> tuple[int, torch.Tensor]:
+        """Iterate until every problem's increment max_n W1(rho_k^n, rho_{k-1}^n)
+        is within `tol` (no serial solution needed; by the exactness theorem it
+        is 0 once k exceeds the problem's slice count), or until max_iters
+        (default: the largest slice count + 1).  Returns the iterations taken
+        and the last increments [n_problems] (device).  One host
+        synchronisation per iteration."""
+        limit = max(p.n_slices for p in self.problems) + 1 if max_iters is None else max_iters
+        prev = [self.rho(i) for i in range(len(self.problems))]
+        inc = torch.full((len(self.problems),), float("inf"), dtype=torch.float64, device=self.device)
+        k = 0
+        while k < limit:
+            self.iterate()
+            k += 1
+            cur = [self.rho(i) for i in range(len(self.problems))]
+            inc = torch.stack([self._w1(i, cur[i], prev[i]).max() for i in range(len(self.problems))])
+            if float(inc.max().item()) <= tol:
+                break
+            prev = cur
+        return k, inc
+
     def tune(self, steps_div: int = 8) -> float:
         return L.pr_batch_tune(self.plan, steps_div, stream=self._s())
 

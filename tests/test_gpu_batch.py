@@ -154,3 +154,33 @@ def test_batch_with_tiny_problems(L):
         np.testing.assert_array_equal(b.fine_state(i)[0].cpu().numpy(), ref[i][1])
     assert b.status() == 0
     b.close()
+
+
+def test_batch_run_to_tolerance(L, orc):
+    """BatchSolver.run(tol): stops at the first iteration where every
+    problem's change of its macroscopic states is within tol (the increments
+    against the oracle's W1 of the host copies), and its states equal those
+    of iterating that many times."""
+    from paper_1912_09240_gb300.batch import BatchSolver
+    probs = _problems(L)
+    xs, ys = _inits(probs)
+    a = BatchSolver(probs)
+    a.set_initial(xs, ys)
+    k, inc = a.run(1e-3)
+    inc = inc.cpu().numpy()
+    assert 1 <= k <= max(p.n_slices for p in probs) + 1
+    assert np.all(inc <= 1e-3), inc
+    b = BatchSolver(probs)
+    b.set_initial(xs, ys)
+    for _ in range(k - 1):
+        b.iterate()
+    before = [b.rho(i).cpu().numpy() for i in range(len(probs))]
+    b.iterate()
+    for i, p in enumerate(probs):
+        after = b.rho(i).cpu().numpy()
+        np.testing.assert_array_equal(after, a.rho(i).cpu().numpy())
+        og = orc.Grid(p.grid.bins, p.grid.lo, p.grid.hi)
+        ref = max(orc.w1(og, after[n], before[i][n]) for n in range(p.n_slices + 1))
+        assert abs(ref - inc[i]) <= 1e-12 + 1e-9 * ref, (i, ref, inc[i])
+    a.close()
+    b.close()
