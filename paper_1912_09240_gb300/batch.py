@@ -80,6 +80,16 @@ class BatchSolver:
         L.pr_w1(p.grid, p.n_slices + 1, a, b, out, stream=self._s())
         return out
 
+    def snapshot(self) -> list[torch.Tensor]:
+        """Copies of every problem's macroscopic states rho_k (device)."""
+        return [self.rho(i) for i in range(len(self.problems))]
+
+    def increments(self, prev: list[torch.Tensor], cur: list[torch.Tensor] | None = None) -> torch.Tensor:
+        """max_n W1(cur^n, prev^n) per problem [n_problems] (device); cur
+        defaults to the current states."""
+        cur = self.snapshot() if cur is None else cur
+        return torch.stack([self._w1(i, cur[i], prev[i]).max() for i in range(len(self.problems))])
+
     def run(self, tol: float, max_iters: int | None = None) -> tuple[int, torch.Tensor]:
         """Iterate until every problem's increment max_n W1(rho_k^n, rho_{k-1}^n)
         is within `tol` (no serial solution needed; by the exactness theorem it
@@ -88,14 +98,14 @@ class BatchSolver:
         and the last increments [n_problems] (device).  One host
         synchronisation per iteration."""
         limit = max(p.n_slices for p in self.problems) + 1 if max_iters is None else max_iters
-        prev = [self.rho(i) for i in range(len(self.problems))]
+        prev = self.snapshot()
         inc = torch.full((len(self.problems),), float("inf"), dtype=torch.float64, device=self.device)
         k = 0
         while k < limit:
             self.iterate()
             k += 1
-            cur = [self.rho(i) for i in range(len(self.problems))]
-            inc = torch.stack([self._w1(i, cur[i], prev[i]).max() for i in range(len(self.problems))])
+            cur = self.snapshot()
+            inc = self.increments(prev, cur)
             if float(inc.max().item()) <= tol:
                 break
             prev = cur
