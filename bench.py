@@ -850,8 +850,7 @@ def run_ours(args):
         batched["increments"] = {"tol": 1e-3, "problems_within_tol_per_iteration": within,
                                  "max_increment_per_iteration": worst,
                                  "note": "increment = max over slices of W1 between consecutive iterates; "
-                                         "small ensembles sit at their sampling noise until the exactness "
-                                         "theorem makes it 0 at iteration K + 1"}
+                                         "the exactness theorem makes it 0 at iteration K + 1"}
         bs.close()
 
     unfused = None if args.no_unfused else _unfused_leg(L, solver, w, stream, _peaks().get("hbm_gbs"))
