@@ -16,10 +16,14 @@
  *    launch returns PR_ERR_CUDA.  Conditions found on the device (a NaN in the
  *    FP64 update, an empty macroscopic state) are written to a caller-provided
  *    int32 status word (device) and read by the caller after synchronising.
+ *  - Every device array must be aligned to its element size (4 bytes for
+ *    float, uint32 and int32, 8 for double and int64); a misaligned pointer
+ *    returns PR_ERR_INVALID_ARG.  Workspaces state their own alignment.
  *  - Ensembles are stored as structure of arrays, slice-major:
  *      x[n_slices][n]            slow variable X^p
  *      y[n_slices][fast_dim][n]  fast variable Y^p (component-major)
- *    in float (PR_F32) or double (PR_F64).  Weights are uniform, W^p = 1/n.
+ *    in float (PR_F32) or double (PR_F64).  Weights are uniform, W^p = 1/n,
+ *    except where a call takes them (Section 5.2 calls, pr_moments).
  *  - A macroscopic state (a histogram of the slow variable on a uniform grid
  *    x_lo = e_0 < ... < e_I = x_hi, Section 2.2.2) is passed as its
  *    piecewise-linear CDF sampled at the I+1 edges (Eq. discr_cdf), double,

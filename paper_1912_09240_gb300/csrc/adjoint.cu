@@ -488,6 +488,9 @@ static pr_status adjoint_check(const pr_model* model, const pr_rng* rng, const f
     if (n < 1 || n > 0xFFFFFFFFll || n_slices < 1 || slice_begin < 0 || steps < 0 || ckpt_every < 1) return PR_ERR_INVALID_ARG;
     if (!(dt > 0.0) || !isfinite(dt) || rng->problem_id >= (1u << 24)) return PR_ERR_INVALID_ARG;
     if (ybar_T && !xbar_T) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(x0, 4) || !elem_aligned(y0, 4) || !elem_aligned(xbar_T, 8) || !elem_aligned(ybar_T, 8) ||
+        !elem_aligned(grad, 8))
+        return PR_ERR_INVALID_ARG;
     return PR_OK;
 }
 
@@ -576,6 +579,8 @@ extern "C" pr_status pr_fine_adjoint(const pr_model* model, const pr_rng* rng, c
     const pr_status chk = adjoint_check(model, rng, x0, y0, n, slice_begin, n_slices, steps, dt, ckpt_every,
                                         xbar_T, ybar_T, grad);
     if (chk != PR_OK) return chk;
+    if (!elem_aligned(x_T, 4) || !elem_aligned(y_T, 4) || !elem_aligned(xbar_0, 8) || !elem_aligned(ybar_0, 8))
+        return PR_ERR_INVALID_ARG;
     if (!workspace) return PR_ERR_INVALID_ARG;
     const size_t need = pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every);
     if (workspace_bytes < need || ((uintptr_t)workspace & 255)) return PR_ERR_INVALID_ARG;
@@ -593,6 +598,8 @@ extern "C" pr_status pr_fine_adjoint_affine(const pr_model* model, const pr_rng*
     const pr_status chk = adjoint_check(model, rng, x0, y0, n, slice_begin, n_slices, steps, dt, ckpt_every,
                                         nullptr, nullptr, grad);
     if (chk != PR_OK) return chk;
+    if (!elem_aligned(x_T, 4) || !elem_aligned(y_T, 4) || !elem_aligned(xbar_0, 8) || !elem_aligned(ybar_0, 8))
+        return PR_ERR_INVALID_ARG;
     if (!isfinite(seed_scale) || !isfinite(seed_shift) || !workspace) return PR_ERR_INVALID_ARG;
     const size_t need = pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every);
     if (workspace_bytes < need || ((uintptr_t)workspace & 255)) return PR_ERR_INVALID_ARG;
@@ -610,6 +617,7 @@ extern "C" pr_status pr_order_statistics(const float* x, int64_t n, const int64_
                                          int64_t* index_out, void* workspace, size_t workspace_bytes, void* stream)
 {
     if (!x || !ranks || !index_out || !workspace || n < 1 || n > 0xFFFFFFFFll || n_ranks < 1) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(x, 4) || !elem_aligned(ranks, 8) || !elem_aligned(index_out, 8)) return PR_ERR_INVALID_ARG;
     if (workspace_bytes < pr_order_statistics_workspace(n) || ((uintptr_t)workspace & 7)) return PR_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t padded = next_pow2(n);
@@ -672,6 +680,8 @@ extern "C" pr_status pr_fine_adjoint_noalloc(const pr_model* model, const pr_rng
     const pr_status chk = adjoint_check(model, rng, x0, y0, n, slice_begin, n_slices, steps, dt, ckpt_every,
                                         xbar_T, ybar_T, grad);
     if (chk != PR_OK) return chk;
+    if (!elem_aligned(x_T, 4) || !elem_aligned(y_T, 4) || !elem_aligned(xbar_0, 8) || !elem_aligned(ybar_0, 8))
+        return PR_ERR_INVALID_ARG;
     // the problem must fit the fixed array (checked before anything else runs)
     if (pr_fine_adjoint_workspace(n, n_slices, steps, ckpt_every) > kNoAllocScratchBytes) return PR_ERR_NOMEM;
     void* scratch = nullptr;

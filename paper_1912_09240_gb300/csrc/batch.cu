@@ -603,7 +603,7 @@ extern "C" int64_t pr_batch_particle_steps(void* plan)
 
 extern "C" pr_status pr_batch_set_initial(void* plan, const float* x0, const float* y0, void* stream)
 {
-    if (!plan || !x0 || !y0) return PR_ERR_INVALID_ARG;
+    if (!plan || !x0 || !y0 || !elem_aligned(x0, 4) || !elem_aligned(y0, 4)) return PR_ERR_INVALID_ARG;
     auto* pl = static_cast<BatchPlan*>(plan);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     pl->xa = pl->xa0;
@@ -659,7 +659,7 @@ extern "C" pr_status pr_batch_iterate(void* plan, void* stream)
 
 extern "C" pr_status pr_batch_rho(void* plan, int32_t problem, double* out, void* stream)
 {
-    if (!plan || !out) return PR_ERR_INVALID_ARG;
+    if (!plan || !out || !elem_aligned(out, 8)) return PR_ERR_INVALID_ARG;
     auto* pl = static_cast<BatchPlan*>(plan);
     if (problem < 0 || problem >= pl->np) return PR_ERR_INVALID_ARG;
     const BatchProblemDev& d = pl->hp[problem];
@@ -670,7 +670,7 @@ extern "C" pr_status pr_batch_rho(void* plan, int32_t problem, double* out, void
 
 extern "C" pr_status pr_batch_fine_state(void* plan, int32_t problem, float* x_out, float* y_out, void* stream)
 {
-    if (!plan || !x_out || !y_out) return PR_ERR_INVALID_ARG;
+    if (!plan || !x_out || !y_out || !elem_aligned(x_out, 4) || !elem_aligned(y_out, 4)) return PR_ERR_INVALID_ARG;
     auto* pl = static_cast<BatchPlan*>(plan);
     if (problem < 0 || problem >= pl->np) return PR_ERR_INVALID_ARG;
     const BatchProblemDev& d = pl->hp[problem];

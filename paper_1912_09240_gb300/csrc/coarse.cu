@@ -326,7 +326,7 @@ extern "C" pr_status pr_coarse_destroy(void* handle)
 
 extern "C" pr_status pr_coarse_matrix(void* handle, double* out, void* stream)
 {
-    if (!handle || !out) return PR_ERR_INVALID_ARG;
+    if (!handle || !out || !elem_aligned(out, 8)) return PR_ERR_INVALID_ARG;
     auto* h = static_cast<CoarseHandle*>(handle);
     const size_t bytes = (size_t)h->g.bins * h->g.bins * sizeof(double);
     PR_TRY_CUDA(cudaMemcpyAsync(out, h->P, bytes, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
@@ -336,6 +336,7 @@ extern "C" pr_status pr_coarse_matrix(void* handle, double* out, void* stream)
 extern "C" pr_status pr_coarse_fp(void* handle, const double* cdf_in, double* cdf_out, int32_t n_vec, void* stream)
 {
     if (!handle || !cdf_in || !cdf_out || n_vec < 1 || cdf_in == cdf_out) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(cdf_in, 8) || !elem_aligned(cdf_out, 8)) return PR_ERR_INVALID_ARG;
     auto* h = static_cast<CoarseHandle*>(handle);
     const int I = h->g.bins;
     const size_t smem = coarse_apply_smem(I);
@@ -387,6 +388,9 @@ extern "C" pr_status pr_parareal_update(void* coarse, pr_iterator iterator, pr_q
                                         double* cdf_next, int32_t* status, void* stream)
 {
     if (!coarse || !cdf0 || !cdf_next || n_slices < 1) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(cdf0, 8) || !elem_aligned(cdf_f_star, 8) || !elem_aligned(cdf_c_star, 8) ||
+        !elem_aligned(cdf_next, 8) || !elem_aligned(status, 4))
+        return PR_ERR_INVALID_ARG;
     if (iterator < PR_ITER_QUANTILE || iterator > PR_ITER_NONE) return PR_ERR_INVALID_ARG;
     if (qmode != PR_QMODE_TWO_SIDED && qmode != PR_QMODE_MIDPOINT) return PR_ERR_INVALID_ARG;
     if (iterator != PR_ITER_NONE && (!cdf_f_star || !cdf_c_star)) return PR_ERR_INVALID_ARG;
@@ -441,6 +445,9 @@ extern "C" pr_status pr_iterate(pr_iterator iterator, pr_quantile_mode qmode, co
                                 void* stream)
 {
     if (!grid_ok(grid) || n_vec < 1 || !a || !b || !c || !out) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(a, 8) || !elem_aligned(b, 8) || !elem_aligned(c, 8) || !elem_aligned(out, 8) ||
+        !elem_aligned(status, 4))
+        return PR_ERR_INVALID_ARG;
     if (iterator < PR_ITER_QUANTILE || iterator > PR_ITER_ROT) return PR_ERR_INVALID_ARG;
     if (qmode != PR_QMODE_TWO_SIDED && qmode != PR_QMODE_MIDPOINT) return PR_ERR_INVALID_ARG;
     if (grid->bins > kUpdateMaxBins) return PR_ERR_UNSUPPORTED;
@@ -458,6 +465,7 @@ extern "C" pr_status pr_w1(const pr_grid* grid, int32_t n_vec, const double* c1,
                            void* stream)
 {
     if (!grid_ok(grid) || n_vec < 1 || !c1 || !c2 || !w1) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(c1, 8) || !elem_aligned(c2, 8) || !elem_aligned(w1, 8)) return PR_ERR_INVALID_ARG;
     const GridDev g = make_grid(*grid);
     w1_kernel<<<n_vec, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, c1, c2, w1);
     PR_CHECK_LAUNCH();

@@ -808,6 +808,9 @@ extern "C" pr_status pr_reweight(pr_precision precision, const void* x_prior, in
                                  const double* cdf_prior, const double* cdf_target, double* w_out, void* stream)
 {
     if (precision != PR_F32 && precision != PR_F64) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(x_prior, elem_bytes(precision)) || !elem_aligned(w_prior, 8) || !elem_aligned(cdf_prior, 8) ||
+        !elem_aligned(cdf_target, 8) || !elem_aligned(w_out, 8))
+        return PR_ERR_INVALID_ARG;
     if (!x_prior || !cdf_prior || !cdf_target || !w_out || !grid_ok(grid)) return PR_ERR_INVALID_ARG;
     if (n < 1 || n_slices < 1 || n_slices > 65535) return PR_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -844,6 +847,10 @@ extern "C" pr_status pr_resample(pr_precision precision, int32_t fast_dim, const
                                  void* x_out, void* y_out, void* workspace, size_t workspace_bytes, void* stream)
 {
     if (precision != PR_F32 && precision != PR_F64) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(x_in, elem_bytes(precision)) || !elem_aligned(y_in, elem_bytes(precision)) ||
+        !elem_aligned(w, 8) || !elem_aligned(index_out, 4) || !elem_aligned(x_out, elem_bytes(precision)) ||
+        !elem_aligned(y_out, elem_bytes(precision)))
+        return PR_ERR_INVALID_ARG;
     if (mode != PR_RESAMPLE_STRATIFIED && mode != PR_RESAMPLE_DETERMINISTIC) return PR_ERR_INVALID_ARG;
     if (!w || !rng || !workspace || n < 1 || n > 0xFFFFFFFFll || n_slices < 1 || n_slices > 65535) return PR_ERR_INVALID_ARG;
     if (slice_begin < 0 || rng->problem_id >= (1u << 24)) return PR_ERR_INVALID_ARG;
@@ -898,6 +905,8 @@ extern "C" pr_status pr_restrict_weighted(pr_precision precision, const void* x,
                                           double* cdf, void* workspace, size_t workspace_bytes, void* stream)
 {
     if (precision != PR_F32 && precision != PR_F64) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(x, elem_bytes(precision)) || !elem_aligned(w, 8) || !elem_aligned(cdf, 8))
+        return PR_ERR_INVALID_ARG;
     if (!x || !w || !cdf || !workspace || !grid_ok(grid) || n < 1 || n_slices < 1 || n_slices > 65535)
         return PR_ERR_INVALID_ARG;
     if (workspace_bytes < pr_restrict_weighted_workspace(n_slices, grid->bins) || ((uintptr_t)workspace & 7))

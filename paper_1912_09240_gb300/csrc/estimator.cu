@@ -150,7 +150,9 @@ extern "C" pr_status pr_moments(pr_precision precision, const void* v, int64_t s
     if (!v || !out || !workspace || n < 1 || n_slices < 1 || n_slices > 65535) return PR_ERR_INVALID_ARG;
     if (max_order < 1 || max_order > kMomMaxOrder || slice_stride < 0 || (n_slices > 1 && slice_stride < n))
         return PR_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(workspace) & 7) != 0) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(workspace, 8) || !elem_aligned(v, elem_bytes(precision)) || !elem_aligned(w, 8) ||
+        !elem_aligned(out, 8))
+        return PR_ERR_INVALID_ARG;
     if (workspace_bytes < pr_moments_workspace(n, n_slices, max_order)) return PR_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t nblk = moments_blocks(n, n_slices);

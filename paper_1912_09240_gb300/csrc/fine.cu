@@ -670,6 +670,14 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
                                        uint32_t* counts_end, double* cdf_end, void* stream)
 {
     if (!model_ok(model) || !rng) return PR_ERR_INVALID_ARG;
+    {
+        const size_t es = elem_bytes(precision);
+        if (!elem_aligned(x_in, es) || !elem_aligned(y_in, es) || !elem_aligned(x_out, es) ||
+            !elem_aligned(y_out, es) || !elem_aligned(cdf_prior, 8) || !elem_aligned(cdf_target, 8) ||
+            !elem_aligned(counts_start, 4) || !elem_aligned(cdf_start, 8) || !elem_aligned(counts_end, 4) ||
+            !elem_aligned(cdf_end, 8))
+            return PR_ERR_INVALID_ARG;
+    }
     if (precision != PR_F32 && precision != PR_F64) return PR_ERR_INVALID_ARG;
     if (!x_in || !y_in || !x_out || !y_out) return PR_ERR_INVALID_ARG;
     if (n < 1 || n > 0xFFFFFFFFll || n_slices < 1 || n_slices > 65535 || slice_begin < 0) return PR_ERR_INVALID_ARG;
@@ -806,6 +814,7 @@ extern "C" pr_status pr_counts_to_cdf(const uint32_t* counts, int64_t n, int32_t
                                       double* cdf, void* stream)
 {
     if (!counts || !cdf || n < 1 || n_slices < 1 || bins < 1 || bins > PR_MAX_BINS) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(counts, 4) || !elem_aligned(cdf, 8)) return PR_ERR_INVALID_ARG;
     counts_to_cdf_kernel<<<n_slices, 256, 0, static_cast<cudaStream_t>(stream)>>>(counts, n, bins, cdf);
     PR_CHECK_LAUNCH();
     return PR_OK;
@@ -815,6 +824,8 @@ extern "C" pr_status pr_restrict(pr_precision precision, const void* x, int64_t 
                                  const pr_grid* grid, uint32_t* counts, double* cdf, void* stream)
 {
     if (precision != PR_F32 && precision != PR_F64) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(x, elem_bytes(precision)) || !elem_aligned(counts, 4) || !elem_aligned(cdf, 8))
+        return PR_ERR_INVALID_ARG;
     if (!x || !counts || n < 1 || n_slices < 1 || n_slices > 65535 || !grid_ok(grid)) return PR_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int bins = grid->bins;
@@ -844,6 +855,9 @@ extern "C" pr_status pr_match(pr_precision precision, const void* x_prior, void*
                               const double* cdf_target, void* stream)
 {
     if (precision != PR_F32 && precision != PR_F64) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(x_prior, elem_bytes(precision)) || !elem_aligned(x_out, elem_bytes(precision)) ||
+        !elem_aligned(cdf_prior, 8) || !elem_aligned(cdf_target, 8))
+        return PR_ERR_INVALID_ARG;
     if (!x_prior || !x_out || !cdf_prior || !cdf_target) return PR_ERR_INVALID_ARG;
     if (n < 1 || n_slices < 1 || n_slices > 65535 || !grid_ok(grid)) return PR_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -35,6 +35,15 @@ inline bool grid_ok(const pr_grid* g)
            g->x_hi - g->x_lo < 1e300;
 }
 
+// A device pointer aligned to its element size (NULL counts as aligned: the
+// optional arguments); entry points reject misaligned data on the host.
+inline bool elem_aligned(const void* p, size_t bytes)
+{
+    return (reinterpret_cast<uintptr_t>(p) & (bytes - 1)) == 0;
+}
+
+inline size_t elem_bytes(pr_precision p) { return p == PR_F64 ? 8 : 4; }
+
 int num_sms();   // of the current device, cached per device
 int smem_optin_max();   // shared memory one CTA may opt in to, current device, cached per device
 

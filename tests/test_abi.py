@@ -161,3 +161,31 @@ def test_moments_rejects_bad_arguments(L):
     assert call(ws=ctypes.c_void_p(0x10004)) == L.PR_ERR_INVALID_ARG
     assert call(v=None) == L.PR_ERR_INVALID_ARG
     assert call(n=0) == L.PR_ERR_INVALID_ARG
+
+
+def test_misaligned_element_pointers_rejected(L):
+    """Device pointers not aligned to their element size are refused on the
+    host before any launch."""
+    lib = L.lib()
+    ok4, ok8 = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x10008)
+    bad4, bad8 = ctypes.c_void_p(0x10002), ctypes.c_void_p(0x10004)
+    g = L.Grid(64, -3.0, 3.0).c()
+    assert lib.pr_restrict(0, bad4, 10, 1, ctypes.byref(g), ok4, None, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_restrict(1, bad8, 10, 1, ctypes.byref(g), ok4, None, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_restrict(0, ok4, 10, 1, ctypes.byref(g), ok4, bad8, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_match(0, ok4, bad4, 10, 1, ctypes.byref(g), ok8, ok8, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_match(0, ok4, ok4, 10, 1, ctypes.byref(g), bad8, ok8, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_counts_to_cdf(bad4, 10, 1, 64, ok8, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_w1(ctypes.byref(g), 1, ok8, bad8, ok8, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_iterate(0, 0, ctypes.byref(g), 1, ok8, ok8, ok8, bad8, None, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_reweight(0, ok4, 0, None, 10, 1, ctypes.byref(g), ok8, ok8, bad8, None) == L.PR_ERR_INVALID_ARG
+    need = lib.pr_restrict_weighted_workspace(1, 64)
+    assert lib.pr_restrict_weighted(0, ok4, 0, bad8, 10, 1, ctypes.byref(g), ok8, ok8, need,
+                                    None) == L.PR_ERR_INVALID_ARG
+    mw = lib.pr_moments_workspace(10, 1, 2)
+    assert lib.pr_moments(1, bad8, 10, None, 10, 1, 2, ok8, ok8, mw, None) == L.PR_ERR_INVALID_ARG
+    r = L.Rng(1, 0).c()
+    m = L.Model(0, 1, 1.0, 1.0, 0.1).c()
+    assert lib.pr_fine_propagate(ctypes.byref(m), 0, ctypes.byref(r), bad4, ok4, 0, ok4, ok4, 10, 0, 1, 10,
+                                 1e-3, None, None, None, None, None, None, None, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_order_statistics(ok4, 10, bad8, 1, ok8, ok8, 1 << 20, None) == L.PR_ERR_INVALID_ARG
