@@ -121,8 +121,13 @@ const char* pr_version(void);
  * normals (Box-Muller) from Philox4x32-10 with key = seed and counter
  *   fast_dim == 1 : (m >> 1, p, n, problem_id << 8), step m taking words
  *                   2(m&1), 2(m&1)+1 (one block serves two steps);
- *   fast_dim  > 1 : (m, p, n, (problem_id << 8) | g), g = 0, 1, ..., words
- *                   taken in pairs;
+ *   fast_dim  > 1 : with Q = 1 + fast_dim, F = Q / 4, t = Q mod 4: normals
+ *                   4g .. 4g+3 of step m (g < F) from (m, p, n,
+ *                   (problem_id << 8) | g), words in pairs, each pair giving
+ *                   a cosine and a sine normal; the last t normals of the
+ *                   steps 4k .. 4k+3 share t blocks (k, p, n,
+ *                   (problem_id << 8) | (F + j)), normal i of step 4k + s
+ *                   being number s t + i of their 4t normals in order;
  * so a slice reuses the same numbers in every parareal iteration (Section 6).
  *
  *   x_in, y_in   (device) start states, [n_slices][n] and [n_slices][d][n];

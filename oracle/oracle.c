@@ -124,8 +124,15 @@ static void or_box_muller(uint32_t w0, uint32_t w1, double* z0, double* z1)
  * numbers are reused across iterations):
  *   Q <= 2 : one block serves two steps, ctr = (m >> 1, p, n, problem << 8);
  *            step m takes words 2*(m & 1) and 2*(m & 1) + 1.
- *   Q  > 2 : ctr = (m, p, n, (problem << 8) | g), g = 0, 1, ..., words taken
- *            in pairs in order; the last pair's spare normal is dropped.
+ *   Q  > 2 : with F = Q / 4 and t = Q mod 4, normals 4g .. 4g + 3 of step m
+ *            (g < F) come from ctr = (m, p, n, (problem << 8) | g), words
+ *            taken in pairs in order, each pair giving its cosine and sine
+ *            normals.  The last t normals of the four steps 4k .. 4k + 3
+ *            share t blocks, ctr = (k, p, n, (problem << 8) | (F + j)),
+ *            j < t: normal i < t of step 4k + s is number s t + i of the 4t
+ *            normals those blocks give in order.  No word is dropped (in a
+ *            slice whose step count is not a multiple of four, the last
+ *            group's spare normals are).
  * z[0] drives the slow variable, z[1 + j] the fast component j. */
 void or_step_normals(uint64_t seed, uint32_t problem, uint32_t p, uint32_t n,
                      uint32_t m, int Q, double* z)
@@ -142,16 +149,21 @@ void or_step_normals(uint64_t seed, uint32_t problem, uint32_t p, uint32_t n,
         if (Q == 2) z[1] = b;
         return;
     }
-    int got = 0;
-    for (uint32_t g = 0; got < Q; ++g) {
-        ctr[0] = m; ctr[1] = p; ctr[2] = n; ctr[3] = (problem << 8) | g;
+    const int F = Q / 4, t = Q % 4;
+    for (int g = 0; g < F; ++g) {
+        ctr[0] = m; ctr[1] = p; ctr[2] = n; ctr[3] = (problem << 8) | (uint32_t)g;
         or_philox4x32_10(ctr, key, w);
-        for (int pair = 0; pair < 2 && got < Q; ++pair) {
-            double a, b;
-            or_box_muller(w[2 * pair], w[2 * pair + 1], &a, &b);
-            z[got++] = a;
-            if (got < Q) z[got++] = b;
-        }
+        or_box_muller(w[0], w[1], &z[4 * g], &z[4 * g + 1]);
+        or_box_muller(w[2], w[3], &z[4 * g + 2], &z[4 * g + 3]);
+    }
+    for (int i = 0; i < t; ++i) {
+        const int idx = (int)(m & 3u) * t + i;   /* within the group's 4t normals */
+        ctr[0] = m >> 2; ctr[1] = p; ctr[2] = n; ctr[3] = (problem << 8) | (uint32_t)(F + idx / 4);
+        or_philox4x32_10(ctr, key, w);
+        const int pair = (idx % 4) / 2;
+        double a, b;
+        or_box_muller(w[2 * pair], w[2 * pair + 1], &a, &b);
+        z[4 * F + i] = (idx % 2) ? b : a;
     }
 }
 

@@ -240,34 +240,84 @@ fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
     const float lam = a.lam_f, ddt = a.drift_dt_f, rel = a.relax_f;
     const float sxk = a.sxk_f, syk = a.syk_f, omr = 1.0f - rel;
     const float invD = 1.0f / (float)D;
+    // Normals of a step: 4 per full block (F of them), and the last T = Q mod 4
+    // from tail blocks shared by the four steps 4k .. 4k + 3 (normal i of
+    // step 4k + s is number s T + i of the group's 4T), so no word is wasted.
+    // With Q = 2 (D = 1) one block serves two steps, as in the d = 1 kernel.
     constexpr int Q = 1 + D;
-    constexpr int PAIRS = (Q + 1) / 2;
-    constexpr int G = (PAIRS + 1) / 2;
+    constexpr int F = Q > 2 ? Q / 4 : 0;
+    constexpr int T = Q > 2 ? Q % 4 : 0;
+    constexpr int FP = F > 0 ? 2 * F : 1;   // Box-Muller pairs of the full blocks
+    constexpr int TP = T > 0 ? 2 * T : 1;   // pairs of a group's tail blocks
     const uint32_t k0 = a.k0, k1 = a.k1, chi = a.ctr_hi, pid = (uint32_t)p;
+    // normal 2i of a pair is sqrt(2 ln 2) q_i cos(theta_i), normal 2i + 1 the
+    // sine; sqrt(2 ln 2) is folded into the amplitudes sxk, syk
+    float tq[TP], tc[TP], ts[TP], tamp[TP];
     for (int m = 0; m < a.steps; ++m) {
-        // normal 2i is sqrt(2 ln 2) q_i cos(theta_i), normal 2i + 1 the sine;
-        // sqrt(2 ln 2) is folded into the amplitudes sxk, syk
-        float q[PAIRS], c[PAIRS], sn[PAIRS];
+        if (T > 0 && (m & 3) == 0) {
 #pragma unroll
-        for (int gi = 0; gi < G; ++gi) {
+            for (int j = 0; j < T; ++j) {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)(m >> 2), pid, slice, chi | (uint32_t)(F + j)),
+                                              k0, k1);
+                box_muller_qcs(w.x, w.y, tq[2 * j], tc[2 * j], ts[2 * j]);
+                box_muller_qcs(w.z, w.w, tq[2 * j + 1], tc[2 * j + 1], ts[2 * j + 1]);
+            }
+#pragma unroll
+            for (int i = 0; i < TP; ++i) tamp[i] = syk * tq[i];
+        }
+        float pq = 0.0f, pc = 0.0f, ps = 0.0f;   // Q = 2: this step's pair
+        if (Q <= 2) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)(m >> 1), pid, slice, chi), k0, k1);
+            if (m & 1) box_muller_qcs(w.z, w.w, pq, pc, ps);
+            else box_muller_qcs(w.x, w.y, pq, pc, ps);
+        }
+        float q[FP], c[FP], sn[FP], amp[FP];
+#pragma unroll
+        for (int gi = 0; gi < F; ++gi) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)m, pid, slice, chi | (uint32_t)gi), k0, k1);
             box_muller_qcs(w.x, w.y, q[2 * gi], c[2 * gi], sn[2 * gi]);
-            if (2 * gi + 1 < PAIRS) box_muller_qcs(w.z, w.w, q[2 * gi + 1], c[2 * gi + 1], sn[2 * gi + 1]);
+            box_muller_qcs(w.z, w.w, q[2 * gi + 1], c[2 * gi + 1], sn[2 * gi + 1]);
         }
+#pragma unroll
+        for (int i = 0; i < 2 * F; ++i) amp[i] = syk * q[i];
+        const int s4 = m & 3;
+        // normal k of this step as (q, trig) of its pair, q scaled by syk for
+        // the fast components (scaled = true)
+        auto normal = [&](int k, bool scaled, float& qq, float& tt) {
+            if (Q <= 2) {
+                qq = scaled ? syk * pq : pq;
+                tt = k ? ps : pc;
+            } else if (k < 4 * F) {
+                qq = scaled ? amp[k >> 1] : q[k >> 1];
+                tt = (k & 1) ? sn[k >> 1] : c[k >> 1];
+            } else {
+                const int idx = s4 * T + (k - 4 * F);
+                const int pr = idx >> 1;
+                const bool odd = idx & 1;
+                qq = scaled ? tamp[0] : tq[0];
+                tt = odd ? ts[0] : tc[0];
+#pragma unroll
+                for (int cc = 1; cc < TP; ++cc)
+                    if (pr == cc) {
+                        qq = scaled ? tamp[cc] : tq[cc];
+                        tt = odd ? ts[cc] : tc[cc];
+                    }
+            }
+        };
         float ysum = 0.0f;
 #pragma unroll
         for (int j = 0; j < D; ++j) ysum += y[j];
         const float f = slow_force<KIND>(x, ysum * invD, lam);
-        const float xn = fmaf(sxk * q[0], c[0], fmaf(-f, ddt, x));
+        float q0, t0;
+        normal(0, false, q0, t0);
+        const float xn = fmaf(sxk * q0, t0, fmaf(-f, ddt, x));
         // y_j <- y_j + (x - y_j) rel + sy dV_j, as y_j (1 - rel) + x rel + sy dV_j
         const float xr = x * rel;
-        float amp[PAIRS];
-#pragma unroll
-        for (int i = 0; i < PAIRS; ++i) amp[i] = syk * q[i];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const int k = 1 + j;   // the normal of component j
-            y[j] = fmaf(amp[k >> 1], (k & 1) ? sn[k >> 1] : c[k >> 1], fmaf(y[j], omr, xr));
+            float aj, tj;
+            normal(1 + j, true, aj, tj);   // the normal of component j
+            y[j] = fmaf(aj, tj, fmaf(y[j], omr, xr));
         }
         x = xn;
     }
@@ -339,15 +389,22 @@ fine_f64_kernel(FineArgs a, FineSmemOffsets so, int flags)
             if (m & 1) box_muller_f64(w.z, w.w, z[0], z[1]);
             else box_muller_f64(w.x, w.y, z[0], z[1]);
         } else {
-            int got = 0;
-            for (uint32_t gi = 0; got < Q; ++gi) {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)m, pid, slice, chi | gi), k0, k1);
-                box_muller_f64(w.x, w.y, z[got], z[got + 1]);
-                got += 2;
-                if (got < Q) {
-                    box_muller_f64(w.z, w.w, z[got], z[got + 1]);
-                    got += 2;
-                }
+            // F full blocks per step, then the step's T = Q mod 4 normals from
+            // the tail blocks shared by its group of four steps
+            const int F = Q / 4, T = Q % 4;
+            for (int gi = 0; gi < F; ++gi) {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)m, pid, slice, chi | (uint32_t)gi), k0, k1);
+                box_muller_f64(w.x, w.y, z[4 * gi], z[4 * gi + 1]);
+                box_muller_f64(w.z, w.w, z[4 * gi + 2], z[4 * gi + 3]);
+            }
+            for (int i = 0; i < T; ++i) {
+                const int idx = (m & 3) * T + i;
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)(m >> 2), pid, slice, chi | (uint32_t)(F + idx / 4)),
+                                              k0, k1);
+                double za, zb;
+                if ((idx & 2) != 0) box_muller_f64(w.z, w.w, za, zb);
+                else box_muller_f64(w.x, w.y, za, zb);
+                z[4 * F + i] = (idx & 1) ? zb : za;
             }
         }
         double ysum = 0.0;

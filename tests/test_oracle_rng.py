@@ -109,3 +109,23 @@ def test_counters_separate_streams(orc):
     for args in [(1, 0, 5, 2, 10), (0, 1, 5, 2, 10), (0, 0, 6, 2, 10), (0, 0, 5, 3, 10),
                  (0, 0, 5, 2, 11), (0, 0, 5, 2, 12)]:
         assert not np.array_equal(base, orc.step_normals(*args, 2))
+
+
+@pytest.mark.parametrize("Q", [3, 6, 7, 17])
+def test_normals_share_no_word(orc, Q):
+    """Q > 2: the last Q mod 4 normals of four consecutive steps share Philox
+    blocks.  Every normal of 8 steps (two groups) of one particle is distinct
+    (a word taken twice would repeat a normal), the components are
+    uncorrelated with each other and with the next step's, and the whole set
+    is standard normal."""
+    from scipy import stats
+    z = orc.normals_block(seed=11, problem=2, p0=7, n_part=3000, n=4, m0=0, n_steps=8, Q=Q)
+    for i in range(5):
+        v = z[i].reshape(-1)
+        assert len(np.unique(v)) == v.size
+    assert stats.kstest(z.reshape(-1), "norm").pvalue > 1e-3
+    a = z[:, :-1, :].reshape(-1, Q)
+    b = z[:, 1:, :].reshape(-1, Q)
+    c = np.corrcoef(np.concatenate([a, b], axis=1).T)
+    off = c[~np.eye(2 * Q, dtype=bool)]
+    assert np.max(np.abs(off)) < 5.0 / np.sqrt(a.shape[0])
