@@ -139,3 +139,16 @@ def test_solver_moments(L, orc, matching):
     with pytest.raises(ValueError):
         s.moments(2, component=3)
     s.close()
+
+
+def test_moments_many_slices(L, orc):
+    """More slices than the grid's block budget (one block per slice then)."""
+    rng = np.random.default_rng(21)
+    S, n = 3000, 37
+    v64 = rng.normal(0.0, 1.0, (S, n))
+    w = rng.random((S, n))
+    w /= w.sum(axis=1, keepdims=True)
+    v = torch.tensor(v64, dtype=torch.float32, device=DEV)
+    v64 = v.double().cpu().numpy()
+    got = _gpu_moments(L, L.PR_F32, v, n, torch.tensor(w, device=DEV), n, S, 3)
+    _check(got, orc.moments(v64, 3, w), v64, w, 3)
