@@ -253,18 +253,20 @@ fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
     // normal 2i of a pair is sqrt(2 ln 2) q_i cos(theta_i), normal 2i + 1 the
     // sine; sqrt(2 ln 2) is folded into the amplitudes sxk, syk
     float tq[TP], tc[TP], ts[TP], tamp[TP];
-    for (int m = 0; m < a.steps; ++m) {
-        if (T > 0 && (m & 3) == 0) {
+    // the tail blocks of the group of four steps from step m on
+    auto tail_blocks = [&](int m) {
 #pragma unroll
-            for (int j = 0; j < T; ++j) {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)(m >> 2), pid, slice, chi | (uint32_t)(F + j)),
-                                              k0, k1);
-                box_muller_qcs(w.x, w.y, tq[2 * j], tc[2 * j], ts[2 * j]);
-                box_muller_qcs(w.z, w.w, tq[2 * j + 1], tc[2 * j + 1], ts[2 * j + 1]);
-            }
-#pragma unroll
-            for (int i = 0; i < TP; ++i) tamp[i] = syk * tq[i];
+        for (int j = 0; j < T; ++j) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)(m >> 2), pid, slice, chi | (uint32_t)(F + j)),
+                                          k0, k1);
+            box_muller_qcs(w.x, w.y, tq[2 * j], tc[2 * j], ts[2 * j]);
+            box_muller_qcs(w.z, w.w, tq[2 * j + 1], tc[2 * j + 1], ts[2 * j + 1]);
         }
+#pragma unroll
+        for (int i = 0; i < TP; ++i) tamp[i] = syk * tq[i];
+    };
+    // step m, the s4-th of its group (a constant where the loop below is unrolled)
+    auto step = [&](int m, int s4) {
         float pq = 0.0f, pc = 0.0f, ps = 0.0f;   // Q = 2: this step's pair
         if (Q <= 2) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)(m >> 1), pid, slice, chi), k0, k1);
@@ -280,7 +282,6 @@ fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
         }
 #pragma unroll
         for (int i = 0; i < 2 * F; ++i) amp[i] = syk * q[i];
-        const int s4 = m & 3;
         // normal k of this step as (q, trig) of its pair, q scaled by syk for
         // the fast components (scaled = true)
         auto normal = [&](int k, bool scaled, float& qq, float& tt) {
@@ -320,7 +321,17 @@ fine_f32_dn_kernel(FineArgs a, FineSmemOffsets so, int flags)
             y[j] = fmaf(aj, tj, fmaf(y[j], omr, xr));
         }
         x = xn;
+    };
+    int m0 = 0;
+    if (T > 0) {
+        for (; m0 + 4 <= a.steps; m0 += 4) {
+            tail_blocks(m0);
+#pragma unroll
+            for (int s4 = 0; s4 < 4; ++s4) step(m0 + s4, s4);
+        }
+        if (m0 < a.steps) tail_blocks(m0);
     }
+    for (int m = m0; m < a.steps; ++m) step(m, m & 3);
     if (ok) {
         xout[p] = x;
 #pragma unroll
