@@ -192,7 +192,8 @@ fine_f32_d1_kernel(FineArgs a, FineSmemOffsets so, int flags)
 
 // ---------------------------------------------------------------------------
 // binary32 kernel, fast_dim = D > 1 (coupling through mean(y)), one particle
-// per thread.  Normals: ceil((1+D)/4) Philox blocks per step.
+// per thread.  Normals: (1+D)/4 whole Philox blocks per step, the last
+// (1+D) mod 4 from blocks shared by four consecutive steps.
 // ---------------------------------------------------------------------------
 
 template <int KIND, int D>
