@@ -118,11 +118,11 @@ def _dist():
     return rank_env()
 
 
-def _cpu_sample(seconds_target: float = 12.0):
-    """Time the oracle on bounded samples of the workloads (host cores of this
-    machine): the double-well fine propagator at all cores and at one core,
-    one slice of the 16-dimensional fast space at 2^16 particles, and the
-    plain FP64 workload's whole parareal run."""
+def _cpu_sample(seconds_target: float = 12.0, detail: bool = False):
+    """Time the oracle on a bounded sample of the double-well workload on
+    this machine's host cores (all of them).  With `detail`, also at one
+    core, one slice of the 16-dimensional fast space at 2^16 particles, and
+    the plain FP64 workload's whole parareal run."""
     from oracle import oracle as orc
     orc.build()
     w = WORKLOAD
@@ -143,6 +143,10 @@ def _cpu_sample(seconds_target: float = 12.0):
         return n * w.steps / el, n, el
 
     value, n, el = rate_of(w.N, seconds_target)
+    out = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{n} particles x {w.steps} EM steps, {el:.1f} s"}
+    if not detail:
+        return out
     orc.set_num_threads(1)
     try:
         v1, n1, el1 = rate_of(w.N, seconds_target / 3)
@@ -163,15 +167,13 @@ def _cpu_sample(seconds_target: float = 12.0):
     orc.parareal(orc.Model(ow.kind, ow.fast_dim, ow.lam, ow.beta, ow.eps, ow.tau_x), orc.Grid(ow.bins, ow.lo, ow.hi),
                  ow.seed, ox, oy, ow.K, ow.steps, ow.step_dt, iters=ow.iters)
     el_o = time.perf_counter() - t0
-    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} particles x 1 slice x {w.steps} EM steps of the double-well workload "
-                      f"(FP64 C oracle, OpenMP), {el:.1f} s",
-            "single_core": {"value": v1, "unit": UNIT, "cores": 1,
-                            "sample": f"{n1} particles x 1 slice x {w.steps} steps, {el1:.1f} s"},
-            "fast16": {"value": nl * lw.steps / el_l, "unit": UNIT, "cores": cores,
-                       "sample": f"{nl} particles x 1 slice x {lw.steps} steps of the 16-dimensional "
-                                 f"fast-space workload, {el_l:.1f} s"},
-            "ou_fp64_full_parareal_s": el_o}
+    out.update({"single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                                "sample": f"{n1} particles x 1 slice x {w.steps} steps, {el1:.1f} s"},
+                "fast16": {"value": nl * lw.steps / el_l, "unit": UNIT, "cores": cores,
+                           "sample": f"{nl} particles x 1 slice x {lw.steps} steps of the 16-dimensional "
+                                     f"fast-space workload, {el_l:.1f} s"},
+                "ou_fp64_full_parareal_s": el_o})
+    return out
 
 
 def run_reference(args):
@@ -581,6 +583,272 @@ def _large_leg(L, dev, stream, rank, chunk, n=None, k=None, iters=1):
             "particle_steps_per_s": ps / (ms / 1e3), "status": status}
 
 
+def _fp64_leg(L, w, model, stream, fine_ms):
+    """The plain FP64 fine kernel on a sample of the workload (2 slices of all
+    particles), against the binary32 fine kernel's rate in the main launch."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x0, y0 = workloads.initial_ensemble(w)
+    xs = torch.tensor(np.stack([x0, x0]), dtype=torch.float64, device=dev)
+    ys = torch.tensor(np.stack([y0, y0]), dtype=torch.float64, device=dev)
+    L.pr_fine_propagate(model, L.PR_F64, L.Rng(w.seed), xs, ys, False, xs, ys, w.N, 1, 2, 50, w.step_dt)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    L.pr_fine_propagate(model, L.PR_F64, L.Rng(w.seed), xs, ys, False, xs, ys, w.N, 1, 2, w.steps, w.step_dt)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp64_rate = 2 * w.N * w.steps / (f0.elapsed_time(f1) / 1e3)
+    fine_rate = (w.K - 1) * w.N * w.steps / (fine_ms / 1e3) if fine_ms else None
+    return {"fp64_particle_steps_per_s": fp64_rate, "fp32_fine_particle_steps_per_s": fine_rate,
+            "fp32_over_fp64": (fine_rate / fp64_rate) if fine_rate else None,
+            "sample": f"FP64 fine kernel, {w.N} particles x 2 slices x {w.steps} steps"}
+
+
+def _fp64_iteration_leg(L, w, model, grid, stream, rank, chunk, ms):
+    """One whole parareal iteration of the workload on the plain FP64 path
+    (pipelined driver), after one warm-up iteration."""
+    import torch
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x0, y0 = workloads.initial_ensemble(w)
+    sv = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F64,
+                        rng=L.Rng(w.seed, rank), device=str(dev), chunk=chunk)
+    sv.set_initial(torch.tensor(x0, dtype=torch.float64, device=dev),
+                   torch.tensor(y0, dtype=torch.float64, device=dev))
+    sv.iterate()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    sv.iterate()
+    sv.join()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    out = {"fp64_iteration_ms": f0.elapsed_time(f1), "fp32_iteration_ms": ms,
+           "fp64_over_fp32_iteration_time": f0.elapsed_time(f1) / ms}
+    sv.close()
+    return out
+
+
+def _convergence_leg(L, solver, w, model, grid, stream, rank, chunk, ms, x0t, y0t, detail):
+    """Iterations until max_n W1(rho_k^n, R X_serial^n) <= 1e-3 against the
+    serial fine solution with the same random numbers, and the time to that
+    target.  With `detail`: the same skipping converged slices, graph-replayed
+    iterations, and binary32 against FP64 on a paired smaller run."""
+    import torch
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    dev = x0t.device
+    _, _, rho_ser = solver.serial_reference()
+    solver.w1_to(rho_ser).max().item()   # first launch of the W1 kernel (module load) outside the clock
+    solver.set_initial(x0t, y0t)
+    w1_hist, k_star = [], None
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for k in range(1, w.iters + 1):
+        solver.iterate()
+        w1k = float(solver.w1_to(rho_ser).max().item())
+        w1_hist.append(w1k)
+        if k_star is None and w1k <= 1e-3:
+            k_star = k
+            c1.record(stream)
+    torch.cuda.synchronize()
+    conv = {"w1_target": 1e-3, "iterations_to_target": k_star, "max_w1_per_iteration": w1_hist,
+            "iteration_ms": ms, "time_to_target_ms": (c0.elapsed_time(c1) if k_star else None),
+            "note": "W1 between the parareal macroscopic states and the restriction of the serial fine "
+                    "solution with the same random numbers, max over slices; time includes the per-"
+                    "iteration W1 reduction"}
+    if not detail:
+        return conv
+    # the same iterations skipping the converged slices (iteration k propagates
+    # slices k..K-1 only; exactness property): same states, less fine work
+    if k_star:
+        ss = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                            rng=L.Rng(w.seed, rank), device=str(dev), chunk=chunk, skip_converged=True)
+        ss.set_initial(x0t, y0t)
+        ss.iterate()                      # module loads and scratch outside the clock
+        torch.cuda.synchronize()
+        ss.set_initial(x0t, y0t)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(k_star):           # timed like the loop above, W1 included
+            ss.iterate()
+            w1_skip = float(ss.w1_to(rho_ser).max().item())
+        s1.record(stream)
+        torch.cuda.synchronize()
+        conv["skip_converged"] = {
+            "time_to_target_ms": s0.elapsed_time(s1),
+            "fine_slices_propagated": sum(w.K - k for k in range(k_star)),
+            "fine_slices_full": k_star * w.K,
+            "max_w1_at_target": w1_skip, "same_as_full": w1_skip == w1_hist[k_star - 1]}
+        ss.close()
+        del ss
+    # wall time per iteration as CUDA graph replays (pipelined chunks inside
+    # each graph), median of 10 after two warm-up iterations
+    gs = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                        rng=L.Rng(w.seed, rank), device=str(dev), chunk=chunk, graph=True)
+    gs.set_initial(x0t, y0t)
+    for _ in range(3):
+        gs.iterate()
+    torch.cuda.synchronize()
+    gt = []
+    for _ in range(10):
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        gs.iterate()
+        g1.record(stream)
+        g1.synchronize()
+        gt.append(g0.elapsed_time(g1))
+    gs.close()
+    del gs
+    conv["graph_iteration_ms_median"] = statistics.median(gt)
+    conv["time_to_target_graph_ms"] = (k_star * statistics.median(gt)) if k_star else None
+    # binary32 against the plain FP64 path on a paired smaller run (2^16 particles, 10 slices, 3 iterations)
+    ws_ = w.scaled(N=1 << 16, K=10, T=w.slice_dt * 10, iters=3)
+    x0s, y0s = workloads.initial_ensemble(ws_)
+    rhos = {}
+    for prec in (L.PR_F32, L.PR_F64):
+        dty = torch.float32 if prec == L.PR_F32 else torch.float64
+        sv = PararealSolver(model, grid, ws_.N, ws_.K, ws_.steps, ws_.step_dt, precision=prec,
+                            rng=L.Rng(w.seed, rank), device=str(dev))
+        sv.set_initial(torch.tensor(x0s, dtype=dty, device=dev), torch.tensor(y0s, dtype=dty, device=dev))
+        for _ in range(ws_.iters):
+            sv.iterate()
+        rhos[prec] = sv.rho.clone()
+        sv.close()
+    wv = torch.empty(ws_.K + 1, dtype=torch.float64, device=dev)
+    L.pr_w1(grid, ws_.K + 1, rhos[L.PR_F32], rhos[L.PR_F64], wv)
+    conv["fp32_vs_fp64_max_w1"] = float(wv.max().item())
+    conv["fp32_vs_fp64_case"] = "2^16 particles, 10 slices x 1000 steps, 3 iterations"
+    return conv
+
+
+def _batched_leg(L, dev, stream, rank, ws, dist):
+    """Batched serving: 64 independent OU problems with uneven eps, lambda and
+    particle counts, one persistent launch per iteration, graph-replayed,
+    scheduling picked by the autotuner; then the batch's convergence from X_0."""
+    import torch
+    from paper_1912_09240_gb300.batch import BatchSolver
+    from paper_1912_09240_gb300.replicas import max_over_ranks, shard, sum_over_ranks
+    bw = workloads.batched_problems()
+    probs, bx, by = [], [], []
+    # independent problems: each rank serves its share, no collective
+    mine = shard([float(pw.N * pw.K * pw.steps) for pw in bw.problems], rank, ws)
+    for pw in (bw.problems[i] for i in mine):
+        probs.append(L.Problem(L.Model(pw.kind, 1, pw.lam, pw.beta, pw.eps), L.Grid(pw.bins, pw.lo, pw.hi),
+                               pw.N, pw.K, pw.steps, pw.step_dt, pw.seed))
+        xx, yy = workloads.initial_ensemble(pw)
+        bx.append(xx.astype(np.float32))
+        by.append(yy[0].astype(np.float32))
+    bs = BatchSolver(probs, device=str(dev))
+    bs.set_initial(bx, by)
+    t_tune0 = time.perf_counter()
+    tuned_ms = bs.tune(steps_div=8)
+    tune_s = time.perf_counter() - t_tune0
+    bs.set_initial(bx, by)
+    bs.iterate()   # zeroth -> first iteration (eager)
+    bs.iterate()   # first graph replay (captures)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nb = 3
+    b0.record(stream)
+    for _ in range(nb):
+        bs.iterate()
+    b1.record(stream)
+    torch.cuda.synchronize()
+    bms = max_over_ranks(b0.elapsed_time(b1) / nb, dist, dev)
+    b_ps = sum_over_ranks(bs.particle_steps, dist, dev)
+    ppt, work, items = bs.config()
+    batched = {"workload": bw.name, "problems": len(bw.problems), "problems_per_rank": len(probs),
+               "particle_steps_per_iteration": b_ps,
+               "iteration_ms": bms, "particle_steps_per_s": b_ps / (bms / 1e3),
+               "graph_replayed": True, "tuned": {"particles_per_thread": ppt, "item_particle_steps": work,
+                                                  "items": items, "tune_s": tune_s, "trial_ms": tuned_ms},
+               "status": bs.status()}
+    # convergence of the batch from X_0: after each iteration, how many
+    # problems have max_n W1(rho_k^n, rho_{k-1}^n) <= 1e-3 (12 iterations)
+    bs.set_initial(bx, by)
+    prev = bs.snapshot()
+    within, worst = [], []
+    for _ in range(12):
+        bs.iterate()
+        cur = bs.snapshot()
+        inc_b = bs.increments(prev, cur)
+        within.append(int((inc_b <= 1e-3).sum().item()))
+        worst.append(float(inc_b.max().item()))
+        prev = cur
+    batched["increments"] = {"tol": 1e-3, "problems_within_tol_per_iteration": within,
+                             "max_increment_per_iteration": worst,
+                             "note": "increment = max over slices of W1 between consecutive iterates; "
+                                     "the exactness theorem makes it 0 at iteration K + 1"}
+    bs.close()
+    return batched
+
+
+# Side legs: off by default (the default run measures the headline, the
+# dominant kernel, the end-to-end path and the CPU baseline); `--legs a,b` or
+# `--legs all` adds them.  Each leg's result goes to stderr as one JSON line
+# {"leg": name, ...} and, with --legs-out, into one JSON file.
+LEGS = ("fp64_iteration", "convergence_detail", "batched", "unfused", "plain_ou", "matchings", "advection",
+        "studies", "adjoint", "fast16", "cpu_detail")
+
+
+def parse_legs(spec: str | None) -> list:
+    if not spec:
+        return []
+    names = [s.strip() for s in spec.split(",") if s.strip()]
+    if names == ["all"]:
+        return list(LEGS)
+    bad = [n for n in names if n not in LEGS]
+    if bad:
+        raise SystemExit(f"unknown leg(s) {bad}; choose from {', '.join(LEGS)} or all")
+    return names
+
+
+def _r(v, digits=4):
+    """A float rounded to `digits` significant digits (compact JSON)."""
+    if v is None:
+        return None
+    return float(f"{v:.{digits}g}")
+
+
+def compact_line(*, metric, value, unit, n_gpus, steps, warmup, ms_per_step, workload, config, clocks, roofline,
+                 cpu, e2e, launches, fp32_over_fp64=None, iters_to_w1=None, time_to_w1_ms=None) -> dict:
+    """The final stdout line: the contract's keys only, rounded, well under
+    1 KB (side legs are reported elsewhere).  `iters_to_w1` is the number of
+    parareal iterations until max_n W1(rho_k^n, R X_serial^n) <= 1e-3 and
+    `ms_to_w1` the time they take; `fp32_over_fp64` the binary32 fine
+    kernel's rate over the plain FP64 kernel's; the roofline is that of the
+    dominant kernel, fine_f32_d1_kernel."""
+    line = {
+        "metric": metric, "value": _r(value), "unit": unit, "n_gpus": n_gpus, "steps": steps, "warmup": warmup,
+        "ms_per_step": _r(ms_per_step), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": dict(workload=workload, **config),
+        "gpu_launches": launches,
+        "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
+                   "reasons": clocks.get("reasons", [])},
+        "roofline": None if roofline is None else {
+            "bound": roofline["bound"], "achieved": _r(roofline["achieved"]), "peak": _r(roofline["peak"]),
+            "unit": roofline["unit"], "frac": _r(roofline["frac"]),
+            "traffic": None if roofline.get("traffic") is None else _r(roofline["traffic"])},
+        "cpu_baseline": None if cpu is None else {"value": _r(cpu["value"]), "unit": cpu["unit"],
+                                                  "cores": cpu["cores"], "kind": cpu["kind"],
+                                                  "sample": cpu["sample"]},
+        "e2e": None if e2e is None else {"value": _r(e2e["value"]), "unit": e2e["unit"],
+                                         "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                                         "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]},
+        "fp32_over_fp64": _r(fp32_over_fp64, 3), "iters_to_w1": iters_to_w1, "ms_to_w1": _r(time_to_w1_ms),
+    }
+    return line
+
+
+def emit_line(line: dict) -> str:
+    s = json.dumps(line, separators=(",", ":"), ensure_ascii=False)
+    if len(s.encode()) >= 1024:
+        raise RuntimeError(f"final bench line is {len(s.encode())} bytes (limit 1024)")
+    print(s, flush=True)
+    return s
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -594,12 +862,14 @@ def run_ours(args):
     from paper_1912_09240_gb300 import _lib as L
     from paper_1912_09240_gb300 import build as b
     from paper_1912_09240_gb300.parareal import PararealSolver
+    from paper_1912_09240_gb300.replicas import max_over_ranks, sum_over_ranks
     if rank == 0 or ws == 1:
         b.build()
     if dist:
         dist.barrier()
     if args.update_cluster:
         L.pr_set_update_cluster(args.update_cluster)
+    legs = parse_legs(args.legs)
     w = WORKLOAD
     model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
     grid = L.Grid(w.bins, w.lo, w.hi)
@@ -637,7 +907,8 @@ def run_ours(args):
             dist.barrier()
     ms = t0.elapsed_time(t1) / args.steps
     # the dominant kernel on its own: sequential iterations (one fine launch
-    # over slices 1..K-1 each), timed with events around that launch
+    # over slices 1..K-1 each), timed with events around that launch on the
+    # stream it runs on
     chunk_saved, solver.chunk = solver.chunk, 0
     solver.fine_events = []
     for _ in range(2):
@@ -646,226 +917,72 @@ def run_ours(args):
     fine_times = solver.fine_events
     solver.fine_events = None
     solver.chunk = chunk_saved
-    from paper_1912_09240_gb300.replicas import max_over_ranks, shard, sum_over_ranks
     ms = max_over_ranks(ms, dist, dev)
     ps_per_step = w.particle_steps_per_iteration
     value = ws * ps_per_step / (ms / 1e3)
     fine_ms = statistics.mean(a.elapsed_time(b_) for a, b_ in fine_times) if fine_times else None
 
-    # end to end through the public API: host X_0 in, host rho out, every step
+    # end to end through the C ABI with host buffers: every step copies X_0
+    # and Y_0 from page-locked host memory (pr_copy_to_device), runs R X_0,
+    # the zeroth iteration and one parareal iteration, and copies rho back
+    # (pr_copy_to_host) before the host synchronises
     x0h = torch.tensor(x0, dtype=torch.float32).pin_memory()
     y0h = torch.tensor(y0, dtype=torch.float32).pin_memory()
     rho_h = torch.empty(w.K + 1, w.bins + 1, dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
+    solver.set_initial_host(x0h, y0h)
+    solver.iterate()
+    solver.rho_to_host(rho_h)
+    L.pr_stream_synchronize(stream)
+    if dist:
+        dist.barrier()
     te0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        x0t.copy_(x0h, non_blocking=True)
-        y0t.copy_(y0h, non_blocking=True)
-        solver.set_initial(x0t, y0t)
+    for _ in range(args.steps):
+        solver.set_initial_host(x0h, y0h)
         solver.iterate()
-        rho_h.copy_(solver.rho, non_blocking=True)   # .rho joins the solver's streams
-        torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - te0) / e2e_steps
+        solver.rho_to_host(rho_h)
+        L.pr_stream_synchronize(stream)
+    e2e_s = max_over_ranks((time.perf_counter() - te0) / args.steps, dist, dev)
     e2e = {"value": ws * ps_per_step / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(x0h.numel() * 4 + y0h.numel() * 4),
            "d2h_bytes_per_step": int(rho_h.numel() * 8)}
 
-    # plain FP64 GPU path on a sample of the same workload (2 slices)
-    fp64 = None
-    if not args.no_fp64:
-        xs = torch.tensor(np.stack([x0, x0]), dtype=torch.float64, device=dev)
-        ys = torch.tensor(np.stack([y0, y0]), dtype=torch.float64, device=dev)
-        L.pr_fine_propagate(model, L.PR_F64, L.Rng(w.seed), xs, ys, False, xs, ys, w.N, 1, 2, 50, w.step_dt)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        L.pr_fine_propagate(model, L.PR_F64, L.Rng(w.seed), xs, ys, False, xs, ys, w.N, 1, 2, w.steps, w.step_dt)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        fp64_rate = 2 * w.N * w.steps / (f0.elapsed_time(f1) / 1e3)
-        fine_rate = (w.K - 1) * w.N * w.steps / (fine_ms / 1e3) if fine_ms else None
-        fp64 = {"fp64_particle_steps_per_s": fp64_rate,
-                "fp32_fine_particle_steps_per_s": fine_rate,
-                "fp32_over_fp64": (fine_rate / fp64_rate) if fine_rate else None,
-                "sample": f"FP64 fine kernel, {w.N} particles x 2 slices x {w.steps} steps"}
-        del xs, ys
-        # one whole parareal iteration of the workload on the plain FP64 path
-        # (pipelined driver as above), after one warm-up iteration
-        sv = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F64,
-                            rng=L.Rng(w.seed, rank), device=str(dev), chunk=args.chunk)
-        sv.set_initial(torch.tensor(x0, dtype=torch.float64, device=dev),
-                       torch.tensor(y0, dtype=torch.float64, device=dev))
-        sv.iterate()
-        torch.cuda.synchronize()
-        f0.record(stream)
-        sv.iterate()
-        sv.join()
-        f1.record(stream)
-        torch.cuda.synchronize()
-        fp64["fp64_iteration_ms"] = f0.elapsed_time(f1)
-        fp64["fp64_over_fp32_iteration_time"] = fp64["fp64_iteration_ms"] / ms
-        sv.close()
-        del sv
+    fp64 = _fp64_leg(L, w, model, stream, fine_ms)
+    conv = _convergence_leg(L, solver, w, model, grid, stream, rank, args.chunk, ms, x0t, y0t,
+                            "convergence_detail" in legs)
 
-    # convergence: iterations until max_n W1(rho_k^n, R X_serial^n) <= 1e-3,
-    # against the serial fine solution with the same random numbers
-    conv = None
-    if not args.no_conv:
-        _, _, rho_ser = solver.serial_reference()
-        solver.w1_to(rho_ser).max().item()   # first launch of the W1 kernel (module load) outside the clock
-        solver.set_initial(x0t, y0t)
-        w1_hist, k_star = [], None
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        for k in range(1, w.iters + 1):
-            solver.iterate()
-            w1k = float(solver.w1_to(rho_ser).max().item())
-            w1_hist.append(w1k)
-            if k_star is None and w1k <= 1e-3:
-                k_star = k
-                c1.record(stream)
-        torch.cuda.synchronize()
-        conv = {"w1_target": 1e-3, "iterations_to_target": k_star, "max_w1_per_iteration": w1_hist,
-                "iteration_ms": ms,
-                "time_to_target_ms": (c0.elapsed_time(c1) if k_star else None),
-                "note": "W1 between the parareal macroscopic states and the restriction of the serial fine "
-                        "solution with the same random numbers, max over slices; time includes the per-"
-                        "iteration W1 reduction"}
-        # the same iterations skipping the converged slices (iteration k propagates
-        # slices k..K-1 only; exactness property): same states, less fine work
-        if k_star:
-            ss = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
-                                rng=L.Rng(w.seed, rank), device=str(dev), chunk=args.chunk, skip_converged=True)
-            ss.set_initial(x0t, y0t)
-            ss.iterate()                      # module loads and scratch outside the clock
-            torch.cuda.synchronize()
-            ss.set_initial(x0t, y0t)
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
-            for _ in range(k_star):           # timed like the loop above, W1 included
-                ss.iterate()
-                w1_skip = float(ss.w1_to(rho_ser).max().item())
-            s1.record(stream)
-            torch.cuda.synchronize()
-            conv["skip_converged"] = {
-                "time_to_target_ms": s0.elapsed_time(s1),
-                "fine_slices_propagated": sum(w.K - k for k in range(k_star)),
-                "fine_slices_full": k_star * w.K,
-                "max_w1_at_target": w1_skip, "same_as_full": w1_skip == w1_hist[k_star - 1]}
-            ss.close()
-            del ss
-        # wall time per iteration as CUDA graph replays (pipelined chunks inside
-        # each graph), median of 10 after two warm-up iterations
-        gs = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
-                            rng=L.Rng(w.seed, rank), device=str(dev), chunk=args.chunk, graph=True)
-        gs.set_initial(x0t, y0t)
-        for _ in range(3):
-            gs.iterate()
-        torch.cuda.synchronize()
-        gt = []
-        for _ in range(10):
-            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            g0.record(stream)
-            gs.iterate()
-            g1.record(stream)
-            g1.synchronize()
-            gt.append(g0.elapsed_time(g1))
-        gs.close()
-        del gs
-        conv["graph_iteration_ms_median"] = statistics.median(gt)
-        conv["time_to_target_graph_ms"] = (k_star * statistics.median(gt)) if k_star else None
-        # FP32 against the plain FP64 path on a paired smaller run (2^16 particles, 10 slices, 3 iterations)
-        ws_ = w.scaled(N=1 << 16, K=10, T=w.slice_dt * 10, iters=3)
-        x0s, y0s = workloads.initial_ensemble(ws_)
-        rhos = {}
-        for prec in (L.PR_F32, L.PR_F64):
-            dty = torch.float32 if prec == L.PR_F32 else torch.float64
-            sv = PararealSolver(model, grid, ws_.N, ws_.K, ws_.steps, ws_.step_dt, precision=prec,
-                                rng=L.Rng(w.seed, rank), device=str(dev))
-            sv.set_initial(torch.tensor(x0s, dtype=dty, device=dev), torch.tensor(y0s, dtype=dty, device=dev))
-            for _ in range(ws_.iters):
-                sv.iterate()
-            rhos[prec] = sv.rho.clone()
-            sv.close()
-        wv = torch.empty(ws_.K + 1, dtype=torch.float64, device=dev)
-        L.pr_w1(grid, ws_.K + 1, rhos[L.PR_F32], rhos[L.PR_F64], wv)
-        conv["fp32_vs_fp64_max_w1"] = float(wv.max().item())
-        conv["fp32_vs_fp64_case"] = "2^16 particles, 10 slices x 1000 steps, 3 iterations"
+    side = {}
 
-    # batched serving: 64 independent OU problems with uneven eps, lambda and
-    # particle counts, one persistent launch per iteration, graph-replayed,
-    # scheduling picked by the autotuner
-    batched = None
-    if not args.no_batch:
-        from paper_1912_09240_gb300.batch import BatchSolver
-        bw = workloads.batched_problems()
-        probs, bx, by = [], [], []
-        # independent problems: each rank serves its share, no collective
-        mine = shard([float(pw.N * pw.K * pw.steps) for pw in bw.problems], rank, ws)
-        for pw in (bw.problems[i] for i in mine):
-            probs.append(L.Problem(L.Model(pw.kind, 1, pw.lam, pw.beta, pw.eps), L.Grid(pw.bins, pw.lo, pw.hi),
-                                   pw.N, pw.K, pw.steps, pw.step_dt, pw.seed))
-            xx, yy = workloads.initial_ensemble(pw)
-            bx.append(xx.astype(np.float32))
-            by.append(yy[0].astype(np.float32))
-        bs = BatchSolver(probs, device=str(dev))
-        bs.set_initial(bx, by)
-        t_tune0 = time.perf_counter()
-        tuned_ms = bs.tune(steps_div=8)
-        tune_s = time.perf_counter() - t_tune0
-        bs.set_initial(bx, by)
-        bs.iterate()   # zeroth -> first iteration (eager)
-        bs.iterate()   # first graph replay (captures)
-        torch.cuda.synchronize()
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        nb = 3
-        b0.record(stream)
-        for _ in range(nb):
-            bs.iterate()
-        b1.record(stream)
-        torch.cuda.synchronize()
-        bms = max_over_ranks(b0.elapsed_time(b1) / nb, dist, dev)
-        b_ps = sum_over_ranks(bs.particle_steps, dist, dev)
-        ppt, work, items = bs.config()
-        batched = {"workload": bw.name, "problems": len(bw.problems), "problems_per_rank": len(probs),
-                   "particle_steps_per_iteration": b_ps,
-                   "iteration_ms": bms, "particle_steps_per_s": b_ps / (bms / 1e3),
-                   "graph_replayed": True, "tuned": {"particles_per_thread": ppt, "item_particle_steps": work,
-                                                      "items": items, "tune_s": tune_s,
-                                                      "trial_ms": tuned_ms},
-                   "status": bs.status()}
-        # convergence of the batch from X_0: after each iteration, how many
-        # problems have max_n W1(rho_k^n, rho_{k-1}^n) <= 1e-3 (12 iterations)
-        bs.set_initial(bx, by)
-        prev = bs.snapshot()
-        within, worst = [], []
-        for _ in range(12):
-            bs.iterate()
-            cur = bs.snapshot()
-            inc_b = bs.increments(prev, cur)
-            within.append(int((inc_b <= 1e-3).sum().item()))
-            worst.append(float(inc_b.max().item()))
-            prev = cur
-        batched["increments"] = {"tol": 1e-3, "problems_within_tol_per_iteration": within,
-                                 "max_increment_per_iteration": worst,
-                                 "note": "increment = max over slices of W1 between consecutive iterates; "
-                                         "the exactness theorem makes it 0 at iteration K + 1"}
-        bs.close()
+    def leg(name, fn):
+        if name in legs:
+            t = time.perf_counter()
+            side[name] = fn()
+            if rank == 0:
+                print(json.dumps({"leg": name, "s": round(time.perf_counter() - t, 1), **side[name]}),
+                      file=sys.stderr, flush=True)
 
-    unfused = None if args.no_unfused else _unfused_leg(L, solver, w, stream, _peaks().get("hbm_gbs"))
-    plain = None if args.no_plain else _plain_leg(L, dev, stream, rank)
-    matchings = None if args.no_matchings else _matching_leg(L, dev, stream, rank, args.chunk)
-    advection = None if args.no_advection else _advection_leg(L, dev, stream)
-    studies = None if args.no_studies else _studies_leg(L, dev, stream, rank)
-    adjoint = None if args.no_adjoint else _adjoint_leg(L, dev, stream, rank, n=args.adjoint_n)
-    large = None
-    if not args.no_large:
+    if "convergence_detail" in legs and rank == 0:
+        print(json.dumps({"leg": "convergence_detail", **conv}), file=sys.stderr, flush=True)
+        side["convergence_detail"] = conv
+    if rank == 0:
+        print(json.dumps({"leg": "fp64_sample", **fp64}), file=sys.stderr, flush=True)
+    leg("fp64_iteration", lambda: _fp64_iteration_leg(L, w, model, grid, stream, rank, args.chunk, ms))
+    leg("batched", lambda: _batched_leg(L, dev, stream, rank, ws, dist))
+    leg("unfused", lambda: _unfused_leg(L, solver, w, stream, _peaks().get("hbm_gbs")))
+    leg("plain_ou", lambda: _plain_leg(L, dev, stream, rank))
+    leg("matchings", lambda: _matching_leg(L, dev, stream, rank, args.chunk))
+    leg("advection", lambda: _advection_leg(L, dev, stream))
+    leg("studies", lambda: _studies_leg(L, dev, stream, rank))
+    leg("adjoint", lambda: _adjoint_leg(L, dev, stream, rank, n=args.adjoint_n))
+    if "fast16" in legs:
         solver.close()
-        large = _large_leg(L, dev, stream, rank, args.chunk, n=args.large_n, k=args.large_k)
-        if dist:
-            large["particle_steps_per_s"] = sum_over_ranks(large["particle_steps_per_iteration"], dist, dev) / (
-                max_over_ranks(large["iteration_ms"], dist, dev) / 1e3)
+
+        def fast16():
+            r = _large_leg(L, dev, stream, rank, args.chunk, n=args.large_n, k=args.large_k)
+            if dist:
+                r["particle_steps_per_s"] = sum_over_ranks(r["particle_steps_per_iteration"], dist, dev) / (
+                    max_over_ranks(r["iteration_ms"], dist, dev) / 1e3)
+            return r
+        leg("fast16", fast16)
 
     if rank != 0:
         if dist:
@@ -885,39 +1002,31 @@ def run_ours(args):
         traffic = (TRAFFIC_BYTES_PER_PARTICLE_SLICE * (w.K - 1) * w.N
                    if TRAFFIC_BYTES_PER_PARTICLE_SLICE else None)
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
-                    "frac": achieved / peak, "traffic": traffic,
-                    "kernel": "fine_f32_d1_kernel (slices 1..49)",
-                    "fine_ms_per_launch": fine_ms,
-                    "achieved_in_step": INST_PER_PARTICLE_STEP * ps_per_step / (ms / 1e3) / 1e12,
-                    "peak_basis": f"152 SMs x 4 warp-instr/clk x 32 lanes x {sm_max:.0f} MHz (max SM clock)",
-                    "algorithmic": f"{INST_PER_PARTICLE_STEP} thread-instructions per particle-step x "
-                                   f"{launch_ps:.3e} particle-steps per launch"}
-    cpu = None if args.no_cpu else _cpu_sample()
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "N": w.N, "K": w.K, "steps_per_slice": w.steps, "dt": w.step_dt,
-                   "bins": w.bins, "iterator": "quantile (two-sided)", "parallelism": f"replicas x{ws}",
-                   "pipeline_chunk": args.chunk, "update_cluster": args.update_cluster or 8,
-                   "l2": "inputs larger than L2: 840 MB of ensemble state per step"},
-        "gpu_launches": launches,
-        "clocks": clocks,
-        "roofline": roofline,
-        "cpu_baseline": cpu,
-        "e2e": e2e,
-        "fp64_vs_fp32": fp64,
-        "convergence": conv,
-        "batched": batched,
-        "unfused": unfused,
-        "plain_ou": plain,
-        "matchings": matchings,
-        "advection": advection,
-        "studies": studies,
-        "adjoint": adjoint,
-        "fast16": large,
-    }
-    print(json.dumps(line), flush=True)
+                    "frac": achieved / peak, "traffic": traffic, "kernel": "fine_f32_d1_kernel"}
+        if rank == 0:
+            print(json.dumps({"leg": "roofline_detail", **roofline, "fine_ms_per_launch": fine_ms,
+                              "achieved_in_step": INST_PER_PARTICLE_STEP * ps_per_step / (ms / 1e3) / 1e12,
+                              "peak_basis": f"152 SMs x 4 warp-instr/clk x 32 lanes x {sm_max:.0f} MHz",
+                              "algorithmic": f"{INST_PER_PARTICLE_STEP} thread-instructions per particle-step x "
+                                             f"{launch_ps:.3e} particle-steps per launch"}),
+                  file=sys.stderr, flush=True)
+    cpu = None
+    if not args.no_cpu:
+        cpu = _cpu_sample(detail="cpu_detail" in legs)
+        print(json.dumps({"leg": "cpu_baseline", **cpu}), file=sys.stderr, flush=True)
+    if args.legs_out:
+        with open(args.legs_out, "w") as f:
+            json.dump({"fp64_sample": fp64, "convergence": conv, "e2e": e2e, "clocks": clocks,
+                       "roofline": roofline, "fine_ms_per_launch": fine_ms, "cpu_baseline": cpu, **side}, f,
+                      indent=1)
+    line = compact_line(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps, warmup=args.warmup,
+        ms_per_step=ms, workload=w.name,
+        config={"bins": w.bins, "parallelism": f"replicas x{ws}", "l2": "inputs>L2"},
+        clocks=clocks, roofline=roofline, cpu=cpu, e2e=e2e, launches=launches,
+        fp32_over_fp64=fp64.get("fp32_over_fp64"), iters_to_w1=conv.get("iterations_to_target"),
+        time_to_w1_ms=conv.get("time_to_target_ms"))
+    emit_line(line)
     solver.close()
     if dist:
         dist.barrier()
@@ -931,20 +1040,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--legs", default="", help=f"side legs to run: comma list of {', '.join(LEGS)}, or all")
+    ap.add_argument("--legs-out", default=None, help="write every measured figure as one JSON file")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU sample")
-    ap.add_argument("--no-conv", action="store_true", help="skip the convergence study")
     ap.add_argument("--update-cluster", type=int, default=None, help="CTAs of the serial-sweep cluster")
     ap.add_argument("--chunk", type=int, default=5, help="slices per pipelined chunk (0: sequential)")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-serving leg")
-    ap.add_argument("--no-unfused", action="store_true", help="skip standalone restriction/matching/coarse timing")
-    ap.add_argument("--no-studies", action="store_true", help="skip the convergence studies")
-    ap.add_argument("--no-advection", action="store_true", help="skip the linear advection case")
-    ap.add_argument("--no-matchings", action="store_true", help="skip the comparison of the matchings")
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain OU workload legs")
-    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--adjoint-n", type=int, default=None, help="particles of the adjoint leg")
-    ap.add_argument("--no-large", action="store_true", help="skip the 16-dimensional fast-space leg")
     ap.add_argument("--large-n", type=int, default=None, help="particles of the 16-dimensional leg")
     ap.add_argument("--large-k", type=int, default=None, help="slices of the 16-dimensional leg")
     ap.add_argument("--n", type=int, default=None, help="particles (smaller case for profiling)")

@@ -433,7 +433,10 @@ pr_status pr_fine_adjoint_affine(const pr_model* model, const pr_rng* rng, const
  *    exceeds the capacity is rejected with PR_ERR_NOMEM before anything runs.
  *  - The first call on a device looks up the array's device address there
  *    (the device must be current); make that first call before any stream
- *    capture.
+ *    capture.  The address is kept for the life of the process: after a
+ *    cudaDeviceReset (or any other teardown of the device's primary context)
+ *    it is stale, and this entry point must not be called on that device
+ *    again in the same process.
  *  - All calls share the one array and it keeps the last call's contents.
  *    Every word a call reads it has written first, so nothing needs clearing;
  *    calls that overlap on the GPU (other streams, other threads) race on the
@@ -525,6 +528,20 @@ pr_status pr_batch_tune(void* plan, int32_t steps_div, double* best_ms, void* st
  */
 pr_status pr_w1(const pr_grid* grid, int32_t n_vec, const double* c1, const double* c2,
                 double* w1, void* stream);
+
+/*
+ * Transfers for callers that keep the initial ensemble X_0 and the resulting
+ * macroscopic states in host memory (no counterpart in the paper: plumbing of
+ * the boundary).  pr_copy_to_device copies `bytes` from src (host) to dst
+ * (device); pr_copy_to_host from src (device) to dst (host).  Both are
+ * asynchronous on `stream` when the host buffer is page-locked (otherwise the
+ * CUDA runtime may return before or after the copy, as it documents for
+ * cudaMemcpyAsync); bytes == 0 is a no-op.  pr_stream_synchronize waits for
+ * everything enqueued on `stream`.  A failed CUDA call returns PR_ERR_CUDA.
+ */
+pr_status pr_copy_to_device(void* dst, const void* src, size_t bytes, void* stream);
+pr_status pr_copy_to_host(void* dst, const void* src, size_t bytes, void* stream);
+pr_status pr_stream_synchronize(void* stream);
 
 #ifdef __cplusplus
 }

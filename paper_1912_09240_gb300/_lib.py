@@ -30,7 +30,8 @@ EXPORTED = (
     "pr_batch_create", "pr_batch_destroy", "pr_batch_particle_steps", "pr_batch_set_initial", "pr_batch_iterate",
     "pr_batch_rho", "pr_batch_fine_state", "pr_batch_status", "pr_batch_set_config", "pr_batch_get_config",
     "pr_batch_tune", "pr_reweight", "pr_resample_workspace", "pr_resample", "pr_restrict_weighted_workspace",
-    "pr_restrict_weighted", "pr_moments_workspace", "pr_moments",
+    "pr_restrict_weighted", "pr_moments_workspace", "pr_moments", "pr_copy_to_device", "pr_copy_to_host",
+    "pr_stream_synchronize",
 )
 
 
@@ -177,6 +178,9 @@ def lib() -> ctypes.CDLL:
     L.pr_moments_workspace.argtypes = [i64, i32, i32]
     L.pr_moments_workspace.restype = ctypes.c_size_t
     L.pr_moments.argtypes = [i32, vp, i64, vp, i64, i32, i32, vp, vp, ctypes.c_size_t, vp]
+    L.pr_copy_to_device.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.pr_copy_to_host.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.pr_stream_synchronize.argtypes = [vp]
     for name in EXPORTED:
         if name not in ("pr_status_string", "pr_version", "pr_set_particles_per_thread",
                         "pr_set_tiles_per_cta", "pr_set_update_cluster", "pr_fine_adjoint_workspace",
@@ -457,3 +461,25 @@ def pr_batch_tune(plan: int, steps_div: int = 8, stream=None) -> float:
     best = ctypes.c_double()
     _check("pr_batch_tune", lib().pr_batch_tune(plan, steps_div, ctypes.byref(best), _stream(stream)))
     return best.value
+
+
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size()
+
+
+def pr_copy_to_device(dst, src, stream=None):
+    """Copy the host tensor `src` into the device tensor `dst` (same size in bytes)."""
+    if _nbytes(dst) != _nbytes(src):
+        raise ValueError("pr_copy_to_device: sizes differ")
+    _check("pr_copy_to_device", lib().pr_copy_to_device(_ptr(dst), _ptr(src), _nbytes(src), _stream(stream)))
+
+
+def pr_copy_to_host(dst, src, stream=None):
+    """Copy the device tensor `src` into the host tensor `dst` (same size in bytes)."""
+    if _nbytes(dst) != _nbytes(src):
+        raise ValueError("pr_copy_to_host: sizes differ")
+    _check("pr_copy_to_host", lib().pr_copy_to_host(_ptr(dst), _ptr(src), _nbytes(src), _stream(stream)))
+
+
+def pr_stream_synchronize(stream=None):
+    _check("pr_stream_synchronize", lib().pr_stream_synchronize(_stream(stream)))

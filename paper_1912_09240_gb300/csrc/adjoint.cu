@@ -650,7 +650,8 @@ constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB
 static __device__ __align__(256) unsigned char g_adjoint_scratch[kNoAllocScratchBytes];
 
 // The array's device address on the current device.  Looked up once per
-// device (with that device current) and kept.
+// device (with that device current) and kept for the life of the process; a
+// reset of the device's primary context makes it stale (stated in pr.h).
 static pr_status adjoint_scratch_address(void** out)
 {
     static std::mutex mu;

@@ -487,3 +487,28 @@ extern "C" const char* pr_status_string(pr_status s)
 }
 
 extern "C" const char* pr_version(void) { return "0.1.0"; }
+
+/* Host <-> device transfers of caller buffers, for callers that hold their
+ * inputs and results in host memory (no method arithmetic: one
+ * cudaMemcpyAsync each, ordered on `stream`). */
+extern "C" pr_status pr_copy_to_device(void* dst, const void* src, size_t bytes, void* stream)
+{
+    if (bytes == 0) return PR_OK;
+    if (!dst || !src) return PR_ERR_INVALID_ARG;
+    PR_TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream)));
+    return PR_OK;
+}
+
+extern "C" pr_status pr_copy_to_host(void* dst, const void* src, size_t bytes, void* stream)
+{
+    if (bytes == 0) return PR_OK;
+    if (!dst || !src) return PR_ERR_INVALID_ARG;
+    PR_TRY_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream)));
+    return PR_OK;
+}
+
+extern "C" pr_status pr_stream_synchronize(void* stream)
+{
+    PR_TRY_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return PR_OK;
+}

@@ -170,6 +170,24 @@ class PararealSolver:
         s = self._s()
         self.x0.copy_(x0.reshape(self.n))
         self.y0.copy_(y0.reshape(self.model.fast_dim, self.n))
+        self._initial_states(s)
+
+    def set_initial_host(self, x0: torch.Tensor, y0: torch.Tensor):
+        """set_initial() from X_0 and Y_0 in host memory (page-locked for an
+        asynchronous copy), copied into the solver by the library."""
+        self.join()
+        s = self._s()
+        L.pr_copy_to_device(self.x0, x0.reshape(self.n), stream=s)
+        L.pr_copy_to_device(self.y0, y0.reshape(self.model.fast_dim, self.n), stream=s)
+        self._initial_states(s)
+
+    def rho_to_host(self, out: torch.Tensor):
+        """Copy rho_k^n, n = 0..K, into the host tensor `out` [K+1][bins+1]
+        (asynchronous on the solver's stream when `out` is page-locked)."""
+        L.pr_copy_to_host(out, self.rho, stream=self._s())
+
+    def _initial_states(self, s):
+        """R X_0 and the zeroth iteration (serial coarse sweep), on stream s."""
         if self.matching == "reweight":   # every restriction carries the weights (here 1/N)
             L.pr_restrict_weighted(self.precision, self.x0, False, self.w_uni, self.n, 1, self.grid, self.cdf0,
                                    self._scratch("wr", 0, L.pr_restrict_weighted_workspace(1, self.grid.bins)),

@@ -8,7 +8,9 @@ agrees; and a problem larger than the array is refused before it runs.
 
 This file is collected last on purpose: run alone in a fresh process the
 array's first use is the first call here; run after the other tests it is
-not."""
+not.  The array's device address is looked up once per device and kept for
+the life of the process, so no test here resets the device (a reset would
+make that address stale, as the header states)."""
 import ctypes
 
 import numpy as np
