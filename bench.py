@@ -8,6 +8,15 @@ states, and the serial quantile-iterator update.  `value` is particle-steps
 per second over the whole job (all ranks); ranks are independent replicas.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--legs a,b|all] [--legs-out FILE]
+
+The last stdout line is one compact JSON object (under 1 KB): the headline,
+the dominant kernel's roofline, the end-to-end figure through the C ABI with
+host buffers, the CPU oracle baseline, clocks, and three scalars (binary32
+over FP64 fine-kernel rate, iterations and time to W1 <= 1e-3).  Side legs
+(the other workloads, standalone passes, studies) run only when named with
+--legs; each prints one JSON line {"leg": name, ...} to stderr, and
+--legs-out writes every figure into one JSON file.
 
 `--impl reference` times the FP64 CPU oracle (the only reference this method
 has) on a bounded sample of the same workload on the host cores.
@@ -137,19 +146,23 @@ def _cpu_sample(seconds_target: float = 12.0, detail: bool = False):
         orc.fine_propagate(om, w.seed, x0[None, :n_cal], y0[None, :, :n_cal], 1, s_cal, w.step_dt)
         rate = n_cal * s_cal / max(time.perf_counter() - t0, 1e-6)
         n = int(min(n_max, max(1 << 12, rate * target / w.steps)))
+        # all particles and still short of the target: several slices
+        nsl = max(1, min(w.K - 1, int(rate * target / (n * w.steps) + 0.5)))
+        xs = np.ascontiguousarray(np.broadcast_to(x0[:n], (nsl, n)))
+        ys = np.ascontiguousarray(np.broadcast_to(y0[:, :n], (nsl, w.fast_dim, n)))
         t0 = time.perf_counter()
-        orc.fine_propagate(om, w.seed, x0[None, :n], y0[None, :, :n], 1, w.steps, w.step_dt)
+        orc.fine_propagate(om, w.seed, xs, ys, 1, w.steps, w.step_dt)
         el = time.perf_counter() - t0
-        return n * w.steps / el, n, el
+        return nsl * n * w.steps / el, n, el, nsl
 
-    value, n, el = rate_of(w.N, seconds_target)
+    value, n, el, nsl = rate_of(w.N, seconds_target)
     out = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"{n} particles x {w.steps} EM steps, {el:.1f} s"}
+           "sample": f"{nsl} slices x {n} particles x {w.steps} EM steps, {el:.1f} s"}
     if not detail:
         return out
     orc.set_num_threads(1)
     try:
-        v1, n1, el1 = rate_of(w.N, seconds_target / 3)
+        v1, n1, el1, _ = rate_of(w.N, seconds_target / 3)
     finally:
         orc.set_num_threads(cores)
     # one slice of the 16-dimensional fast space, 2^16 particles
