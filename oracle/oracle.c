@@ -254,6 +254,95 @@ void or_fine_propagate(int kind, int d, double lambda, double beta, double eps, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* The chemically reacting system of Section 2.1.2 (Eqs. F_Bruna, G_Bruna,   */
+/* D, E_Bruna) under Euler-Maruyama (Eqs. EMx/EMy), one fast variable.       */
+/* Rates k[0..5] = k0 .. k5.  The paper prints                              */
+/*   F(x,y) = -k4 x y - k5 x^2 / 2,                                         */
+/*   G(x,y) = -k0 y - k1 y^2 / 2 + k2 y^2 (y/3 - 1/2) - k3 y^2 (y/2 - 1)^2,  */
+/*   D = (k4 y + k5 x) / 2,  E = (k0 + k1 y + k2 y(y-1) + k3 y(y-1)(y-2)) / 2 */
+/* whose D and E are half the total propensities of the reactions            */
+/* Y -> Y + X (k4 y), X -> 0 (k5 x), 0 -> Y (k0), Y -> 0 (k1 y),             */
+/* 2Y -> 3Y (k2 y(y-1)), 3Y -> 2Y (k3 y(y-1)(y-2)): the chemical Langevin   */
+/* form.  Two readings of the drifts:                                        */
+/*   reading 0 (chemical Langevin; the default): -d_x F = k4 y - k5 x and    */
+/*     -d_y G = k0 - k1 y + k2 y(y-1) - k3 y(y-1)(y-2), the net rates of     */
+/*     those reactions;                                                      */
+/*   reading 1 (as printed): d_x F = -k4 y - k5 x and                        */
+/*     d_y G = -k0 - k1 y + k2 y(y-1) - k3 y(y-1)(y-2), the derivatives of   */
+/*     the printed F and G.                                                  */
+/* 2D and 2E are sums of propensities, non-negative for x, y >= 0; where an  */
+/* Euler step leaves that range the square root takes max(2D, 0) and         */
+/* max(2E, 0) (a reading: the paper is silent).                             */
+/* ------------------------------------------------------------------------ */
+
+static double or_chem_dFdx(int reading, const double* k, double x, double y)
+{
+    if (reading == 0) return -(k[4] * y - k[5] * x);
+    return -k[4] * y - k[5] * x;
+}
+
+static double or_chem_dGdy(int reading, const double* k, double y)
+{
+    const double net = k[0] - k[1] * y + k[2] * y * (y - 1.0) - k[3] * y * (y - 1.0) * (y - 2.0);
+    if (reading == 0) return -net;
+    return -k[0] - k[1] * y + k[2] * y * (y - 1.0) - k[3] * y * (y - 1.0) * (y - 2.0);
+}
+
+static double or_chem_D(const double* k, double x, double y)
+{
+    return 0.5 * (k[4] * y + k[5] * x);
+}
+
+static double or_chem_E(const double* k, double y)
+{
+    return 0.5 * (k[0] + k[1] * y + k[2] * y * (y - 1.0) + k[3] * y * (y - 1.0) * (y - 2.0));
+}
+
+/* d_x F, d_y G, D and E at (x, y): out[0..3]. */
+void or_chem_coefficients(int reading, const double* k, double x, double y, double* out)
+{
+    out[0] = or_chem_dFdx(reading, k, x, y);
+    out[1] = or_chem_dGdy(reading, k, y);
+    out[2] = or_chem_D(k, x, y);
+    out[3] = or_chem_E(k, y);
+}
+
+/* As or_fine_propagate_ids, for the chemical system (d = 1, two normals per
+ * step: z[0] drives X, z[1] drives Y). */
+void or_fine_propagate_chem(int reading, const double* k, double eps, double tau_x,
+                            uint64_t seed, uint32_t problem,
+                            double* x, double* y, int64_t N, const uint32_t* ids,
+                            int slice_begin, int n_slices, int S, double dt)
+{
+    const double sqrt_dt = sqrt(dt);
+    for (int s = 0; s < n_slices; ++s) {
+        const uint32_t n = (uint32_t)(slice_begin + s);
+        double* xs = x + (int64_t)s * N;
+        double* ys = y + (int64_t)s * N;
+#pragma omp parallel for schedule(static)
+        for (int64_t p = 0; p < N; ++p) {
+            double X = xs[p], Y = ys[p], z[2];
+            const uint32_t pid = ids ? ids[p] : (uint32_t)p;
+            for (int m = 0; m < S; ++m) {
+                or_step_normals(seed, problem, pid, n, (uint32_t)m, 2, z);
+                const double dU = sqrt_dt * z[0];
+                const double dV = sqrt_dt * z[1];
+                const double D = or_chem_D(k, X, Y);
+                const double E = or_chem_E(k, Y);
+                const double Xnew = X - (1.0 / tau_x) * or_chem_dFdx(reading, k, X, Y) * dt
+                                      + sqrt(fmax(2.0 * D, 0.0) / tau_x) * dU;
+                const double Ynew = Y - (1.0 / eps) * or_chem_dGdy(reading, k, Y) * dt
+                                      + sqrt(fmax(2.0 * E, 0.0) / eps) * dV;
+                X = Xnew;
+                Y = Ynew;
+            }
+            xs[p] = X;
+            ys[p] = Y;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Tangent-linear (forward-mode) derivatives of the EM recursion with fixed   */
 /* noise (pathwise sensitivities; the paper has no adjoint, this checks one). */
 /* One particle per column, one slow and one fast variable (d = 1), drift     */

@@ -16,6 +16,7 @@ Parity pins live in ``tests/test_oracle_*.py``; every function below is pinned
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 import subprocess
 from dataclasses import dataclass
@@ -28,6 +29,7 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
 
 MODEL_OU, MODEL_DOUBLE_WELL, MODEL_DW_MULTI, MODEL_ADVECTION = 0, 1, 2, 3
+MODEL_CHEM, MODEL_CHEM_PRINTED = 4, 5
 
 
 def build(force: bool = False) -> str:
@@ -59,6 +61,8 @@ def lib():
         _lib.or_uniform.restype = d
         _lib.or_step_normals.argtypes = [u64, u32, u32, u32, u32, i32, vp]
         _lib.or_normals_block.argtypes = [u64, u32, u32, i64, u32, u32, i32, i32, vp]
+        _lib.or_fine_propagate_chem.argtypes = [i32, vp, d, d, u64, u32, vp, vp, i64, vp, i32, i32, i32, d]
+        _lib.or_chem_coefficients.argtypes = [i32, vp, d, d, vp]
         _lib.or_fine_propagate.argtypes = [i32, i32, d, d, d, d, u64, u32, vp, vp, i64,
                                            i32, i32, i32, d]
         _lib.or_fine_propagate_ids.argtypes = [i32, i32, d, d, d, d, u64, u32, vp, vp, i64, vp,
@@ -105,6 +109,11 @@ class Model:
     kind 3: no microscopic model; the coarse potential Fbar(x) = x/eps (the
             linear advection test of Section 6), diffusion 1/beta
     fast:   d_y G = y - x per component, E = 1; slow diffusion D = 1/beta.
+    kind 4: the chemically reacting system of Section 2.1.2 with rates
+            k0..k5 (`rates`), drifts read as the net reaction rates
+            (chemical Langevin form; see oracle.c); kind 5: the same with
+            the drifts of the potentials as printed.  fast_dim = 1; lam and
+            beta unused.
     """
     kind: int
     fast_dim: int = 1
@@ -112,6 +121,16 @@ class Model:
     beta: float = 1.0
     eps: float = 0.1
     tau_x: float = 1.0
+    rates: tuple = ()
+
+    @property
+    def chem(self) -> bool:
+        return self.kind in (MODEL_CHEM, MODEL_CHEM_PRINTED)
+
+    def rates_array(self) -> np.ndarray:
+        k = np.ascontiguousarray(self.rates, dtype=np.float64)
+        assert k.shape == (6,), "the chemical system needs six rates k0..k5"
+        return k
 
 
 @dataclass(frozen=True)
@@ -178,6 +197,17 @@ def fine_propagate(model: Model, seed: int, x: np.ndarray, y: np.ndarray, slice_
     y = np.array(y, dtype=np.float64, order="C", copy=True)
     n_slices, N = x.shape
     assert y.shape == (n_slices, model.fast_dim, N)
+    if model.chem:
+        assert model.fast_dim == 1
+        k = model.rates_array()
+        idp = None
+        if ids is not None:
+            ids = np.ascontiguousarray(ids, dtype=np.uint32)
+            assert ids.shape == (N,)
+            idp = _p(ids)
+        lib().or_fine_propagate_chem(model.kind - MODEL_CHEM, _p(k), model.eps, model.tau_x, seed, problem,
+                                     _p(x), _p(y), N, idp, slice_begin, n_slices, steps, dt)
+        return x, y
     if ids is None:
         lib().or_fine_propagate(model.kind, model.fast_dim, model.lam, model.beta, model.eps,
                                 model.tau_x, seed, problem, _p(x), _p(y), N, slice_begin,
@@ -340,19 +370,101 @@ def w1(grid: Grid, c1: np.ndarray, c2: np.ndarray) -> float:
 # form of Eq. FPz_rewritten, exact in time through the matrix exponential.
 # --------------------------------------------------------------------------
 
+# Equilibrium of the chemical system's fast variable (Section 2.2.3): the mean
+# ybar of phi(y) ~ exp(-int_0^y G'(s)/E(s) ds) / E(y) by the trapezoidal
+# rule.  The paper does not give the quadrature grid; the reading is
+# y_j = j * CHEM_DY, j = 0 .. CHEM_J (y in [0, 2000], far beyond both wells,
+# where phi has decayed by many orders), the inner integral by the
+# cumulative trapezoidal rule on the same grid.
+CHEM_DY = 0.5
+CHEM_J = 4000
+
+
+def _chem_coefficients(reading: int, k: np.ndarray, x: float, y: float):
+    out = np.empty(4)
+    lib().or_chem_coefficients(reading, _p(k), x, y, _p(out))
+    return out
+
+
+def chem_coefficients(model: Model, x: float, y: float):
+    """(d_x F, d_y G, D, E) of the chemical system at (x, y) (Section 2.1.2)."""
+    return _chem_coefficients(model.kind - MODEL_CHEM, model.rates_array(), x, y)
+
+
+def chem_ybar(model: Model) -> float:
+    return _chem_ybar(model.kind, tuple(float(v) for v in model.rates_array()))
+
+
+@functools.lru_cache(maxsize=64)
+def _chem_ybar(kind: int, rates: tuple) -> float:
+    k = np.ascontiguousarray(rates, dtype=np.float64)
+    reading = kind - MODEL_CHEM
+    y = np.array([j * CHEM_DY for j in range(CHEM_J + 1)])
+    ratio = np.empty(CHEM_J + 1)            # G'(y) / E(y)
+    log_e = np.empty(CHEM_J + 1)
+    for j in range(CHEM_J + 1):
+        _, dg, _, e = _chem_coefficients(reading, k, 0.0, y[j])
+        ratio[j] = dg / e
+        log_e[j] = np.log(e)
+    integral = 0.0                           # int_0^{y_j} G'/E, cumulative trapezoid
+    log_phi = np.empty(CHEM_J + 1)
+    for j in range(CHEM_J + 1):
+        if j:
+            integral += 0.5 * CHEM_DY * (ratio[j - 1] + ratio[j])
+        log_phi[j] = -integral - log_e[j]
+    top = max(log_phi)
+    num = den = 0.0
+    for j in range(CHEM_J + 1):              # trapezoid weights 1/2 at the ends (dy cancels)
+        wgt = 0.5 if j in (0, CHEM_J) else 1.0
+        phi = np.exp(log_phi[j] - top)
+        num += wgt * y[j] * phi
+        den += wgt * phi
+    return num / den
+
+
 def effective_potential(model: Model, x):
-    """Fbar(x) with Fbar(0) = 0, by averaging d_x F over phi(y; x) = N(x, 1)
-    (Eq. Fbar; the fast OU has E[y | x] = x in every component)."""
+    """Fbar(x) with Fbar(0) = 0, by averaging d_x F over phi(y; x) (Eq. Fbar).
+    The fast OU has E[y | x] = x in every component; the chemical system's
+    F is linear in y, so Fbar needs only ybar (Section 2.2.3)."""
     x = np.asarray(x, dtype=np.float64)
     if model.kind == MODEL_ADVECTION:     # given directly (Section 6, linear advection case)
         return x / model.eps
+    if model.chem:
+        k, yb = model.rates_array(), chem_ybar(model)
+        if model.kind == MODEL_CHEM:      # F = -k4 x y + k5 x^2 / 2 (the net rates' potential)
+            return -k[4] * x * yb + 0.5 * k[5] * x * x
+        return -k[4] * x * yb - 0.5 * k[5] * x * x      # as printed
     if model.kind == MODEL_OU:
         return 0.5 * (1.0 - model.lam) * x * x
     return 0.25 * x ** 4 - 0.5 * (1.0 - model.lam) * x * x
 
 
+def effective_diffusion(model: Model, x):
+    """Dbar(x) (Eq. Dbar): 1/beta, or (k4 ybar + k5 x)/2 for the chemical system."""
+    x = np.asarray(x, dtype=np.float64)
+    if model.chem:
+        k = model.rates_array()
+        return 0.5 * (k[4] * chem_ybar(model) + k[5] * x)
+    return np.full_like(x, 1.0 / model.beta)
+
+
 def log_rho_inf(model: Model, x):
-    """log rho_inf(x) = log(1/Dbar) - int_0^x Fbar'(s)/Dbar ds, Dbar = 1/beta (Eq. Dbar)."""
+    """log rho_inf(x) = log(1/Dbar(x)) - int_0^x Fbar'(s)/Dbar(s) ds (Eq. FPz_rewritten).
+
+    Constant Dbar: the integral is Fbar(x)/Dbar.  The chemical system, with
+    a = k4 ybar, Dbar(s) = (a + k5 s)/2: Fbar'(s) = k5 s - a (net rates)
+    gives int_0^x 2 (k5 s - a)/(a + k5 s) ds = 2x - (4a/k5) log(1 + k5 x/a);
+    Fbar'(s) = -(a + k5 s) (as printed) gives -2x."""
+    x = np.asarray(x, dtype=np.float64)
+    if model.chem:
+        k = model.rates_array()
+        a = k[4] * chem_ybar(model)
+        Dbar = 0.5 * (a + k[5] * x)
+        if model.kind == MODEL_CHEM:
+            integral = 2.0 * x - (4.0 * a / k[5]) * np.log1p(k[5] * x / a)
+        else:
+            integral = -2.0 * x
+        return np.log(1.0 / Dbar) - integral
     Dbar = 1.0 / model.beta
     return np.log(1.0 / Dbar) - effective_potential(model, x) / Dbar
 
@@ -361,7 +473,7 @@ def coarse_generator(model: Model, grid: Grid) -> np.ndarray:
     """A with d m/dt = A m for the cell masses m_c (zero flux at both ends).
 
     Flux at interior edge e between cells e-1 and e:
-      phi_e = Dbar rho_inf(x_e) / h_e * ( m_e / (h_{e+1/2} rho_inf(xi_e))
+      phi_e = Dbar(x_e) rho_inf(x_e) / h_e * ( m_e / (h_{e+1/2} rho_inf(xi_e))
                                        - m_{e-1} / (h_{e-1/2} rho_inf(xi_{e-1})) )
     with h_e the distance between the two centres; dm_c/dt = (phi_{c+1} - phi_c)/tau_x.
     """
@@ -369,11 +481,10 @@ def coarse_generator(model: Model, grid: Grid) -> np.ndarray:
     x = grid.edges()
     xi = 0.5 * (x[:-1] + x[1:])
     width = x[1:] - x[:-1]
-    Dbar = 1.0 / model.beta
     A = np.zeros((I, I), dtype=np.float64)
     for e in range(1, I):
         h_e = xi[e] - xi[e - 1]
-        coef = Dbar / h_e
+        coef = float(effective_diffusion(model, x[e])) / h_e
         r_right = np.exp(log_rho_inf(model, x[e]) - log_rho_inf(model, xi[e])) / width[e]
         r_left = np.exp(log_rho_inf(model, x[e]) - log_rho_inf(model, xi[e - 1])) / width[e - 1]
         # phi_e = coef * (r_right * m_e - r_left * m_{e-1})

@@ -710,12 +710,12 @@ static pr_status launch_f32_multi(int D, const FineArgs& a, FineSmemOffsets so, 
                                   size_t smem, int n_slices, cudaStream_t st)
 {
     switch (D) {
-    case 1: return launch_f32_dn<PR_MODEL_DW_MULTI, 1>(a, so, flags, smem, n_slices, st);
-    case 2: return launch_f32_dn<PR_MODEL_DW_MULTI, 2>(a, so, flags, smem, n_slices, st);
-    case 3: return launch_f32_dn<PR_MODEL_DW_MULTI, 3>(a, so, flags, smem, n_slices, st);
-    case 4: return launch_f32_dn<PR_MODEL_DW_MULTI, 4>(a, so, flags, smem, n_slices, st);
-    case 8: return launch_f32_dn<PR_MODEL_DW_MULTI, 8>(a, so, flags, smem, n_slices, st);
-    case 16: return launch_f32_dn<PR_MODEL_DW_MULTI, 16>(a, so, flags, smem, n_slices, st);
+#define PR_DN_CASE(d) \
+    case d: return launch_f32_dn<PR_MODEL_DW_MULTI, d>(a, so, flags, smem, n_slices, st);
+    PR_DN_CASE(1) PR_DN_CASE(2) PR_DN_CASE(3) PR_DN_CASE(4) PR_DN_CASE(5) PR_DN_CASE(6) PR_DN_CASE(7)
+    PR_DN_CASE(8) PR_DN_CASE(9) PR_DN_CASE(10) PR_DN_CASE(11) PR_DN_CASE(12) PR_DN_CASE(13) PR_DN_CASE(14)
+    PR_DN_CASE(15) PR_DN_CASE(16)
+#undef PR_DN_CASE
     default: return PR_ERR_UNSUPPORTED;
     }
 }

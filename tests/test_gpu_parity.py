@@ -43,7 +43,13 @@ def _models(L, orc):
         (L.Model(L.PR_MODEL_DW_MULTI, 1, 0.5, 3.0, 1e-2), orc.Model(2, 1, 0.5, 3.0, 1e-2)),
         (L.Model(L.PR_MODEL_DW_MULTI, 2, 0.4, 2.0, 2e-2), orc.Model(2, 2, 0.4, 2.0, 2e-2)),
         (L.Model(L.PR_MODEL_DW_MULTI, 8, 0.5, 3.0, 1e-2), orc.Model(2, 8, 0.5, 3.0, 1e-2)),
+        # 1 + d = 5 and 6 normals per step: one and two shared tail blocks per four steps
+        (L.Model(L.PR_MODEL_DW_MULTI, 4, 0.5, 3.0, 1e-2), orc.Model(2, 4, 0.5, 3.0, 1e-2)),
+        (L.Model(L.PR_MODEL_DW_MULTI, 5, 0.5, 3.0, 1e-2), orc.Model(2, 5, 0.5, 3.0, 1e-2)),
     ]
+
+
+N_MODELS = 9
 
 
 # ---------------------------------------------------------------------------
@@ -74,7 +80,7 @@ def _initial(n, d, seed=0):
     return x, y
 
 
-@pytest.mark.parametrize("mi", range(7))
+@pytest.mark.parametrize("mi", range(N_MODELS))
 @pytest.mark.parametrize("n,steps", [(1000, 125), (4096, 7), (1, 3), (257, 0)])
 def test_fine_f64_matches_oracle(L, orc, mi, n, steps):
     gm, om = _models(L, orc)[mi]
@@ -95,7 +101,7 @@ def test_fine_f64_matches_oracle(L, orc, mi, n, steps):
     assert np.max(np.abs(gx.cpu().numpy() - ox)) < 1e-10
 
 
-@pytest.mark.parametrize("mi", range(7))
+@pytest.mark.parametrize("mi", range(N_MODELS))
 @pytest.mark.parametrize("ppt", [1, 2, 4])
 def test_fine_f32_matches_oracle(L, orc, mi, ppt):
     gm, om = _models(L, orc)[mi]
