@@ -63,12 +63,29 @@ typedef enum { PR_F32 = 0, PR_F64 = 1 } pr_precision;
  *   PR_MODEL_DW_MULTI    d_x F = x^3 - x + lambda*mean(y) (fast_dim 1..16)
  *   PR_MODEL_ADVECTION   no microscopic model (pr_coarse_create only): the coarse
  *                        potential Fbar(x) = x/eps, diffusion 1/beta -- the linear
- *                        advection case of Section 6 */
+ *                        advection case of Section 6
+ * and the chemically reacting system of Section 2.1.2 (fast_dim = 1, rates
+ * k0..k5 in pr_model.rate; lambda and beta unused), with
+ *   D = (k4 y + k5 x)/2,  E = (k0 + k1 y + k2 y(y-1) + k3 y(y-1)(y-2))/2
+ * (half the total propensities of the reactions 0 -> Y, Y -> 0, 2Y -> 3Y,
+ * 3Y -> 2Y, Y -> Y + X, X -> 0), the square roots taking max(2D, 0) and
+ * max(2E, 0), and the drifts
+ *   PR_MODEL_CHEM         the net rates of those reactions (chemical Langevin
+ *                         form): -d_x F = k4 y - k5 x,
+ *                         -d_y G = k0 - k1 y + k2 y(y-1) - k3 y(y-1)(y-2)
+ *   PR_MODEL_CHEM_PRINTED the derivatives of the potentials as printed
+ *                         (Eqs. F_Bruna, G_Bruna): d_x F = -k4 y - k5 x,
+ *                         d_y G = -k0 - k1 y + k2 y(y-1) - k3 y(y-1)(y-2).
+ * Its coarse model (Section 2.2.3) averages over the fast equilibrium
+ * phi(y) ~ exp(-int_0^y G'/E) / E through its mean ybar, taken by the
+ * trapezoidal rule on y = 0, 1/2, ..., 2000 (pr_coarse_create). */
 typedef enum {
     PR_MODEL_OU = 0,
     PR_MODEL_DOUBLE_WELL = 1,
     PR_MODEL_DW_MULTI = 2,
-    PR_MODEL_ADVECTION = 3
+    PR_MODEL_ADVECTION = 3,
+    PR_MODEL_CHEM = 4,
+    PR_MODEL_CHEM_PRINTED = 5
 } pr_model_kind;
 
 /* Iterators of Section 4: quantile (4.4), additive (4.1), multiplicative
@@ -94,6 +111,7 @@ typedef struct {
     double beta;        /* inverse temperature of the slow variable, D = 1/beta */
     double eps;         /* fast time scale */
     double tau_x;       /* slow time scale */
+    double rate[6];     /* k0..k5 of the chemical system (other kinds ignore them) */
 } pr_model;
 
 typedef struct {

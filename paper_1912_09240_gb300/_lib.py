@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpr.so")
 PR_OK, PR_ERR_INVALID_ARG, PR_ERR_CUDA, PR_ERR_TIMEOUT, PR_ERR_UNSUPPORTED, PR_ERR_NOMEM, PR_ERR_NUMERIC = range(7)
 PR_F32, PR_F64 = 0, 1
 PR_MODEL_OU, PR_MODEL_DOUBLE_WELL, PR_MODEL_DW_MULTI, PR_MODEL_ADVECTION = 0, 1, 2, 3
+PR_MODEL_CHEM, PR_MODEL_CHEM_PRINTED = 4, 5
 PR_ITER_QUANTILE, PR_ITER_ADD, PR_ITER_MULT, PR_ITER_ROT, PR_ITER_NONE = 0, 1, 2, 3, 4
 PR_QMODE_TWO_SIDED, PR_QMODE_MIDPOINT = 0, 1
 PR_RESAMPLE_STRATIFIED, PR_RESAMPLE_DETERMINISTIC = 0, 1
@@ -43,7 +44,8 @@ class PrError(RuntimeError):
 
 class _Model(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("fast_dim", ctypes.c_int32), ("lambda_", ctypes.c_double),
-                ("beta", ctypes.c_double), ("eps", ctypes.c_double), ("tau_x", ctypes.c_double)]
+                ("beta", ctypes.c_double), ("eps", ctypes.c_double), ("tau_x", ctypes.c_double),
+                ("rate", ctypes.c_double * 6)]
 
 
 class _Grid(ctypes.Structure):
@@ -67,9 +69,11 @@ class Model:
     beta: float = 1.0
     eps: float = 0.1
     tau_x: float = 1.0
+    rates: tuple = ()     # k0..k5 (chemical system)
 
     def c(self) -> _Model:
-        return _Model(self.kind, self.fast_dim, self.lam, self.beta, self.eps, self.tau_x)
+        r = tuple(float(v) for v in self.rates) + (0.0,) * (6 - len(self.rates))
+        return _Model(self.kind, self.fast_dim, self.lam, self.beta, self.eps, self.tau_x, (ctypes.c_double * 6)(*r))
 
 
 @dataclass(frozen=True)

@@ -20,6 +20,11 @@
 
 namespace pr {
 
+struct ChemRates {
+    double k[6];
+    bool printed;
+};
+
 struct CoarseHandle {
     GridDev g;
     double* P;   // row-major I x I
@@ -30,20 +35,75 @@ struct CoarseHandle {
 // Kernels
 // ---------------------------------------------------------------------------
 
+// Mean ybar of the chemical system's fast equilibrium (Section 2.2.3),
+// phi(y) ~ exp(-int_0^y G'(s)/E(s) ds) / E(y), by the trapezoidal rule on
+// y_j = j/2, j = 0..4000 (the inner integral cumulatively on the same grid).
+// One thread walks the grid twice in order (the maximum of log phi, then the
+// weighted sums); set-up work of a few milliseconds.
+constexpr double kChemDy = 0.5;
+constexpr int kChemJ = 4000;
+
+__device__ __forceinline__ void chem_fast_terms(const double* k, bool printed, double y, double& ratio,
+                                                double& log_e)
+{
+    const double y1 = y * (y - 1.0), y2 = y1 * (y - 2.0);
+    const double net = k[0] - k[1] * y + k[2] * y1 - k[3] * y2;              // -G' (net rates)
+    const double dg = printed ? -k[0] - k[1] * y + k[2] * y1 - k[3] * y2 : -net;
+    const double e = 0.5 * (k[0] + k[1] * y + k[2] * y1 + k[3] * y2);
+    ratio = dg / e;
+    log_e = log(e);
+}
+
+__global__ void chem_ybar_kernel(ChemRates r, double* __restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double top = -INFINITY;
+    for (int pass = 0; pass < 2; ++pass) {
+        double integral = 0.0, prev = 0.0, num = 0.0, den = 0.0;
+        for (int j = 0; j <= kChemJ; ++j) {
+            const double y = j * kChemDy;
+            double ratio, log_e;
+            chem_fast_terms(r.k, r.printed, y, ratio, log_e);
+            if (j) integral += 0.5 * kChemDy * (prev + ratio);
+            prev = ratio;
+            const double log_phi = -integral - log_e;
+            if (pass == 0) {
+                top = fmax(top, log_phi);
+            } else {
+                const double w = (j == 0 || j == kChemJ) ? 0.5 : 1.0;
+                const double phi = exp(log_phi - top);
+                num += w * y * phi;
+                den += w * phi;
+            }
+        }
+        if (pass == 1) *out = num / den;
+    }
+}
+
 __global__ void assemble_generator_kernel(GridDev g, int kind, double lam, double beta, double eps, double tau_x,
+                                          double k4, double k5, const double* __restrict__ ybar_ptr,
                                           double slice_dt, double* __restrict__ A)
 {
     const int I = g.bins;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= I) return;
-    const double Dbar = 1.0 / beta;
-    // log rho_inf(x) = log(1/Dbar) - Fbar(x)/Dbar, Fbar the averaged potential
+    const bool chem = kind == PR_MODEL_CHEM || kind == PR_MODEL_CHEM_PRINTED;
+    const double a = chem ? k4 * *ybar_ptr : 0.0;   // k4 ybar
+    // Dbar(x): 1/beta, or (k4 ybar + k5 x)/2 for the chemical system
+    auto dbar = [&](double x) { return chem ? 0.5 * (a + k5 * x) : 1.0 / beta; };
+    // log rho_inf(x) = log(1/Dbar(x)) - int_0^x Fbar'/Dbar: Fbar(x)/Dbar for a
+    // constant Dbar; for the chemical system 2x - (4a/k5) log(1 + k5 x/a)
+    // (Fbar' = k5 x - a, net rates) or -2x (Fbar' = -(a + k5 x), as printed)
     auto fbar = [&](double x) {
         if (kind == PR_MODEL_ADVECTION) return x / eps;   // given directly (linear advection case)
         return kind == PR_MODEL_OU ? 0.5 * (1.0 - lam) * x * x
                                    : 0.25 * x * x * x * x - 0.5 * (1.0 - lam) * x * x;
     };
-    auto log_rho_inf = [&](double x) { return log(1.0 / Dbar) - fbar(x) / Dbar; };
+    auto log_rho_inf = [&](double x) {
+        if (!chem) return log(1.0 / dbar(x)) - fbar(x) / dbar(x);
+        const double integral = kind == PR_MODEL_CHEM ? 2.0 * x - (4.0 * a / k5) * log1p(k5 * x / a) : -2.0 * x;
+        return log(1.0 / dbar(x)) - integral;
+    };
     auto centre = [&](int k) { return 0.5 * (edge(g, k) + edge(g, k + 1)); };
     auto width = [&](int k) { return edge(g, k + 1) - edge(g, k); };
     double* row = A + (size_t)c * I;
@@ -53,7 +113,7 @@ __global__ void assemble_generator_kernel(GridDev g, int kind, double lam, doubl
     if (c >= 1) {
         const int e = c;
         const double xe = edge(g, e);
-        const double coef = Dbar / (centre(e) - centre(e - 1));
+        const double coef = dbar(xe) / (centre(e) - centre(e - 1));
         const double rr = exp(log_rho_inf(xe) - log_rho_inf(centre(e))) / width(e);
         const double rl = exp(log_rho_inf(xe) - log_rho_inf(centre(e - 1))) / width(e - 1);
         diag -= coef * rr / tau_x;
@@ -63,7 +123,7 @@ __global__ void assemble_generator_kernel(GridDev g, int kind, double lam, doubl
     if (c + 1 <= I - 1) {
         const int e = c + 1;
         const double xe = edge(g, e);
-        const double coef = Dbar / (centre(e) - centre(e - 1));
+        const double coef = dbar(xe) / (centre(e) - centre(e - 1));
         const double rr = exp(log_rho_inf(xe) - log_rho_inf(centre(e))) / width(e);
         const double rl = exp(log_rho_inf(xe) - log_rho_inf(centre(e - 1))) / width(e - 1);
         row[c + 1] += coef * rr / tau_x;
@@ -252,9 +312,19 @@ extern "C" pr_status pr_coarse_create(const pr_model* model, const pr_grid* grid
                                       void** handle, void* stream)
 {
     if (!model || !grid_ok(grid) || !handle || !(slice_dt > 0.0) || !std::isfinite(slice_dt)) return PR_ERR_INVALID_ARG;
-    if (model->kind < PR_MODEL_OU || model->kind > PR_MODEL_ADVECTION) return PR_ERR_INVALID_ARG;
-    if (!(model->beta > 0.0) || !(model->tau_x > 0.0) || !std::isfinite(model->lambda)) return PR_ERR_INVALID_ARG;
-    if (model->kind == PR_MODEL_ADVECTION && !(model->eps > 0.0)) return PR_ERR_INVALID_ARG;
+    const bool chem = model->kind == PR_MODEL_CHEM || model->kind == PR_MODEL_CHEM_PRINTED;
+    if (chem) {
+        // rates finite and non-negative, k4 and k5 positive (Dbar > 0 needs a
+        // positive ybar and x_lo >= 0)
+        if (!(model->tau_x > 0.0) || !(grid->x_lo >= 0.0)) return PR_ERR_INVALID_ARG;
+        for (int i = 0; i < 6; ++i)
+            if (!std::isfinite(model->rate[i]) || model->rate[i] < 0.0) return PR_ERR_INVALID_ARG;
+        if (!(model->rate[4] > 0.0) || !(model->rate[5] > 0.0) || !(model->rate[0] > 0.0)) return PR_ERR_INVALID_ARG;
+    } else {
+        if (model->kind < PR_MODEL_OU || model->kind > PR_MODEL_ADVECTION) return PR_ERR_INVALID_ARG;
+        if (!(model->beta > 0.0) || !(model->tau_x > 0.0) || !std::isfinite(model->lambda)) return PR_ERR_INVALID_ARG;
+        if (model->kind == PR_MODEL_ADVECTION && !(model->eps > 0.0)) return PR_ERR_INVALID_ARG;
+    }
     *handle = nullptr;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int I = grid->bins;
@@ -267,13 +337,30 @@ extern "C" pr_status pr_coarse_create(const pr_model* model, const pr_grid* grid
         if (nrm) cudaFree(nrm);
     };
     if (cudaMalloc(&B, nn * 8) != cudaSuccess || cudaMalloc(&X, nn * 8) != cudaSuccess ||
-        cudaMalloc(&Y, nn * 8) != cudaSuccess || cudaMalloc(&nrm, 8) != cudaSuccess) {
+        cudaMalloc(&Y, nn * 8) != cudaSuccess || cudaMalloc(&nrm, 16) != cudaSuccess) {
         release();
         return PR_ERR_NOMEM;
     }
     const GridDev g = make_grid(*grid);
+    if (chem) {   // ybar (nrm[1]) first; it must be positive and finite
+        ChemRates r;
+        for (int i = 0; i < 6; ++i) r.k[i] = model->rate[i];
+        r.printed = model->kind == PR_MODEL_CHEM_PRINTED;
+        chem_ybar_kernel<<<1, 32, 0, st>>>(r, nrm + 1);
+        double ybar = 0.0;
+        if (cudaMemcpyAsync(&ybar, nrm + 1, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            release();
+            return PR_ERR_CUDA;
+        }
+        if (!std::isfinite(ybar) || !(ybar > 0.0)) {
+            release();
+            return PR_ERR_NUMERIC;
+        }
+    }
     assemble_generator_kernel<<<(I + 127) / 128, 128, 0, st>>>(g, model->kind, model->lambda, model->beta,
-                                                               model->eps, model->tau_x, slice_dt, B);
+                                                               model->eps, model->tau_x, model->rate[4],
+                                                               model->rate[5], nrm + 1, slice_dt, B);
     norm1_kernel<<<1, 256, 0, st>>>(B, I, nrm);
     double norm = 0.0;
     if (cudaMemcpyAsync(&norm, nrm, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

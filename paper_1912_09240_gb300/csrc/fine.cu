@@ -75,6 +75,8 @@ struct FineArgs {
     double sy;         // sqrt(2 E / eps) sqrt(dt), E = 1
     float lam_f, drift_dt_f, relax_f, sx_f, sy_f;   // the same, rounded once on the host
     float sxk_f, syk_f;                             // sx, sy times sqrt(2 ln 2)
+    ChemConsts<float> chem_f;                       // the chemical system (kinds CHEM, CHEM_PRINTED)
+    ChemConsts<double> chem_d;
     int tiles_per_cta;  // binary32 d = 1 kernel: consecutive tiles handled by one CTA
     // random numbers
     uint32_t k0, k1, ctr_hi;   // key words; (problem_id << 8)
@@ -176,7 +178,7 @@ fine_f32_d1_kernel(FineArgs a, FineSmemOffsets so, int flags)
     const float* __restrict__ yin = static_cast<const float*>(a.y_in) + (int64_t)s * a.in_slice_stride;
     float* __restrict__ xout = static_cast<float*>(a.x_out) + (int64_t)s * N;
     float* __restrict__ yout = static_cast<float*>(a.y_out) + (int64_t)s * N;
-    D1Consts cst{a.lam_f, a.drift_dt_f, a.relax_f, a.sxk_f, a.syk_f, a.k0, a.k1, a.ctr_hi};
+    D1Consts cst{a.lam_f, a.drift_dt_f, a.relax_f, a.sxk_f, a.syk_f, a.k0, a.k1, a.ctr_hi, a.chem_f};
     D1Smem sm{thr, hist_s, hist_e, &ms, bf, do_match, do_hs, do_he};
     const int64_t span = (int64_t)a.tiles_per_cta * blockDim.x * PPT;
     const int64_t p_begin = (int64_t)blockIdx.x * span;
@@ -419,6 +421,10 @@ fine_f64_kernel(FineArgs a, FineSmemOffsets so, int flags)
                 z[4 * F + i] = (idx & 1) ? zb : za;
             }
         }
+        if (KIND == PR_MODEL_CHEM) {   // sx = sy = 1: the amplitudes depend on the state
+            em_step_chem_f64(x, y[0], a.sx * z[0], a.sy * z[1], a.chem_d);
+            continue;
+        }
         double ysum = 0.0;
         for (int j = 0; j < D; ++j) ysum += y[j];
         const double ym = (KIND == PR_MODEL_DW_MULTI) ? ysum / (double)D : y[0];
@@ -637,9 +643,17 @@ __global__ void rng_words_kernel(const uint4* __restrict__ ctr, int64_t n, uint3
 // host side
 // ---------------------------------------------------------------------------
 
+static bool is_chem(int kind) { return kind == PR_MODEL_CHEM || kind == PR_MODEL_CHEM_PRINTED; }
+
 static bool model_ok(const pr_model* m)
 {
     if (!m) return false;
+    if (is_chem(m->kind)) {   // rates finite and non-negative, one fast variable
+        if (m->fast_dim != 1 || !(m->eps > 0.0) || !(m->tau_x > 0.0)) return false;
+        for (int i = 0; i < 6; ++i)
+            if (!isfinite(m->rate[i]) || m->rate[i] < 0.0) return false;
+        return true;
+    }
     if (m->kind < PR_MODEL_OU || m->kind > PR_MODEL_DW_MULTI) return false;
     if (m->fast_dim < 1 || m->fast_dim > PR_MAX_FAST_DIM) return false;
     if (m->kind != PR_MODEL_DW_MULTI && m->fast_dim != 1) return false;
@@ -787,6 +801,16 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
     a.sy_f = (float)a.sy;
     a.sxk_f = (float)(a.sx * 1.1774100225154746910);
     a.syk_f = (float)(a.sy * 1.1774100225154746910);
+    if (is_chem(model->kind)) {
+        // state-dependent amplitudes: dt is folded into the variance
+        // polynomials, so the binary64 normals enter unscaled and the
+        // binary32 ones scaled by sqrt(2 ln 2) alone
+        const bool printed = model->kind == PR_MODEL_CHEM_PRINTED;
+        a.chem_d = make_chem_consts<double>(model->rate, printed, dt, model->tau_x, model->eps);
+        a.chem_f = make_chem_consts<float>(model->rate, printed, dt, model->tau_x, model->eps);
+        a.sx = a.sy = 1.0;
+        a.sxk_f = a.syk_f = 1.1774100225154746910f;
+    }
     a.tiles_per_cta = 1;
     a.k0 = (uint32_t)(rng->seed & 0xFFFFFFFFull);
     a.k1 = (uint32_t)(rng->seed >> 32);
@@ -814,6 +838,12 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
     if (precision == PR_F32) {
         if (model->kind == PR_MODEL_DW_MULTI && D > 1) {
             rc = launch_f32_multi(D, a, so, flags, L.total, n_slices, st);
+        } else if (is_chem(model->kind)) {
+            switch (g_ppt) {
+            case 2: rc = launch_f32_d1<PR_MODEL_CHEM, 2>(a, so, flags, L.total, n_slices, st); break;
+            case 4: rc = launch_f32_d1<PR_MODEL_CHEM, 4>(a, so, flags, L.total, n_slices, st); break;
+            default: rc = launch_f32_d1<PR_MODEL_CHEM, 1>(a, so, flags, L.total, n_slices, st);
+            }
         } else {
             // (the multi-component family with one component is the double well)
             const bool ou = model->kind == PR_MODEL_OU;
@@ -843,6 +873,13 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
         }
         case PR_MODEL_DOUBLE_WELL: {
             auto k = fine_f64_kernel<PR_MODEL_DOUBLE_WELL>;
+            PR_TRY_CUDA(set_smem(k, L.total));
+            k<<<g, threads, L.total, st>>>(a, so, flags);
+            break;
+        }
+        case PR_MODEL_CHEM:
+        case PR_MODEL_CHEM_PRINTED: {
+            auto k = fine_f64_kernel<PR_MODEL_CHEM>;
             PR_TRY_CUDA(set_smem(k, L.total));
             k<<<g, threads, L.total, st>>>(a, so, flags);
             break;

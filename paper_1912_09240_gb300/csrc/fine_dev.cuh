@@ -12,7 +12,18 @@ namespace pr {
 struct D1Consts {
     float lam, ddt, rel, sxk, syk;   // EM constants; sxk, syk include sqrt(2 ln 2)
     uint32_t k0, k1, chi;            // Philox key words and (problem_id << 8)
+    ChemConsts<float> chem;          // the chemical system's constants (KIND == PR_MODEL_CHEM)
 };
+
+// One step of the d = 1 families from a Box-Muller pair (q, cos, sin).
+template <int KIND>
+__device__ __forceinline__ void em_step_d1(float& x, float& y, float q, float c, float s, const D1Consts& k)
+{
+    if (KIND == PR_MODEL_CHEM)
+        em_step_chem_f32(x, y, q * k.sxk, c, q * k.syk, s, k.chem);
+    else
+        em_step_f32<KIND>(x, y, q * k.sxk, c, q * k.syk, s, k.lam, k.ddt, k.rel);
+}
 
 struct D1Smem {
     const float* thr;                // edge thresholds [bins+1]
@@ -31,7 +42,6 @@ __device__ __forceinline__ void fine_d1_range(const float* __restrict__ xin, con
                                               int64_t p_begin, int64_t p_end, uint32_t slice, int steps,
                                               const D1Consts& c, const D1Smem& sm)
 {
-    const float lam = c.lam, ddt = c.ddt, rel = c.rel, sxk = c.sxk, syk = c.syk;
     const uint32_t k0 = c.k0, k1 = c.k1, chi = c.chi;
     const int pairs = steps >> 1;
     const int64_t tile = (int64_t)blockDim.x * PPT;
@@ -66,8 +76,8 @@ __device__ __forceinline__ void fine_d1_range(const float* __restrict__ xin, con
                 box_muller_qcs(w.x, w.y, q0, c0, s0);
                 box_muller_qcs(w.z, w.w, q1, c1, s1);
                 // steps 2 mp and 2 mp + 1: sx z0 = (q sxk) cos, sy z1 = (q syk) sin
-                em_step_f32<KIND>(x[k], y[k], q0 * sxk, c0, q0 * syk, s0, lam, ddt, rel);
-                em_step_f32<KIND>(x[k], y[k], q1 * sxk, c1, q1 * syk, s1, lam, ddt, rel);
+                em_step_d1<KIND>(x[k], y[k], q0, c0, s0, c);
+                em_step_d1<KIND>(x[k], y[k], q1, c1, s1, c);
             }
         }
         if (steps & 1) {
@@ -76,7 +86,7 @@ __device__ __forceinline__ void fine_d1_range(const float* __restrict__ xin, con
                 const uint4 w = philox4x32_10(make_uint4((uint32_t)pairs, pid[k], slice, chi), k0, k1);
                 float q0, c0, s0;
                 box_muller_qcs(w.x, w.y, q0, c0, s0);
-                em_step_f32<KIND>(x[k], y[k], q0 * sxk, c0, q0 * syk, s0, lam, ddt, rel);
+                em_step_d1<KIND>(x[k], y[k], q0, c0, s0, c);
             }
         }
 #pragma unroll

@@ -152,6 +152,68 @@ __device__ __forceinline__ void em_step_f32(float& x, float& y, float ax, float 
     y = yn;
 }
 
+// The chemically reacting system (Section 2.1.2, Eqs. EMx/EMy), both
+// readings of its drifts, with every constant folded on the host:
+//   x' = x + a4 y + a5 x + sqrt(max(a4 y + v5 x, 0)) zx
+//   y' = y + ((f3 y + f2) y + f1) y + f0 + sqrt(max(((e3 y + e2) y + e1) y + e0, 0)) zy
+// a4 = k4 dt/tau_x, v5 = k5 dt/tau_x, a5 = -v5 (net reaction rates) or +v5
+// (printed potential); f_i the coefficients of the cubic -d_y G and e_i those
+// of 2E = k0 + k1 y + k2 y(y-1) + k3 y(y-1)(y-2), both times dt/eps.  The
+// noise is given as products zx = ax * cx, zy = ay * cy (ax, ay = q sqrt(2 ln 2)).
+template <typename T>
+struct ChemConsts {
+    T a4, a5, v5, f0, f1, f2, f3, e0, e1, e2, e3;
+};
+
+__device__ __forceinline__ void em_step_chem_f32(float& x, float& y, float ax, float cx, float ay, float cy,
+                                                 const ChemConsts<float>& k)
+{
+    const float vx = fmaxf(fmaf(k.a4, y, k.v5 * x), 0.0f);
+    const float vy = fmaxf(fmaf(fmaf(fmaf(k.e3, y, k.e2), y, k.e1), y, k.e0), 0.0f);
+    const float fy = fmaf(fmaf(fmaf(k.f3, y, k.f2), y, k.f1), y, k.f0);
+    const float xn = fmaf(ax * sqrt_approx(vx), cx, fmaf(k.a4, y, fmaf(k.a5, x, x)));
+    const float yn = fmaf(ay * sqrt_approx(vy), cy, y + fy);
+    x = xn;
+    y = yn;
+}
+
+__device__ __forceinline__ void em_step_chem_f64(double& x, double& y, double zx, double zy,
+                                                 const ChemConsts<double>& k)
+{
+    const double vx = fmax(k.a4 * y + k.v5 * x, 0.0);
+    const double vy = fmax(((k.e3 * y + k.e2) * y + k.e1) * y + k.e0, 0.0);
+    const double fy = ((k.f3 * y + k.f2) * y + k.f1) * y + k.f0;
+    const double xn = x + (k.a4 * y + k.a5 * x) + sqrt(vx) * zx;
+    const double yn = y + fy + sqrt(vy) * zy;
+    x = xn;
+    y = yn;
+}
+
+// Host-side folding of the rates (k[0..5]) into ChemConsts; `printed` selects
+// the drifts of the printed potentials.
+template <typename T>
+inline ChemConsts<T> make_chem_consts(const double* k, bool printed, double dt, double tau_x, double eps)
+{
+    const double ax = dt / tau_x, ay = dt / eps;
+    // -d_y G (net rates) = k0 - (k1 + k2 + 2 k3) y + (k2 + 3 k3) y^2 - k3 y^3;
+    // the printed reading flips the sign of the terms in y, y^2, y^3
+    const double sg = printed ? -1.0 : 1.0;
+    ChemConsts<T> c;
+    c.a4 = (T)(k[4] * ax);
+    c.v5 = (T)(k[5] * ax);
+    c.a5 = (T)((printed ? 1.0 : -1.0) * k[5] * ax);
+    c.f0 = (T)(k[0] * ay);
+    c.f1 = (T)(sg * -(k[1] + k[2] + 2.0 * k[3]) * ay);
+    c.f2 = (T)(sg * (k[2] + 3.0 * k[3]) * ay);
+    c.f3 = (T)(sg * -k[3] * ay);
+    // 2E = k0 + (k1 - k2 + 2 k3) y + (k2 - 3 k3) y^2 + k3 y^3
+    c.e0 = (T)(k[0] * ay);
+    c.e1 = (T)((k[1] - k[2] + 2.0 * k[3]) * ay);
+    c.e2 = (T)((k[2] - 3.0 * k[3]) * ay);
+    c.e3 = (T)(k[3] * ay);
+    return c;
+}
+
 __device__ __forceinline__ void box_muller_f64(uint32_t w0, uint32_t w1, double& z0, double& z1)
 {
     const double u0 = uniform_f64(w0);

@@ -1,0 +1,168 @@
+"""The chemically reacting system (Section 2.1.2; coarse model of Section
+2.2.3) on the GPU through the C ABI, against the FP64 oracle:
+
+* fine propagator, one slice from identical inputs, both readings of the
+  drifts: binary64 |dx| <= 1e-5 per particle, binary32 <= 2e-3 max(|x|, 1);
+* the coarse propagator (ybar, Dbar at the edges, rho_inf, the matrix
+  exponential) within 1e-12 of the oracle's P;
+* the exactness theorem on the GPU itself, bit for bit;
+* whole parareal runs of the paper's workload geometry (20 slices of 2000
+  steps, 600 cells on [0, 600]) at reduced particle counts: binary64 within
+  W1 1e-4 of the oracle, binary32 within the tolerance stated in the test."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1912_09240_gb300 import build as b
+    b.build()
+    from paper_1912_09240_gb300 import _lib
+    return _lib
+
+
+def _models(L, orc, kind, rates=None, eps=2.5e-2, tau_x=25.0):
+    # each reading with the rates that keep its fast variable bounded (the
+    # printed drifts with the workload's k3 send y to infinity)
+    if rates is None:
+        rates = workloads.CHEM_RATES if kind == 4 else workloads.CHEM_RATES_PRINTED
+    return (L.Model(kind, 1, 0.0, 1.0, eps, tau_x, tuple(rates)),
+            orc.Model(kind, 1, eps=eps, tau_x=tau_x, rates=tuple(rates)))
+
+
+def _initial(n, n_slices, seed=0):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(20.0, 500.0, (n_slices, n))
+    y = rng.uniform(20.0, 480.0, (n_slices, 1, n))
+    return x, y
+
+
+@pytest.mark.parametrize("kind", [4, 5])
+@pytest.mark.parametrize("n,steps", [(1000, 125), (4096, 7), (1, 3), (257, 0)])
+def test_fine_f64_matches_oracle(L, orc, kind, n, steps):
+    gm, om = _models(L, orc, kind)
+    x0, y0 = _initial(n, 3)
+    gx, gy = torch.tensor(x0, device="cuda"), torch.tensor(y0, device="cuda")
+    L.pr_fine_propagate(gm, L.PR_F64, L.Rng(7, 3), gx, gy, False, gx, gy, n, 5, 3, steps, 1e-3)
+    torch.cuda.synchronize()
+    ox, oy = orc.fine_propagate(om, 7, x0, y0, 5, steps, 1e-3, problem=3)
+    assert np.all(np.isfinite(ox)) and np.all(np.isfinite(oy))
+    assert np.max(np.abs(gx.cpu().numpy() - ox)) <= 1e-5
+    assert np.max(np.abs(gy.cpu().numpy() - oy)) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", [4, 5])
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+def test_fine_f32_matches_oracle(L, orc, kind, ppt):
+    gm, om = _models(L, orc, kind)
+    n, steps = 3000, 125
+    x0, y0 = _initial(n, 2, seed=1)
+    x0, y0 = x0.astype(np.float32), y0.astype(np.float32)
+    gx, gy = torch.tensor(x0, device="cuda"), torch.tensor(y0, device="cuda")
+    ox_, oy_ = gx.clone(), gy.clone()
+    L.pr_set_particles_per_thread(ppt)
+    try:
+        L.pr_fine_propagate(gm, L.PR_F32, L.Rng(0), gx, gy, False, ox_, oy_, n, 11, 2, steps, 1e-3)
+        torch.cuda.synchronize()
+    finally:
+        L.pr_set_particles_per_thread(4)
+    ox, oy = orc.fine_propagate(om, 0, x0.astype(np.float64), y0.astype(np.float64), 11, steps, 1e-3)
+    assert np.all(np.abs(ox_.cpu().numpy() - ox) <= 2e-3 * np.maximum(np.abs(ox), 1.0))
+    assert np.all(np.abs(oy_.cpu().numpy() - oy) <= 2e-3 * np.maximum(np.abs(oy), 1.0))
+
+
+@pytest.mark.parametrize("kind,rates", [(4, workloads.CHEM_RATES), (5, workloads.CHEM_RATES_PRINTED)])
+def test_coarse_propagator_matches_oracle(L, orc, kind, rates):
+    gm, om = _models(L, orc, kind, rates)
+    grid, og = L.Grid(600, 0.0, 600.0), orc.Grid(600, 0.0, 600.0)
+    h = L.pr_coarse_create(gm, grid, 2.0)
+    P = torch.empty(600, 600, dtype=torch.float64, device="cuda")
+    L.pr_coarse_matrix(h, P)
+    torch.cuda.synchronize()
+    L.pr_coarse_destroy(h)
+    ref = orc.coarse_propagator(om, og, 2.0)
+    np.testing.assert_allclose(P.cpu().numpy(), ref, rtol=0, atol=1e-12)
+
+
+def test_coarse_create_rejects_bad_rates(L):
+    grid = L.Grid(600, 0.0, 600.0)
+    for rates in [(60.0, 1.0, 4.8e-3, 6.66e-6, 0.0, 1.0), (60.0, -1.0, 4.8e-3, 6.66e-6, 0.833, 1.0),
+                  (60.0, 1.0, float("nan"), 6.66e-6, 0.833, 1.0)]:
+        with pytest.raises(L.PrError):
+            L.pr_coarse_create(L.Model(4, 1, 0.0, 1.0, 2.5e-2, 25.0, rates), grid, 2.0)
+    with pytest.raises(L.PrError):   # Dbar would be negative left of 0
+        L.pr_coarse_create(L.Model(4, 1, 0.0, 1.0, 2.5e-2, 25.0, workloads.CHEM_RATES), L.Grid(10, -5.0, 5.0), 2.0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_exactness_theorem_chem(L, prec):
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    w = workloads.CHEM.scaled(N=5000, K=5, T=0.5)
+    precision = L.PR_F64 if prec == "f64" else L.PR_F32
+    dt_ = torch.float64 if prec == "f64" else torch.float32
+    gm = L.Model(w.kind, 1, 0.0, 1.0, w.eps, w.tau_x, w.rates)
+    s = PararealSolver(gm, L.Grid(w.bins, w.lo, w.hi), w.N, w.K, w.steps, w.step_dt, precision=precision,
+                       rng=L.Rng(w.seed, 0))
+    x0, y0 = workloads.initial_ensemble(w)
+    s.set_initial(torch.tensor(x0, dtype=dt_, device="cuda"), torch.tensor(y0, dtype=dt_, device="cuda"))
+    xs, _, rs = s.serial_reference()
+    for k in range(1, w.K + 1):
+        s.iterate()
+        rho = s.rho.cpu().numpy()
+        for n in range(k + 1):
+            np.testing.assert_array_equal(rho[n], rs[n].cpu().numpy())
+        xa = s.xa.cpu().numpy()
+        for n in range(1, k + 1):
+            np.testing.assert_array_equal(xa[n - 1], xs[n].cpu().numpy())
+    s.close()
+
+
+def _whole_run(L, orc, w, precision, iters, chunk):
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    gm = L.Model(w.kind, 1, 0.0, 1.0, w.eps, w.tau_x, w.rates)
+    om = orc.Model(w.kind, 1, eps=w.eps, tau_x=w.tau_x, rates=w.rates)
+    og = orc.Grid(w.bins, w.lo, w.hi)
+    dt_ = torch.float64 if precision == L.PR_F64 else torch.float32
+    npd = np.float64 if precision == L.PR_F64 else np.float32
+    x0, y0 = workloads.initial_ensemble(w)
+    x0, y0 = x0.astype(npd), y0.astype(npd)
+    s = PararealSolver(gm, L.Grid(w.bins, w.lo, w.hi), w.N, w.K, w.steps, w.step_dt, precision=precision,
+                       rng=L.Rng(w.seed, 0), chunk=chunk)
+    s.set_initial(torch.tensor(x0, device="cuda"), torch.tensor(y0, device="cuda"))
+    rho = [s.rho.cpu().numpy().copy()]
+    for _ in range(iters):
+        s.iterate()
+        rho.append(s.rho.cpu().numpy().copy())
+    assert int(s.status.item()) == 0
+    s.close()
+    ref = orc.parareal(om, og, w.seed, x0.astype(np.float64), y0.astype(np.float64), w.K, w.steps, w.step_dt,
+                       iters=iters)
+    return np.array([[orc.w1(og, rho[k][n], ref.rho[k][n]) for n in range(w.K + 1)] for k in range(iters + 1)])
+
+
+def test_whole_run_f64_against_oracle(L, orc):
+    w = workloads.CHEM.scaled(N=4096)
+    assert w.K == 20 and w.steps == 2000 and w.bins == 600
+    w1 = _whole_run(L, orc, w, L.PR_F64, 2, 0)
+    print(f"chem f64: max W1 per iteration {w1.max(axis=1)}")
+    assert np.all(w1 <= 1e-4), w1.max(axis=1)
+
+
+def test_whole_run_f32_against_oracle(L, orc):
+    """Binary32 against the FP64 oracle on 2^14 particles, 3 pipelined
+    iterations.  The fast variable is bistable: a trajectory that passes near
+    the saddle can end in the other well under a rounding-level difference,
+    and then its x moves apart by up to k4 (410 - 105) dT / tau_x ~ 20.  The
+    restricted densities still agree as distributions; the tolerance is the
+    double-well workload's 1e-3 in bin widths of that grid (h = 6/512),
+    rescaled to this grid's h = 1: W1 <= 1e-3 * 512/6 = 0.085."""
+    w = workloads.CHEM.scaled(N=1 << 14)
+    w1 = _whole_run(L, orc, w, L.PR_F32, 3, 5)
+    print(f"chem f32: max W1 per iteration {w1.max(axis=1)}")
+    assert np.all(w1 <= 1e-3 * 512 / 6), w1.max(axis=1)
