@@ -437,75 +437,83 @@ def _advection_leg(L, dev, stream, iters=4):
     return out
 
 
-def _studies_leg(L, dev, stream, rank, n=1 << 18, iters=12):
-    """The convergence studies of Section 6 (varying the time-scale separation;
-    scaling with the number of intervals) on the double-well family, T = 5,
-    dt = 1e-4, 512 bins: the L2 error of the slow variable's histogram at T,
-    sqrt(sum_i (rho_i - rho_ref,i)^2 / h), against a serial fine solution with
-    ten times the particles, per parareal iteration."""
+def _chem_leg(L, dev, stream, rank, chunk, iters=20):
+    """The paper's chemical-reaction workload (Section 2.1.2, Table 1: 1e5
+    particles, 20 slices of 2000 steps, 600 cells on [0, 600]): time per
+    pipelined parareal iteration in binary32 and FP64, and max_n W1 against
+    the serial fine solution with the same random numbers per iteration."""
     import torch
     from paper_1912_09240_gb300.parareal import PararealSolver
-
-    def reference_cdfs(w):
-        """CDFs [K+1][bins+1] of the serial fine solution with 10 N particles."""
-        nr = 10 * w.N
-        wr = w.scaled(N=nr)
-        x0 = workloads.initial_slow(wr)
-        model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
-        grid = L.Grid(w.bins, w.lo, w.hi)
-        x = torch.tensor(x0, dtype=torch.float32, device=dev).reshape(1, nr)
-        y = x.reshape(1, 1, nr).clone()
-        cnt = torch.empty(1, w.bins, dtype=torch.int32, device=dev)
-        cdf = torch.empty(w.K + 1, w.bins + 1, dtype=torch.float64, device=dev)
-        L.pr_restrict(L.PR_F32, x, nr, 1, grid, cnt, cdf[0:1], stream=stream)
-        for s_ in range(w.K):
-            L.pr_fine_propagate(model, L.PR_F32, L.Rng(w.seed, rank), x, y, False, x, y, nr, s_, 1, w.steps,
-                                w.step_dt, stream=stream)
-            L.pr_restrict(L.PR_F32, x, nr, 1, grid, cnt, cdf[s_ + 1:s_ + 2], stream=stream)
-        return cdf
-
-    def errors(w, iterator, matching, ref):
-        model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
-        grid = L.Grid(w.bins, w.lo, w.hi)
-        sv = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
-                            rng=L.Rng(w.seed, rank), device=str(dev), iterator=iterator, matching=matching)
-        x0 = torch.tensor(workloads.initial_slow(w), dtype=torch.float32, device=dev)
-        sv.set_initial(x0, x0.reshape(1, -1))
-        h = (w.hi - w.lo) / w.bins
-        mref = torch.diff(ref, dim=1)
-        w1 = torch.empty(w.K + 1, dtype=torch.float64, device=dev)
-        out = {"l2_at_T": [], "l2_max_over_slices": [], "w1_max_over_slices": []}
-        for k in range(iters + 1):
-            if k:
-                sv.iterate()
-            m = torch.diff(sv.rho, dim=1)
-            l2 = torch.sqrt(((m - mref) ** 2).sum(dim=1) / h)
-            L.pr_w1(grid, w.K + 1, sv.rho, ref, w1, stream=stream)
-            out["l2_at_T"].append(float(l2[w.K].item()))
-            out["l2_max_over_slices"].append(float(l2.max().item()))
-            out["w1_max_over_slices"].append(float(w1.max().item()))
+    w = workloads.CHEM
+    model = L.Model(w.kind, 1, 0.0, 1.0, w.eps, w.tau_x, w.rates)
+    grid = L.Grid(w.bins, w.lo, w.hi)
+    x0, y0 = workloads.initial_ensemble(w)
+    out = {"workload": w.name, "particle_steps_per_iteration": w.particle_steps_per_iteration}
+    for prec, tag in ((L.PR_F32, "f32"), (L.PR_F64, "f64")):
+        dty = torch.float32 if prec == L.PR_F32 else torch.float64
+        sv = PararealSolver(model, grid, w.N, w.K, w.steps, w.step_dt, precision=prec, rng=L.Rng(w.seed, rank),
+                            device=str(dev), chunk=chunk)
+        x0t, y0t = torch.tensor(x0, dtype=dty, device=dev), torch.tensor(y0, dtype=dty, device=dev)
+        sv.set_initial(x0t, y0t)
+        _, _, rser = sv.serial_reference()
+        sv.w1_to(rser).max().item()
+        sv.set_initial(x0t, y0t)
+        times, w1s = [], [float(sv.w1_to(rser).max().item())]
+        for _ in range(iters if prec == L.PR_F32 else 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sv.iterate()
+            sv.join()
+            e1.record(stream)
+            w1s.append(float(sv.w1_to(rser).max().item()))
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times[1:])
+        out[tag] = {"iteration_ms": ms, "particle_steps_per_s": w.particle_steps_per_iteration / (ms / 1e3),
+                    "max_w1_per_iteration": w1s, "status": int(sv.status.item())}
         sv.close()
-        return out
+    out["f64_over_f32_iteration_time"] = out["f64"]["iteration_ms"] / out["f32"]["iteration_ms"]
+    return out
 
-    base = workloads.DOUBLE_WELL.scaled(N=n, T=5.0, dt=1e-4)
-    res = {"particles": n, "reference_particles": 10 * n, "T": 5.0, "dt": 1e-4,
-           "errors": "L2 of the densities sqrt(sum (rho_i - rho_ref,i)^2 / h) at T and max over slices; W1 max over "
-                     "slices; the 10N reference's first N particles share the parareal ensemble's noise"}
-    e1 = {}
-    for eps in (1e-1, 1e-2, 1e-3):
-        w = base.scaled(eps=eps, K=20)
-        ref = reference_cdfs(w)
-        e1[f"eps={eps:g}"] = {f"{it_name}/{m}": errors(w, it, m, ref)
-                              for it_name, it in (("quantile", L.PR_ITER_QUANTILE), ("add", L.PR_ITER_ADD))
-                              for m in ("quantile", "resample")}
-    res["time_scale_separation"] = e1
-    e2 = {}
-    for K in (20, 50, 100):
-        w = base.scaled(K=K)
-        ref = reference_cdfs(w)
-        e2[f"slices={K}"] = {f"quantile/{m}": errors(w, L.PR_ITER_QUANTILE, m, ref) for m in ("quantile", "resample")}
-    res["number_of_intervals"] = e2
-    return res
+
+def _studies_leg(L, dev, stream, rank, n=None, iters=20):
+    """The convergence studies of Section 6 on the chemical system with the
+    defaults of Table 1 (1e5 particles, T = 40, fine step 1e-3, 600 cells):
+    varying the time-scale separation eps (20 slices), and the number of
+    slices N = 20, 50, 100 at eps = 2.5e-2; every iterator with every
+    matching; per iteration, the L2 error of the slow variable's histogram
+    (piecewise-constant densities) and W1 against a serial fine solution with
+    ten times the particles, at T and as the maximum over slices."""
+    from paper_1912_09240_gb300.studies import ConvergenceStudy
+    base = workloads.CHEM if n is None else workloads.CHEM.scaled(N=n)
+    iterators = {"quantile": L.PR_ITER_QUANTILE, "add": L.PR_ITER_ADD, "mult": L.PR_ITER_MULT,
+                 "rot": L.PR_ITER_ROT}
+    matchings = ("quantile", "resample", "resample_det", "reweight")
+    r4 = lambda v: [float(f"{a:.4g}") for a in v]
+
+    def study(w):
+        x0, y0 = workloads.initial_ensemble(w)
+        xe, ye = workloads.initial_ensemble(w.scaled(N=9 * w.N), seed=w.seed + 1)
+        model = L.Model(w.kind, 1, 0.0, 1.0, w.eps, w.tau_x, w.rates)
+        st = ConvergenceStudy(model, L.Grid(w.bins, w.lo, w.hi), w.K, w.steps, w.step_dt, x0, y0,
+                              np.concatenate([x0, xe]), np.concatenate([y0, ye], axis=1), seed=w.seed)
+        res = {}
+        for it_name, it in iterators.items():
+            for m in matchings:
+                r = st.run(iters, iterator=it, matching=m)
+                res[f"{it_name}/{m}"] = {"l2_at_T": r4(r["l2"][:, -1].tolist()),
+                                         "l2_max": r4(r["l2"].max(dim=1).values.tolist()),
+                                         "w1_max": r4(r["w1"].max(dim=1).values.tolist()),
+                                         "status": r["status"]}
+        return res
+
+    out = {"workload": base.name, "particles": base.N, "reference_particles": 10 * base.N, "T": base.T,
+           "iterations": iters,
+           "errors": "L2 of the piecewise-constant densities sqrt(sum (m_i - m_ref,i)^2 / h) at T and max over "
+                     "slices; W1 max over slices; the reference's first N particles are the parareal ensemble"}
+    out["time_scale_separation"] = {f"eps={eps:g}": study(base.scaled(eps=eps))
+                                    for eps in (2.5e-2, 1e-2, 5e-3, 2.5e-3)}
+    out["number_of_intervals"] = {f"slices={K}": study(base.scaled(K=K)) for K in (20, 50, 100)}
+    return out
 
 
 def _adjoint_leg(L, dev, stream, rank, n=None):
@@ -802,7 +810,7 @@ def _batched_leg(L, dev, stream, rank, ws, dist):
 # `--legs all` adds them.  Each leg's result goes to stderr as one JSON line
 # {"leg": name, ...} and, with --legs-out, into one JSON file.
 LEGS = ("fp64_iteration", "convergence_detail", "batched", "unfused", "plain_ou", "matchings", "advection",
-        "studies", "adjoint", "fast16", "cpu_detail")
+        "chem", "studies", "adjoint", "fast16", "cpu_detail")
 
 
 def parse_legs(spec: str | None) -> list:
@@ -984,7 +992,8 @@ def run_ours(args):
     leg("plain_ou", lambda: _plain_leg(L, dev, stream, rank))
     leg("matchings", lambda: _matching_leg(L, dev, stream, rank, args.chunk))
     leg("advection", lambda: _advection_leg(L, dev, stream))
-    leg("studies", lambda: _studies_leg(L, dev, stream, rank))
+    leg("chem", lambda: _chem_leg(L, dev, stream, rank, args.chunk))
+    leg("studies", lambda: _studies_leg(L, dev, stream, rank, n=args.studies_n))
     leg("adjoint", lambda: _adjoint_leg(L, dev, stream, rank, n=args.adjoint_n))
     if "fast16" in legs:
         solver.close()
@@ -1059,6 +1068,7 @@ def main():
     ap.add_argument("--update-cluster", type=int, default=None, help="CTAs of the serial-sweep cluster")
     ap.add_argument("--chunk", type=int, default=5, help="slices per pipelined chunk (0: sequential)")
     ap.add_argument("--adjoint-n", type=int, default=None, help="particles of the adjoint leg")
+    ap.add_argument("--studies-n", type=int, default=None, help="particles of the studies leg (default 1e5)")
     ap.add_argument("--large-n", type=int, default=None, help="particles of the 16-dimensional leg")
     ap.add_argument("--large-k", type=int, default=None, help="slices of the 16-dimensional leg")
     ap.add_argument("--n", type=int, default=None, help="particles (smaller case for profiling)")

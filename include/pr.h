@@ -548,6 +548,16 @@ pr_status pr_w1(const pr_grid* grid, int32_t n_vec, const double* c1, const doub
                 double* w1, void* stream);
 
 /*
+ * L2 distance between the piecewise-constant densities (Eq.
+ * piecewise_constant_pdf: bin mass / h) of pairs of macroscopic states, the
+ * histogram error of the experiments of Section 6:
+ * sqrt(sum_i (m1_i - m2_i)^2 / h) with m_i = C_{i+1} - C_i.
+ *   c1, c2 (device) [n_vec][bins+1]; l2 (device) [n_vec] doubles.
+ */
+pr_status pr_l2_density(const pr_grid* grid, int32_t n_vec, const double* c1, const double* c2,
+                        double* l2, void* stream);
+
+/*
  * Transfers for callers that keep the initial ensemble X_0 and the resulting
  * macroscopic states in host memory (no counterpart in the paper: plumbing of
  * the boundary).  pr_copy_to_device copies `bytes` from src (host) to dst

@@ -735,6 +735,23 @@ double or_w1(int I, double lo, double hi, const double* C1, const double* C2)
     return acc;
 }
 
+/* L2 distance between the piecewise-constant densities of two histograms on
+ * the same uniform grid (Eq. piecewise_constant_pdf: density rho_i / h on bin
+ * i), the error measure of the experiments of Section 6:
+ * sqrt( int (rho1_pc - rho2_pc)^2 dx ) = sqrt( sum_i (m1_i - m2_i)^2 / h ),
+ * with the bin masses m_i = C_{i+1} - C_i read from the CDFs at the edges. */
+double or_l2_density(int I, double lo, double hi, const double* C1, const double* C2)
+{
+    const double h = (hi - lo) / (double)I;
+    double acc = 0.0;
+    for (int i = 0; i < I; ++i) {
+        const double m1 = C1[i + 1] - C1[i];
+        const double m2 = C2[i + 1] - C2[i];
+        acc += (m1 - m2) * (m1 - m2) / h;
+    }
+    return sqrt(acc);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Matching that preserves the conditional distribution (Section 5.2):      */
 /* mu = mubar f(x) with f = rho / rhobar, sampled by reweighting the prior  */

@@ -63,6 +63,8 @@ def lib():
         _lib.or_normals_block.argtypes = [u64, u32, u32, i64, u32, u32, i32, i32, vp]
         _lib.or_fine_propagate_chem.argtypes = [i32, vp, d, d, u64, u32, vp, vp, i64, vp, i32, i32, i32, d]
         _lib.or_chem_coefficients.argtypes = [i32, vp, d, d, vp]
+        _lib.or_l2_density.argtypes = [i32, d, d, vp, vp]
+        _lib.or_l2_density.restype = d
         _lib.or_fine_propagate.argtypes = [i32, i32, d, d, d, d, u64, u32, vp, vp, i64,
                                            i32, i32, i32, d]
         _lib.or_fine_propagate_ids.argtypes = [i32, i32, d, d, d, d, u64, u32, vp, vp, i64, vp,
@@ -363,6 +365,14 @@ def w1(grid: Grid, c1: np.ndarray, c2: np.ndarray) -> float:
     c1 = np.ascontiguousarray(c1, dtype=np.float64)
     c2 = np.ascontiguousarray(c2, dtype=np.float64)
     return lib().or_w1(grid.bins, grid.lo, grid.hi, _p(c1), _p(c2))
+
+
+def l2_density(grid: Grid, c1: np.ndarray, c2: np.ndarray) -> float:
+    """L2 distance of the piecewise-constant densities of two CDFs (the
+    histogram error of the experiments of Section 6)."""
+    c1 = np.ascontiguousarray(c1, dtype=np.float64)
+    c2 = np.ascontiguousarray(c2, dtype=np.float64)
+    return lib().or_l2_density(grid.bins, grid.lo, grid.hi, _p(c1), _p(c2))
 
 
 # --------------------------------------------------------------------------

@@ -32,7 +32,7 @@ EXPORTED = (
     "pr_batch_rho", "pr_batch_fine_state", "pr_batch_status", "pr_batch_set_config", "pr_batch_get_config",
     "pr_batch_tune", "pr_reweight", "pr_resample_workspace", "pr_resample", "pr_restrict_weighted_workspace",
     "pr_restrict_weighted", "pr_moments_workspace", "pr_moments", "pr_copy_to_device", "pr_copy_to_host",
-    "pr_stream_synchronize",
+    "pr_stream_synchronize", "pr_l2_density",
 )
 
 
@@ -146,6 +146,7 @@ def lib() -> ctypes.CDLL:
     L.pr_parareal_update.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp]
     L.pr_iterate.argtypes = [i32, i32, P(_Grid), i32, vp, vp, vp, vp, vp, vp]
     L.pr_w1.argtypes = [P(_Grid), i32, vp, vp, vp, vp]
+    L.pr_l2_density.argtypes = [P(_Grid), i32, vp, vp, vp, vp]
     L.pr_fine_adjoint_workspace.argtypes = [i64, i32, i32, i32]
     L.pr_fine_adjoint_workspace.restype = ctypes.c_size_t
     L.pr_fine_adjoint.argtypes = [P(_Model), P(_Rng), vp, vp, i64, i32, i32, i32, d, i32, vp, vp, vp, vp, vp,
@@ -307,6 +308,12 @@ def pr_iterate(iterator: int, qmode: int, grid: Grid, n_vec: int, a, b, c, out, 
 def pr_w1(grid: Grid, n_vec: int, c1, c2, w1, stream=None):
     g = grid.c()
     _check("pr_w1", lib().pr_w1(ctypes.byref(g), n_vec, _ptr(c1), _ptr(c2), _ptr(w1), _stream(stream)))
+
+
+def pr_l2_density(grid: Grid, n_vec: int, c1, c2, l2, stream=None):
+    g = grid.c()
+    _check("pr_l2_density", lib().pr_l2_density(ctypes.byref(g), n_vec, _ptr(c1), _ptr(c2), _ptr(l2),
+                                                _stream(stream)))
 
 
 def pr_fine_adjoint_workspace(n: int, n_slices: int, steps: int, ckpt_every: int) -> int:

@@ -294,6 +294,23 @@ w1_kernel(GridDev g, const double* __restrict__ c1, const double* __restrict__ c
     if (threadIdx.x == 0) w1[blockIdx.x] = s;
 }
 
+// L2 distance of the piecewise-constant densities (bin mass / h) of two CDFs:
+// sqrt(sum_i (m1_i - m2_i)^2 / h), one CTA per pair.
+__global__ void __launch_bounds__(256)
+l2_density_kernel(GridDev g, const double* __restrict__ c1, const double* __restrict__ c2, double* __restrict__ out)
+{
+    __shared__ double wsum[40];
+    const int I = g.bins;
+    const size_t off = (size_t)blockIdx.x * (I + 1);
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < I; i += blockDim.x) {
+        const double d = (c1[off + i + 1] - c1[off + i]) - (c2[off + i + 1] - c2[off + i]);
+        acc += d * d / g.h;
+    }
+    const double s = block_sum_f64(acc, wsum);
+    if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s);
+}
+
 // CTAs of the cluster that runs the serial sweep (1, 2, 4 or 8; portable sizes).
 static int g_update_cluster = 8;
 
@@ -555,6 +572,17 @@ extern "C" pr_status pr_w1(const pr_grid* grid, int32_t n_vec, const double* c1,
     if (!elem_aligned(c1, 8) || !elem_aligned(c2, 8) || !elem_aligned(w1, 8)) return PR_ERR_INVALID_ARG;
     const GridDev g = make_grid(*grid);
     w1_kernel<<<n_vec, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, c1, c2, w1);
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}
+
+extern "C" pr_status pr_l2_density(const pr_grid* grid, int32_t n_vec, const double* c1, const double* c2,
+                                   double* l2, void* stream)
+{
+    if (!grid_ok(grid) || n_vec < 1 || !c1 || !c2 || !l2) return PR_ERR_INVALID_ARG;
+    if (!elem_aligned(c1, 8) || !elem_aligned(c2, 8) || !elem_aligned(l2, 8)) return PR_ERR_INVALID_ARG;
+    const GridDev g = make_grid(*grid);
+    l2_density_kernel<<<n_vec, 256, 0, static_cast<cudaStream_t>(stream)>>>(g, c1, c2, l2);
     PR_CHECK_LAUNCH();
     return PR_OK;
 }
