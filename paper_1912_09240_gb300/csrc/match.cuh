@@ -19,25 +19,32 @@
 namespace pr {
 
 // Shared-memory layout (bins = I).  The table, live while particles are mapped:
+//   rec    : float4 [I]     one record per prior bin i.  Where the bin's map
+//            has one piece, or two pieces whose target bins j, j+1 meet at
+//            the edge e_{j+1}, the record is (m, fs, b1, b2): the map is
+//            X = m + b (f - fs), b = b1 for f < fs and b2 beyond, with
+//            m = thr[j+1] (two pieces: they meet there at fs; one piece: the
+//            line of the piece reaches it at fs >= 1), the particle's target
+//            bin jm - 1 below fs and jm from fs on (jm the index of the edge
+//            m), so that such a particle reads one 16-byte record.  Otherwise
+//            b1 = -1 and m holds the bits of start | end << 16: the pieces
+//            [start, end) of the bin in the arrays below (start == end:
+//            identity; at most 2I+1 <= 8193 pieces).
 //   piece  : float4 [2I+1]  (alpha, beta, thr[j], thr[j+1]) of target bin j:
 //            on prior bin i the map is X = clamp(alpha + beta f, thr[j], thr[j+1])
 //            for the first piece of the bin whose f_end >= f (or its last piece)
-//   pst    : uint2  [I]     pieces [start, end) of prior bin i as start | end << 16
-//            (start == end: identity; at most 2I+1 <= 8193 pieces) and the
-//            bin's left threshold thr[i] (float bits)
-//   fend   : float  [2I+1]  f_end of each piece (read only where a bin has more
-//            than one piece)
-// so that a particle on a bin with one piece reads an 8-byte and a 16-byte record.
+//   fend   : float  [2I+1]  f_end of each piece
 // Build scratch, dead once the table is built:
 //   Cp, Ct : double [I+1]   prior / target CDF
 //   nzpre  : int    [I+1]   number of non-empty target bins below j
 //   nzlist : int    [I]     non-empty target bins in order
 //   jfirst : int    [I]     first piece's target bin of prior bin i
 //   pstart : int    [I+1]   first piece of prior bin i
-// The binary64 path keeps using Cp, Ct, nzpre and nzlist while it maps.
+// The binary64 path (carve_match_smem) has no table: it keeps Cp, Ct, nzpre
+// and nzlist and maps every particle from them.
 struct MatchSmem {
+    float4* rec;
     float4* piece;
-    uint2* pst;
     float* fend;
     double* Cp;
     double* Ct;
@@ -51,7 +58,7 @@ struct MatchSmem {
 __host__ __device__ inline size_t match_table_bytes(int bins)
 {
     const size_t I = (size_t)bins;
-    return (((2 * I + 1) * 16 + I * 8 + (2 * I + 1) * 4) + 15) & ~(size_t)15;
+    return ((I * 16 + (2 * I + 1) * 16 + (2 * I + 1) * 4) + 15) & ~(size_t)15;
 }
 
 __host__ __device__ inline size_t match_build_bytes(int bins)
@@ -63,7 +70,9 @@ __host__ __device__ inline size_t match_build_bytes(int bins)
     return (b + 15) & ~(size_t)15;
 }
 
-__host__ __device__ inline size_t match_smem_bytes(int bins) { return match_table_bytes(bins) + match_build_bytes(bins); }
+// The binary64 path maps every particle from the CDFs and their index arrays
+// (no binary32 pieces), so its shared memory is the build scratch alone.
+__host__ __device__ inline size_t match_smem_bytes(int bins) { return match_build_bytes(bins); }
 
 // The binary32 table reads the CDFs from global memory while it is built, so
 // its scratch holds only the integer arrays (nzpre, nzlist, jfirst, pstart,
@@ -86,9 +95,9 @@ __device__ inline MatchSmem carve_match_smem_f32(unsigned char* base, int bins, 
 {
     const int I = bins;
     MatchSmem m;
-    m.piece = reinterpret_cast<float4*>(base);
-    m.pst = reinterpret_cast<uint2*>(m.piece + (2 * I + 1));
-    m.fend = reinterpret_cast<float*>(m.pst + I);
+    m.rec = reinterpret_cast<float4*>(base);
+    m.piece = m.rec + I;
+    m.fend = reinterpret_cast<float*>(m.piece + (2 * I + 1));
     m.Cp = const_cast<double*>(cp_g);
     m.Ct = const_cast<double*>(ct_g);
     int* ip = reinterpret_cast<int*>(base + match_table_bytes(bins));
@@ -104,10 +113,10 @@ __device__ inline MatchSmem carve_match_smem(unsigned char* base, int bins)
 {
     const int I = bins;
     MatchSmem m;
-    m.piece = reinterpret_cast<float4*>(base);
-    m.pst = reinterpret_cast<uint2*>(m.piece + (2 * I + 1));
-    m.fend = reinterpret_cast<float*>(m.pst + I);
-    m.Cp = reinterpret_cast<double*>(base + match_table_bytes(bins));
+    m.rec = nullptr;
+    m.piece = nullptr;
+    m.fend = nullptr;
+    m.Cp = reinterpret_cast<double*>(base);
     m.Ct = m.Cp + (I + 1);
     int* ip = reinterpret_cast<int*>(m.Ct + (I + 1));
     m.nzpre = ip;
@@ -227,8 +236,6 @@ __device__ inline void build_match_table(const GridDev& g, const float* thr, Mat
     }
     const int npieces = m.pstart[I];
     const float h_f = (float)g.h;
-    for (int i = threadIdx.x; i < I; i += blockDim.x)
-        m.pst[i] = make_uint2((uint32_t)m.pstart[i] | ((uint32_t)m.pstart[i + 1] << 16), __float_as_uint(thr[i]));
     // one thread per piece: its prior bin by binary search over pstart.  CDF
     // values are subtracted in FP64 (they cancel); the quotients, which end
     // up rounded to binary32 anyway, are taken in binary32, and the target
@@ -258,26 +265,63 @@ __device__ inline void build_match_table(const GridDev& g, const float* thr, Mat
         m.fend[k] = fe;
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < I; i += blockDim.x) {
+        const int k0 = m.pstart[i], k1 = m.pstart[i + 1];
+        float4 r = make_float4(__uint_as_float((uint32_t)k0 | ((uint32_t)k1 << 16)), 0.0f, -1.0f, 0.0f);
+        if (k1 == k0 + 1) {
+            // one piece X = alpha + beta f on [thr_j, thr_{j+1}]: anchored at
+            // the right edge, reached at fs = (thr_{j+1} - alpha) / beta
+            const float4 pc = m.piece[k0];
+            if (pc.y > 0.0f && pc.y < 1e30f) {
+                const float fs = (float)(((double)pc.w - (double)pc.x) / (double)pc.y);
+                if (fs >= 1.0f && fs < 1e30f) r = make_float4(pc.w, fs, pc.y, pc.y);
+            }
+        } else if (k1 == k0 + 2) {
+            // two pieces meeting at the edge thr_{j+1} = hi of the first = lo of the second
+            const float4 p1 = m.piece[k0], p2 = m.piece[k0 + 1];
+            if (p1.w == p2.z && p1.y >= 0.0f && p2.y >= 0.0f && p1.y < 1e30f && p2.y < 1e30f)
+                r = make_float4(p1.w, m.fend[k0], p1.y, p2.y);
+        }
+        m.rec[i] = r;
+    }
+    __syncthreads();
 }
 
 // Map one binary32 particle through the table.
+// The bin fraction f = (x - e_i)/h takes the left edge as lo + i h in
+// binary32 (one fma, within half an ulp of x's magnitude of the edge).  On
+// a bin with one piece, or two pieces meeting at a target edge, the particle
+// reads a single 16-byte record; its image is checked against its target bin
+// by the fast binning (no table read) and clamped into it by the bin's
+// thresholds only where that check does not confirm it (near an edge).
 __device__ __forceinline__ float match_one_f32(const MatchSmem& m, const float* __restrict__ thr, const BinF32& bf,
                                                float x)
 {
-    const int i = bin_fast_f32(bf, thr, x);
-    const uint2 kk = m.pst[i];
-    const int k0 = (int)(kk.x & 0xFFFFu), k1 = (int)(kk.x >> 16);
-    if (k0 == k1) return x;   // identity on this bin
+    float fi;
+    const int i = bin_fast_f32(bf, thr, x, fi);
+    const float4 r = m.rec[i];
     const bool below = !(x >= bf.thr0);
     const bool above = x >= bf.thrI;
-    float f = (x - __uint_as_float(kk.y)) * bf.inv_h;
+    float f = (x - fmaf(fi, bf.h, bf.lo)) * bf.inv_h;
     f = fminf(fmaxf(f, 0.0f), 1.0f);
     if (below) f = 0.0f;
     if (above) f = 1.0f;
-    int k = k0;
-    while (k < k1 - 1 && f > m.fend[k]) ++k;
-    const float4 pc = m.piece[k];
-    const float xn = fminf(fmaxf(fmaf(pc.y, f, pc.x), pc.z), pc.w);
+    float xn;
+    if (r.z >= 0.0f) {
+        const bool second = f >= r.y;
+        xn = fmaf(second ? r.w : r.z, f - r.y, r.x);
+        const int jm = __float2int_rn((r.x - bf.lo) * bf.inv_h);
+        const int j = min(second ? jm : jm - 1, bf.bins - 1);
+        if (bin_try_f32(bf, xn) != j) xn = fminf(fmaxf(xn, thr[j]), thr[j + 1]);
+    } else {
+        const uint32_t kk = __float_as_uint(r.x);
+        const int k0 = (int)(kk & 0xFFFFu), k1 = (int)(kk >> 16);
+        if (k0 == k1) return x;   // identity on this bin
+        int k = k0;
+        while (k < k1 - 1 && f > m.fend[k]) ++k;
+        const float4 pc = m.piece[k];
+        xn = fminf(fmaxf(fmaf(pc.y, f, pc.x), pc.z), pc.w);
+    }
     if (below) return x + (xn - bf.thr0);
     if (above) return x + (xn - bf.thrI);
     return xn;

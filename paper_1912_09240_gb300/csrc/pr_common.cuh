@@ -295,7 +295,7 @@ __device__ __forceinline__ int bin_of_f32(const float* __restrict__ thr, int bin
 // thresholds decide as in bin_of_f32; the result equals bin_of_f32's for
 // every x, and the common case needs one fma, three adds and no conversion.
 struct BinF32 {
-    float lo, inv_h, c, thr0, thrI, half_m;
+    float lo, inv_h, c, thr0, thrI, half_m, h;
     int bins;
 };
 
@@ -304,6 +304,7 @@ __device__ __forceinline__ BinF32 make_bin_f32(float thr0, float thrI, int bins,
     BinF32 b;
     b.lo = lo_f;
     b.inv_h = inv_h_f;
+    b.h = __frcp_rn(inv_h_f);
     b.bins = bins;
     b.thr0 = thr0;
     b.thrI = thrI;
@@ -349,6 +350,24 @@ __device__ __forceinline__ int bin_fast_f32(const BinF32& b, const float* __rest
     const int i = bin_try_f32(b, x);
     if (i >= 0) return i;
     return bin_slow_f32(b, [thr](int k) { return thr[k]; }, x);
+}
+
+// bin_fast_f32, also giving the bin index as a float (taken from the fast
+// path's rounding, which already holds it, else converted).
+__device__ __forceinline__ int bin_fast_f32(const BinF32& b, const float* __restrict__ thr, float x, float& fi)
+{
+    const float g = fmaf(x, b.inv_h, b.c);
+    const float t = g + 12582912.0f;
+    const float r = t - 12582912.0f;
+    const float d = g - r;
+    const int i = __float_as_int(t) - 0x4B400000;
+    if ((unsigned)i < (unsigned)b.bins && fabsf(d) <= b.half_m) {
+        fi = r;
+        return i;
+    }
+    const int k = bin_slow_f32(b, [thr](int q) { return thr[q]; }, x);
+    fi = (float)k;
+    return k;
 }
 
 // thr[i] for i = 0..bins, cooperatively by the block.

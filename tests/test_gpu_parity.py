@@ -187,7 +187,8 @@ def _cdf_pair(orc, og, rng, n):
     return prior_x, cp[0], ct[0]
 
 
-@pytest.mark.parametrize("bins,lo,hi", [(64, -3.0, 3.0), (512, -3.0, 3.0), (37, -2.2, 4.1), (2400, -3.0, 3.0)])
+@pytest.mark.parametrize("bins,lo,hi", [(64, -3.0, 3.0), (512, -3.0, 3.0), (37, -2.2, 4.1), (2400, -3.0, 3.0),
+                                       (4096, -3.0, 3.0)])
 def test_match_f64_bit_exact(L, orc, bins, lo, hi):
     og = orc.Grid(bins, lo, hi)
     rng = np.random.default_rng(3)
@@ -483,14 +484,15 @@ def test_update_cluster_sizes_agree(L, bins):
 
 
 def test_matching_table_beyond_shared_memory_is_unsupported(L):
-    """A grid whose matching table does not fit one CTA's shared memory
-    (4096 bins) is refused with PR_ERR_UNSUPPORTED, standalone and fused into
-    the fine propagator, in both precisions; the restriction alone still
-    runs at 4096 bins."""
+    """A grid whose binary32 matching table does not fit one CTA's shared
+    memory (4096 bins) is refused with PR_ERR_UNSUPPORTED, standalone and
+    fused into the fine propagator; the restriction alone still runs at 4096
+    bins.  (The binary64 matching keeps no table and covers 4096 bins:
+    test_match_f64_bit_exact, test_fused_matching_equals_standalone.)"""
     bins, n = 4096, 1000
     grid = L.Grid(bins, -3.0, 3.0)
     cdf = torch.linspace(0.0, 1.0, bins + 1, dtype=torch.float64, device=DEV).reshape(1, -1)
-    for prec, dt in ((L.PR_F32, torch.float32), (L.PR_F64, torch.float64)):
+    for prec, dt in ((L.PR_F32, torch.float32),):
         x = torch.zeros(1, n, dtype=dt, device=DEV)
         y = torch.zeros(1, 1, n, dtype=dt, device=DEV)
         out = torch.empty_like(x)
@@ -510,7 +512,7 @@ def test_matching_table_beyond_shared_memory_is_unsupported(L):
 
 
 @pytest.mark.parametrize("prec,bins,kind,d", [(0, 64, 1, 1), (0, 512, 1, 1), (0, 2900, 0, 1), (0, 512, 2, 3),
-                                              (1, 64, 0, 1), (1, 2400, 1, 1), (1, 256, 2, 3)])
+                                              (1, 64, 0, 1), (1, 2400, 1, 1), (1, 256, 2, 3), (1, 4096, 1, 1)])
 def test_fused_matching_equals_standalone(L, orc, prec, bins, kind, d):
     """pr_fine_propagate with the matching fused into its prologue equals
     pr_match followed by pr_fine_propagate without it, bit for bit, and the
