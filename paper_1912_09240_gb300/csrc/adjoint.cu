@@ -8,7 +8,10 @@
 // (n_slices x steps), drawing exactly the random numbers pr_fine_propagate
 // draws and taking exactly its steps (em_step_f32), and stores (x, y) every
 // `ckpt_every` steps in the caller's workspace.
-// Backward, for each checkpoint segment from the last: the segment is
+// Backward, where a segment's reconstruction stays accurate (see
+// adjoint_reverse_ok): the reverse walk (adjoint_rev_kernel), which
+// reconstructs the states by inverting the Euler steps.  Otherwise, exact
+// replay, for each checkpoint segment from the last: the segment is
 // replayed once from its checkpoint to leave sub-checkpoints every 12 steps in
 // a scratch area of the workspace (16 B per particle per 12 steps); each
 // 12-step block is then replayed once more, keeping its states and noise
@@ -29,6 +32,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "pr_common.cuh"
@@ -49,6 +53,8 @@ struct AdjArgs {
     int64_t n_ckpt;
     float lam, ddt, rel, sxk, syk;               // forward constants, as pr_fine_propagate
     float inv2beta, inv2eps, rel_over_eps;       // derivative factors: 1/(2 beta), 1/(2 eps), dt/eps^2
+    float ia, ib, ic, id;     // inverse of the OU step's matrix [[1-ddt, lam ddt], [rel, 1-rel]]
+    float inv1mrel;           // 1 / (1 - rel)
     uint32_t k0, k1, chi;
     float* ckpt_buf;          // [n_ckpt][2][n]
     float* sub_buf;           // [ceil(min(ckpt, total) / kSub)][2][n]
@@ -383,6 +389,180 @@ adjoint_paired_kernel(AdjArgs a)
     if (a.partial) block_partials(a, g0, g1, g2);
 }
 
+// Reverse-walk adjoint.  The backward pass does not replay the forward: it
+// reconstructs each state from the next by inverting the Euler step with the
+// same noise increments, which it draws again, and runs the adjoint recursion
+// on the fly:
+//   OU:          (x, y) = M^{-1} (x' - dU, y' - dV), M = [[1-ddt, lam ddt], [rel, 1-rel]]
+//   double well: y = (y' - dV - rel x) / (1 - rel), x the fixed point of
+//                x = x' - dU + ddt (x^3 - x + lam y(x)), two iterations from
+//                x' - dU (each shrinks the error by ddt |3x^2 - 1 - lam rel/(1-rel)|)
+// Each checkpoint segment starts again from the stored exact state at its
+// end, so the rounding of the reconstruction grows over one segment only, by
+// at most (1/(1-rel))^ckpt / (1-ddt)^ckpt, which the host bounds before it
+// picks this kernel.  Cost: the forward pass and one backward pass with its
+// Philox blocks, no sub-checkpoints, no shared memory.
+template <int KIND>
+__device__ __forceinline__ void inverse_step(const AdjArgs& a, float& x, float& y, float nx, float ny)
+{
+    const float bx = x - nx, by = y - ny;
+    if (KIND == PR_MODEL_OU) {
+        x = fmaf(a.ia, bx, a.ib * by);
+        y = fmaf(a.ic, bx, a.id * by);
+    } else {
+        float u = bx;
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+            const float v = (by - a.rel * u) * a.inv1mrel;
+            u = fmaf(a.ddt, fmaf(u * u, u, -u) + a.lam * v, bx);
+        }
+        x = u;
+        y = (by - a.rel * u) * a.inv1mrel;
+    }
+}
+
+// Adjoint of step t at its start state (x, y), given lbar_{t+1} in (lx, ly):
+// the parameter sums and lbar_t.
+template <int KIND>
+__device__ __forceinline__ void adjoint_step(const AdjArgs& a, float x, float y, float nx, float ny, float& lx,
+                                             float& ly, float& p0, float& p1, float& p2)
+{
+    float jxx, jxy, dxdl;
+    if (KIND == PR_MODEL_OU) {
+        jxx = 1.0f - a.ddt;
+        jxy = a.lam * a.ddt;
+        dxdl = a.ddt * y;
+    } else {
+        jxx = 1.0f - a.ddt * (3.0f * x * x - 1.0f);
+        jxy = -a.lam * a.ddt;
+        dxdl = -a.ddt * y;
+    }
+    p0 = fmaf(lx, dxdl, p0);
+    p1 = fmaf(lx, -nx * a.inv2beta, p1);
+    p2 = fmaf(ly, -a.rel_over_eps * (x - y) - ny * a.inv2eps, p2);
+    const float nlx = lx * jxx + ly * a.rel;
+    const float nly = lx * jxy + ly * (1.0f - a.rel);
+    lx = nlx;
+    ly = nly;
+}
+
+// PAIRED: every slice has an even number of steps and the checkpoint
+// interval is even, so each Philox block serves the pair (m, m+1) of one
+// segment, forwards and backwards.
+template <int KIND, bool PAIRED>
+__global__ void __launch_bounds__(kAdjThreads, 8)
+adjoint_rev_kernel(AdjArgs a)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool ok = p < a.n;
+    const uint32_t pid = (uint32_t)p;
+    const int S = a.steps;
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    float lx = 0.0f, ly = 0.0f;
+    if (ok) {
+        // ---- forward with checkpoints (pr_fine_propagate's steps) ----
+        float x = a.x0[p], y = a.y0[p];
+        NoiseWalker nw;
+        nw.seek(0, S);
+        int slice = 0, m = 0;
+        for (int64_t c = 0; c < a.n_ckpt; ++c) {
+            a.ckpt_buf[(c * 2) * a.n + p] = x;
+            a.ckpt_buf[(c * 2 + 1) * a.n + p] = y;
+            const int L = (int)min((int64_t)a.ckpt, a.total - c * a.ckpt);
+            if (PAIRED) {
+                for (int i = 0; i < L; i += 2) {
+                    const uint4 w = philox4x32_10(
+                        make_uint4((uint32_t)(m >> 1), pid, (uint32_t)(a.slice_begin + slice), a.chi), a.k0, a.k1);
+                    float q0, c0, s0, q1, c1, s1;
+                    box_muller_qcs(w.x, w.y, q0, c0, s0);
+                    box_muller_qcs(w.z, w.w, q1, c1, s1);
+                    em_step_f32<KIND>(x, y, q0 * a.sxk, c0, q0 * a.syk, s0, a.lam, a.ddt, a.rel);
+                    em_step_f32<KIND>(x, y, q1 * a.sxk, c1, q1 * a.syk, s1, a.lam, a.ddt, a.rel);
+                    m += 2;
+                    if (m == S) { m = 0; ++slice; }
+                }
+            } else {
+                for (int i = 0; i < L; ++i) {
+                    float q, cc, sn;
+                    nw.draw(a, pid, q, cc, sn);
+                    em_step_f32<KIND>(x, y, q * a.sxk, cc, q * a.syk, sn, a.lam, a.ddt, a.rel);
+                    nw.advance(S);
+                }
+            }
+        }
+        if (a.xT) a.xT[p] = x;
+        if (a.yT) a.yT[p] = y;
+        const float xe = x, ye = y;
+
+        // ---- backward, segment by segment from the last ----
+        lx = seed_of(a, p, xe);
+        ly = a.ybar ? (float)a.ybar[p] : 0.0f;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        int cached_mp = -1, cached_slice = -1;
+        for (int64_t c = a.n_ckpt - 1; c >= 0; --c) {
+            const int64_t t0 = c * a.ckpt;
+            const int L = (int)min((int64_t)a.ckpt, a.total - t0);
+            if (c + 1 < a.n_ckpt) {   // the exact state at the segment's end
+                x = a.ckpt_buf[((c + 1) * 2) * a.n + p];
+                y = a.ckpt_buf[((c + 1) * 2 + 1) * a.n + p];
+            } else {
+                x = xe;
+                y = ye;
+            }
+            const int64_t tl = t0 + L - 1;
+            slice = (int)(tl / S);
+            m = (int)(tl - (int64_t)slice * S);
+            // blocks of at most kSub steps, backwards; binary32 partial sums
+            // per block, added into the binary64 sums after it
+            for (int left = L; left > 0; left -= kSub) {
+                const int len = min(kSub, left);
+                float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
+                if (PAIRED) {   // m is odd here: steps m and m - 1 from one block
+                    for (int i = 0; i < len; i += 2) {
+                        const uint4 wp = philox4x32_10(
+                            make_uint4((uint32_t)(m >> 1), pid, (uint32_t)(a.slice_begin + slice), a.chi), a.k0,
+                            a.k1);
+                        float q0, c0, s0, q1, c1, s1;
+                        box_muller_qcs(wp.z, wp.w, q1, c1, s1);
+                        box_muller_qcs(wp.x, wp.y, q0, c0, s0);
+                        float nx = (q1 * a.sxk) * c1, ny = (q1 * a.syk) * s1;
+                        inverse_step<KIND>(a, x, y, nx, ny);
+                        adjoint_step<KIND>(a, x, y, nx, ny, lx, ly, p0, p1, p2);
+                        nx = (q0 * a.sxk) * c0;
+                        ny = (q0 * a.syk) * s0;
+                        inverse_step<KIND>(a, x, y, nx, ny);
+                        adjoint_step<KIND>(a, x, y, nx, ny, lx, ly, p0, p1, p2);
+                        m -= 2;
+                        if (m < 0) { --slice; m = S - 1; }
+                    }
+                } else {
+                    for (int i = 0; i < len; ++i) {
+                        const int mp = m >> 1;
+                        if (mp != cached_mp || slice != cached_slice) {
+                            w = philox4x32_10(
+                                make_uint4((uint32_t)mp, pid, (uint32_t)(a.slice_begin + slice), a.chi), a.k0, a.k1);
+                            cached_mp = mp;
+                            cached_slice = slice;
+                        }
+                        float q, cc, sn;
+                        if (m & 1) box_muller_qcs(w.z, w.w, q, cc, sn);
+                        else box_muller_qcs(w.x, w.y, q, cc, sn);
+                        const float nx = (q * a.sxk) * cc, ny = (q * a.syk) * sn;
+                        inverse_step<KIND>(a, x, y, nx, ny);
+                        adjoint_step<KIND>(a, x, y, nx, ny, lx, ly, p0, p1, p2);
+                        if (--m < 0) { --slice; m = S - 1; }
+                    }
+                }
+                g0 += (double)p0;
+                g1 += (double)p1;
+                g2 += (double)p2;
+            }
+        }
+        store_outputs(a, p, lx, ly, g0, g1, g2);
+    }
+    if (a.partial) block_partials(a, g0, g1, g2);
+}
+
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int64_t blocks, double* __restrict__ grad)
 {
     __shared__ double red[3][256];
@@ -477,6 +657,18 @@ static AdjLayout adjoint_layout(int64_t n, int32_t n_slices, int32_t steps, int3
     return l;
 }
 
+// The reverse walk is taken when the reconstruction over one checkpoint
+// segment of L steps cannot amplify rounding by more than a factor 2:
+// (1/(1-rel))^L (1/(1-ddt))^L <= 2 (the inverse step's growth in y, and its
+// bound in x for the double well).  Otherwise the backward pass replays the
+// forward exactly from sub-checkpoints.
+static bool adjoint_reverse_ok(double drift_dt, double relax, int32_t ckpt_every, int64_t total)
+{
+    const double seg = (double)std::min<int64_t>(ckpt_every, std::max<int64_t>(total, 1));
+    return relax < 0.5 && drift_dt < 0.5 &&
+           seg * (-std::log1p(-relax) - std::log1p(-drift_dt)) <= std::log(2.0);
+}
+
 static pr_status adjoint_check(const pr_model* model, const pr_rng* rng, const float* x0, const float* y0,
                                int64_t n, int32_t slice_begin, int32_t n_slices, int32_t steps, double dt,
                                int32_t ckpt_every, const double* xbar_T, const double* ybar_T, const double* grad)
@@ -525,6 +717,15 @@ static pr_status adjoint_launch(const pr_model* model, const pr_rng* rng, const 
     a.inv2beta = (float)(0.5 / model->beta);
     a.inv2eps = (float)(0.5 / model->eps);
     a.rel_over_eps = (float)(dt / (model->eps * model->eps));
+    {
+        const double m00 = 1.0 - drift_dt, m01 = model->lambda * drift_dt, m10 = relax, m11 = 1.0 - relax;
+        const double det = m00 * m11 - m01 * m10;
+        a.ia = (float)(m11 / det);
+        a.ib = (float)(-m01 / det);
+        a.ic = (float)(-m10 / det);
+        a.id = (float)(m00 / det);
+        a.inv1mrel = (float)(1.0 / (1.0 - relax));
+    }
     a.k0 = (uint32_t)(rng->seed & 0xFFFFFFFFull);
     a.k1 = (uint32_t)(rng->seed >> 32);
     a.chi = rng->problem_id << 8;
@@ -546,7 +747,15 @@ static pr_status adjoint_launch(const pr_model* model, const pr_rng* rng, const 
     const size_t smem = (size_t)4 * kSub * kAdjThreads * sizeof(float);
     const bool paired = steps > 0 && (steps % 2) == 0 && (ckpt_every % 2) == 0;
     const unsigned grid = (unsigned)l.blocks;
-    if (model->kind == PR_MODEL_OU) {
+    if (adjoint_reverse_ok(drift_dt, relax, ckpt_every, l.total)) {
+        if (model->kind == PR_MODEL_OU) {
+            if (paired) adjoint_rev_kernel<PR_MODEL_OU, true><<<grid, kAdjThreads, 0, st>>>(a);
+            else adjoint_rev_kernel<PR_MODEL_OU, false><<<grid, kAdjThreads, 0, st>>>(a);
+        } else {
+            if (paired) adjoint_rev_kernel<PR_MODEL_DOUBLE_WELL, true><<<grid, kAdjThreads, 0, st>>>(a);
+            else adjoint_rev_kernel<PR_MODEL_DOUBLE_WELL, false><<<grid, kAdjThreads, 0, st>>>(a);
+        }
+    } else if (model->kind == PR_MODEL_OU) {
         if (paired) adjoint_paired_kernel<PR_MODEL_OU><<<grid, kAdjThreads, smem, st>>>(a);
         else adjoint_kernel<PR_MODEL_OU><<<grid, kAdjThreads, smem, st>>>(a);
     } else {

@@ -3,7 +3,7 @@ against the FP64 oracle's tangent-linear derivatives and against central
 finite differences with common random numbers.
 
 Tolerances: per-particle sensitivities <= 2e-3 relative (binary32 state
-against FP64) to max(|value|, ensemble scale), ensemble gradients <= 5e-3
+against FP64) to max(|value|, RMS over the ensemble), ensemble gradients <= 5e-3
 relative against central differences (h = 1e-4, FP64 propagation on the
 GPU)."""
 import math
@@ -25,8 +25,11 @@ def L():
 
 
 def _close(a, b, rel, abs_=0.0):
+    """|a - b| <= rel max(|b|, RMS of b over the ensemble) + abs_: a
+    sensitivity that crosses zero has no relative scale of its own, so the
+    ensemble's RMS sets it."""
     a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
-    scale = np.maximum(np.abs(b), np.max(np.abs(b)) * 1e-3)
+    scale = np.maximum(np.abs(b), np.sqrt(np.mean(b * b)))
     return np.all(np.abs(a - b) <= rel * scale + abs_)
 
 
@@ -68,6 +71,54 @@ def test_per_particle_against_tangent(L, orc, kind, slices, steps, ckpt):
     np.testing.assert_array_equal(x.reshape(n).cpu().numpy(), xT.cpu().numpy())
 
 
+def _reverse_walk(dt, eps, tau, ckpt, total):
+    """The host's rule for the reverse-walk backward pass (include/pr.h):
+    (1/(1-rel))^L (1/(1-ddt))^L <= 2 over a segment of L steps."""
+    L_ = min(ckpt, max(total, 1))
+    rel, ddt = dt / eps, dt / tau
+    return rel < 0.5 and ddt < 0.5 and L_ * (-math.log1p(-rel) - math.log1p(-ddt)) <= math.log(2.0)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("slices,steps,ckpt", [(2, 1000, 256), (2, 999, 256), (3, 400, 100), (1, 300, 300)])
+def test_reverse_walk_per_particle_against_tangent(L, orc, kind, slices, steps, ckpt):
+    """Configurations where the backward pass reconstructs the states by
+    inverting the Euler steps (fine steps of 1e-4 at eps = 0.1 and 0.05,
+    paired and unpaired step counts, one segment over the whole horizon):
+    per-particle sensitivities against the oracle's tangent-linear, end
+    state equal to pr_fine_propagate's."""
+    rng = np.random.default_rng(kind + steps + ckpt)
+    n, dt = 1000, 1e-4
+    lam, beta, eps, tau = (1.0, 1.0, 0.1, 1.0) if kind == 0 else (0.5, 3.0, 0.05, 1.0)
+    assert _reverse_walk(dt, eps, tau, ckpt, slices * steps)
+    x0 = rng.normal(1.0 if kind == 0 else -1.0, 0.3, n).astype(np.float32)
+    y0 = rng.normal(0.0, 1.0, n).astype(np.float32)
+    gm = L.Model(kind, 1, lam, beta, eps, tau)
+    om = orc.Model(kind, 1, lam, beta, eps, tau)
+    gx0, gy0 = torch.tensor(x0, device="cuda"), torch.tensor(y0, device="cuda")
+    xT = torch.empty(n, dtype=torch.float32, device="cuda")
+    grads = torch.empty(n, 3, dtype=torch.float64, device="cuda")
+    xb0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    yb0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    ws = torch.empty(L.pr_fine_adjoint_workspace(n, slices, steps, ckpt), dtype=torch.uint8, device="cuda")
+    L.pr_fine_adjoint(gm, L.Rng(4, 1), gx0, gy0, n, 2, slices, steps, dt, ckpt, xT, None, None, None, grads,
+                      xb0, yb0, ws)
+    torch.cuda.synchronize()
+    X, Y, dX, dY = orc.fine_tangent(om, 4, x0.astype(np.float64), y0.astype(np.float64), 2, slices, steps, dt,
+                                    problem=1)
+    g = grads.cpu().numpy()
+    for k in range(3):
+        assert _close(g[:, k], dX[:, k], 2e-3, 1e-7), k
+    assert _close(xb0.cpu().numpy(), dX[:, 3], 2e-3, 1e-7)
+    assert _close(yb0.cpu().numpy(), dX[:, 4], 2e-3, 1e-7)
+    x = gx0.reshape(1, n).clone()
+    y = gy0.reshape(1, 1, n).clone()
+    for s in range(slices):
+        L.pr_fine_propagate(gm, L.PR_F32, L.Rng(4, 1), x, y, False, x, y, n, 2 + s, 1, steps, dt)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(x.reshape(n).cpu().numpy(), xT.cpu().numpy())
+
+
 def test_seeded_sum_equals_contracted_per_particle(L):
     n, slices, steps, dt = 5000, 2, 100, 1e-3
     gm = L.Model(0, 1, 0.8, 1.5, 0.1, 1.0)
@@ -93,13 +144,16 @@ def test_seeded_sum_equals_contracted_per_particle(L):
     np.testing.assert_array_equal(tot.cpu().numpy(), tot2.cpu().numpy())   # deterministic reduction
 
 
-@pytest.mark.parametrize("kind", [0, 1])
-def test_second_moment_gradient_against_central_differences(L, kind):
+@pytest.mark.parametrize("kind,eps_dw", [(0, None), (1, 0.01), (1, 0.05)])
+def test_second_moment_gradient_against_central_differences(L, kind, eps_dw):
     """Central differences (h = 1e-4) of E[X_T^2] with common random numbers,
-    propagated in FP64 on the GPU, against the binary32 adjoint."""
+    propagated in FP64 on the GPU, against the binary32 adjoint (the OU case
+    and the double well at eps = 0.05 take the reverse walk, the double well
+    at eps = 0.01 the exact replay)."""
     from paper_1912_09240_gb300.adjoint import second_moment_gradient
     n, slices, steps, dt = 1 << 16, 2, 1000, 1e-4
-    lam, beta, eps = (1.0, 1.0, 0.1) if kind == 0 else (0.5, 3.0, 0.01)
+    lam, beta, eps = (1.0, 1.0, 0.1) if kind == 0 else (0.5, 3.0, eps_dw)
+    assert _reverse_walk(dt, eps, 1.0, 256, slices * steps) == (eps >= 0.05)
     rng = np.random.default_rng(3)
     x0n = rng.normal(1.0 if kind == 0 else -1.0, 0.1, n)
     y0n = rng.normal(0.0, 1.0, n) if kind == 0 else x0n.copy()
