@@ -484,6 +484,12 @@ pr_status pr_fine_adjoint_noalloc(const pr_model* model, const pr_rng* rng, cons
  * quantile function, Q(p) = X_(ceil(p n)).
  *   x (device) [n]; ranks (device) [n_ranks] int64; index_out (device) [n_ranks] int64
  *   workspace (device) >= pr_order_statistics_workspace(n) bytes, 8-byte aligned.
+ * The ranks are selected, not sorted for: the values are binned into 8192
+ * equal-width buckets of [min, max], and only the buckets holding a requested
+ * rank are gathered and sorted (by value, then index).  Where a value is not
+ * finite or such a bucket holds more than 4096 particles (many equal values,
+ * far outliers), every key is sorted instead; the result is the same.  The
+ * call synchronises `stream` once (the host reads which of the two applies).
  */
 size_t pr_order_statistics_workspace(int64_t n);
 pr_status pr_order_statistics(const float* x, int64_t n, const int64_t* ranks, int32_t n_ranks,

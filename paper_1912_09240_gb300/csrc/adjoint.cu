@@ -584,7 +584,8 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int64
 }
 
 // ---------------------------------------------------------------------------
-// Order statistics: bitonic sort of (orderable float bits << 32 | index)
+// Order statistics: the requested ranks of (orderable float bits << 32 |
+// index), by bucket selection, or by a bitonic sort of all keys
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ uint32_t float_order_bits(float v)
@@ -622,6 +623,197 @@ __global__ void gather_ranks_kernel(const unsigned long long* __restrict__ keys,
     if (r >= n_ranks) return;
     const int64_t rk = ranks[r];
     idx[r] = (rk >= 0 && rk < n) ? (int64_t)(keys[rk] & 0xFFFFFFFFull) : -1;   // -1: rank out of range
+}
+
+// Selection of the requested ranks without sorting everything: the values
+// are binned into kSelBuckets equal-width buckets of [min, max] (a monotone
+// map, so the sorted order is bucket by bucket), the buckets holding a
+// requested rank are found from the bucket counts' prefix sums, their
+// particles are gathered, and each such bucket (at most kSelCap particles) is
+// sorted by (value, index) in shared memory by one CTA per rank.  Non-finite
+// values or a bucket beyond kSelCap fall back to the full sort.
+constexpr int kSelBuckets = 8192;
+constexpr int kSelCap = 4096;
+
+struct SelWs {
+    unsigned* counts;    // [kSelBuckets]
+    unsigned* starts;    // [kSelBuckets + 1] exclusive prefix sums of counts
+    unsigned* seg;       // [kSelBuckets] offset of a wanted bucket's particles in cand, or ~0u
+    unsigned* cursor;    // [kSelBuckets]
+    unsigned* mm;        // [2] orderable min, max
+    unsigned* flag;      // [1] 1: fall back to the full sort
+    unsigned long long* cand;
+};
+
+__device__ __forceinline__ float float_from_order_bits(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+__device__ __forceinline__ int sel_bucket(float v, float vmin, float scale)
+{
+    const float t = (v - vmin) * scale;
+    return t >= (float)(kSelBuckets - 1) ? kSelBuckets - 1 : (int)t;
+}
+
+__device__ __forceinline__ void sel_range(const SelWs& w, float& vmin, float& scale)
+{
+    vmin = float_from_order_bits(w.mm[0]);
+    const float vmax = float_from_order_bits(w.mm[1]);
+    scale = vmax > vmin ? (float)kSelBuckets / (vmax - vmin) : 0.0f;
+}
+
+__global__ void sel_minmax_kernel(const float* __restrict__ x, int64_t n, SelWs w)
+{
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = float_order_bits(x[i]);
+        lo = min(lo, k);
+        hi = max(hi, k);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&w.mm[0], lo);
+        atomicMax(&w.mm[1], hi);
+    }
+}
+
+__global__ void __launch_bounds__(1024) sel_hist_kernel(const float* __restrict__ x, int64_t n, SelWs w)
+{
+    __shared__ unsigned h[kSelBuckets];
+    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x) h[b] = 0u;
+    __syncthreads();
+    float vmin, scale;
+    sel_range(w, vmin, scale);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[sel_bucket(x[i], vmin, scale)], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSelBuckets; b += blockDim.x)
+        if (h[b]) atomicAdd(&w.counts[b], h[b]);
+}
+
+// One CTA: prefix sums of the counts, the wanted buckets and their offsets in
+// cand, and the fallback flag.
+__global__ void __launch_bounds__(1024) sel_plan_kernel(const int64_t* __restrict__ ranks, int n_ranks, int64_t n,
+                                                        SelWs w)
+{
+    __shared__ unsigned part[1024];
+    __shared__ unsigned char want[kSelBuckets];
+    const int T = blockDim.x, t = threadIdx.x;
+    constexpr int per = kSelBuckets / 1024;
+    unsigned s = 0;
+    for (int k = 0; k < per; ++k) s += w.counts[t * per + k];
+    part[t] = s;
+    for (int b = t; b < kSelBuckets; b += T) want[b] = 0;
+    __syncthreads();
+    if (t == 0) {   // exclusive scan of the per-thread sums (1024 values)
+        unsigned run = 0;
+        for (int i = 0; i < T; ++i) {
+            const unsigned v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        w.starts[kSelBuckets] = run;
+    }
+    __syncthreads();
+    unsigned run = part[t];
+    for (int k = 0; k < per; ++k) {
+        w.starts[t * per + k] = run;
+        run += w.counts[t * per + k];
+    }
+    __syncthreads();
+    // the bucket of each requested rank: the last b with starts[b] <= rank
+    for (int r = t; r < n_ranks; r += T) {
+        const int64_t rk = ranks[r];
+        if (rk < 0 || rk >= n) continue;
+        int lo = 0, hi = kSelBuckets - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)w.starts[mid] <= rk) lo = mid; else hi = mid - 1;
+        }
+        want[lo] = 1;
+    }
+    __syncthreads();
+    if (t == 0) {
+        const float vmin = float_from_order_bits(w.mm[0]), vmax = float_from_order_bits(w.mm[1]);
+        unsigned fb = (isfinite(vmin) && isfinite(vmax)) ? 0u : 1u;
+        unsigned off = 0;
+        for (int b = 0; b < kSelBuckets; ++b) {
+            const unsigned c = w.counts[b];
+            if (want[b]) {
+                if (c > (unsigned)kSelCap) fb = 1u;
+                w.seg[b] = off;
+                off += c;
+            } else {
+                w.seg[b] = 0xFFFFFFFFu;
+            }
+        }
+        *w.flag = fb;
+    }
+}
+
+__global__ void sel_gather_kernel(const float* __restrict__ x, int64_t n, SelWs w)
+{
+    float vmin, scale;
+    sel_range(w, vmin, scale);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = x[i];
+        const int b = sel_bucket(v, vmin, scale);
+        const unsigned o = w.seg[b];
+        if (o != 0xFFFFFFFFu) {
+            const unsigned pos = atomicAdd(&w.cursor[b], 1u);
+            w.cand[o + pos] = ((unsigned long long)float_order_bits(v) << 32) | (unsigned long long)i;
+        }
+    }
+}
+
+// One CTA per requested rank: sort its bucket's (value, index) keys in shared
+// memory and read the rank's index.
+__global__ void __launch_bounds__(512) sel_rank_kernel(const int64_t* __restrict__ ranks, int64_t n, SelWs w,
+                                                       int64_t* __restrict__ idx)
+{
+    __shared__ unsigned long long k[kSelCap];
+    __shared__ int bucket;
+    const int64_t rk = ranks[blockIdx.x];
+    if (rk < 0 || rk >= n) {
+        if (threadIdx.x == 0) idx[blockIdx.x] = -1;   // rank out of range
+        return;
+    }
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = kSelBuckets - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)w.starts[mid] <= rk) lo = mid; else hi = mid - 1;
+        }
+        bucket = lo;
+    }
+    __syncthreads();
+    const int b = bucket;
+    const int c = (int)w.counts[b];
+    int P = 1;
+    while (P < c) P <<= 1;
+    const unsigned long long* src = w.cand + w.seg[b];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) k[i] = i < c ? src[i] : ~0ull;
+    __syncthreads();
+    for (int kk = 2; kk <= P; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = k[i], bb = k[l];
+                    if ((a > bb) == ((i & kk) == 0)) {
+                        k[i] = bb;
+                        k[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    if (threadIdx.x == 0) idx[blockIdx.x] = (int64_t)(k[rk - (int64_t)w.starts[b]] & 0xFFFFFFFFull);
 }
 
 inline int64_t next_pow2(int64_t v)
@@ -817,9 +1009,11 @@ extern "C" pr_status pr_fine_adjoint_affine(const pr_model* model, const pr_rng*
                           seed_shift);
 }
 
+static size_t sel_tables_bytes() { return align256((size_t)(4 * kSelBuckets + 8) * sizeof(unsigned)); }
+
 extern "C" size_t pr_order_statistics_workspace(int64_t n)
 {
-    return n < 1 ? 0 : align256((size_t)next_pow2(n) * sizeof(unsigned long long));
+    return n < 1 ? 0 : align256((size_t)next_pow2(n) * sizeof(unsigned long long)) + sel_tables_bytes();
 }
 
 extern "C" pr_status pr_order_statistics(const float* x, int64_t n, const int64_t* ranks, int32_t n_ranks,
@@ -831,6 +1025,37 @@ extern "C" pr_status pr_order_statistics(const float* x, int64_t n, const int64_
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t padded = next_pow2(n);
     auto* keys = static_cast<unsigned long long*>(workspace);
+    // selection first
+    {
+        unsigned* tab = reinterpret_cast<unsigned*>(static_cast<char*>(workspace) +
+                                                    align256((size_t)padded * sizeof(unsigned long long)));
+        SelWs w;
+        w.counts = tab;
+        w.starts = tab + kSelBuckets;
+        w.seg = w.starts + kSelBuckets + 1;
+        w.cursor = w.seg + kSelBuckets;
+        w.mm = w.cursor + kSelBuckets;
+        w.flag = w.mm + 2;
+        w.cand = keys;
+        PR_TRY_CUDA(cudaMemsetAsync(w.counts, 0, kSelBuckets * sizeof(unsigned), st));
+        PR_TRY_CUDA(cudaMemsetAsync(w.cursor, 0, kSelBuckets * sizeof(unsigned), st));
+        PR_TRY_CUDA(cudaMemsetAsync(w.mm, 0xFF, sizeof(unsigned), st));
+        PR_TRY_CUDA(cudaMemsetAsync(w.mm + 1, 0, sizeof(unsigned), st));
+        const int sb = (int)std::min<int64_t>((n + 1023) / 1024, 2 * (int64_t)num_sms());
+        sel_minmax_kernel<<<sb, 1024, 0, st>>>(x, n, w);
+        sel_hist_kernel<<<sb, 1024, 0, st>>>(x, n, w);
+        sel_plan_kernel<<<1, 1024, 0, st>>>(ranks, n_ranks, n, w);
+        unsigned fb = 1u;
+        PR_TRY_CUDA(cudaMemcpyAsync(&fb, w.flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        PR_TRY_CUDA(cudaStreamSynchronize(st));
+        if (fb == 0u) {
+            sel_gather_kernel<<<sb, 1024, 0, st>>>(x, n, w);
+            sel_rank_kernel<<<n_ranks, 512, 0, st>>>(ranks, n, w, index_out);
+            PR_CHECK_LAUNCH();
+            return PR_OK;
+        }
+    }
+    // full sort: bitonic network over (value, index) keys
     const int blocks = (int)std::min<int64_t>((padded + 255) / 256, 16 * (int64_t)num_sms());
     make_keys_kernel<<<blocks, 256, 0, st>>>(x, n, padded, keys);
     for (int64_t k = 2; k <= padded; k <<= 1)

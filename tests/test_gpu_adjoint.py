@@ -221,6 +221,55 @@ def test_order_statistics(L):
         assert got[-2] == -1 and got[-1] == -1
 
 
+@pytest.mark.parametrize("case", ["normal_2^20", "bimodal", "rounded_ties", "all_equal_small", "all_equal_large",
+                                  "cauchy", "with_inf_nan", "one_outlier", "ragged_tiny"])
+def test_order_statistics_selection_cases(L, case):
+    """The bucket selection and its fallback to the full sort against
+    np.lexsort (value in the total order of binary32, -0 before +0, then
+    index): a large normal ensemble with the 512
+    quantile ranks, a bimodal one, values rounded to few levels (many ties),
+    equal values (within and beyond one bucket's sort capacity), heavy tails,
+    infinities and NaN, a single far outlier, and tiny ensembles."""
+    rng = np.random.default_rng(hash(case) % (1 << 32))
+    n = 1 << 20 if case == "normal_2^20" else 100_003
+    if case in ("normal_2^20", "ragged_tiny"):
+        x = rng.normal(0, 1, n)
+    elif case == "bimodal":
+        x = np.where(rng.random(n) < 0.3, rng.normal(-1, 0.1, n), rng.normal(1.5, 0.3, n))
+    elif case == "rounded_ties":
+        x = np.round(rng.normal(0, 1, n) * 20) / 20
+    elif case == "all_equal_small":
+        n = 3000
+        x = np.full(n, 0.25)
+    elif case == "all_equal_large":
+        x = np.full(n, -1.5)
+    elif case == "cauchy":
+        x = rng.standard_cauchy(n)
+    elif case == "with_inf_nan":
+        x = rng.normal(0, 1, n)
+        x[[5, 77, 1000]] = [np.inf, -np.inf, np.nan]
+    else:   # one_outlier
+        x = rng.normal(0, 1, n)
+        x[12345] = 1e30
+    if case == "ragged_tiny":
+        n = 37
+        x = x[:n]
+    x = x.astype(np.float32)
+    p = (np.arange(512) + 0.5) / 512
+    ranks = np.unique(np.concatenate([np.ceil(p * n).astype(np.int64) - 1, [0, n - 1]]))
+    gx = torch.tensor(x, device="cuda")
+    gr = torch.tensor(ranks, dtype=torch.int64, device="cuda")
+    idx = torch.empty(gr.numel(), dtype=torch.int64, device="cuda")
+    ws = torch.empty(L.pr_order_statistics_workspace(n), dtype=torch.uint8, device="cuda")
+    L.pr_order_statistics(gx, n, gr, gr.numel(), idx, ws)
+    torch.cuda.synchronize()
+    # the total order of binary32 values (-0 before +0, NaN above +inf), then the index
+    k = x.view(np.uint32)
+    key = np.where(k & 0x80000000, ~k, k | 0x80000000)
+    order = np.lexsort((np.arange(n), key))
+    np.testing.assert_array_equal(idx.cpu().numpy(), order[ranks])
+
+
 def test_adjoint_workload_sampled_at_full_size(L, orc):
     """The adjoint workload at full size (2^20 particles, 20 slices x 1000
     steps, checkpoints every 256 steps): sampled particles' sensitivities
