@@ -512,10 +512,10 @@ adjoint_rev_kernel(AdjArgs a)
             const int64_t tl = t0 + L - 1;
             slice = (int)(tl / S);
             m = (int)(tl - (int64_t)slice * S);
-            // blocks of at most kSub steps, backwards; binary32 partial sums
-            // per block, added into the binary64 sums after it
-            for (int left = L; left > 0; left -= kSub) {
-                const int len = min(kSub, left);
+            // blocks of at most 4 kSub steps, backwards; binary32 partial sums
+            // per block (48 terms at most), added into the binary64 sums after it
+            for (int left = L; left > 0; left -= 4 * kSub) {
+                const int len = min(4 * kSub, left);
                 float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
                 if (PAIRED) {   // m is odd here: steps m and m - 1 from one block
                     for (int i = 0; i < len; i += 2) {
