@@ -42,17 +42,17 @@ import workloads  # noqa: E402
 METRIC = "fine-propagator particle-steps/s (FP32 vs FP64 GPU) and parareal iter time at W1≤1e-3"
 UNIT = "particle-steps/s"
 WORKLOAD = workloads.DOUBLE_WELL
-# Thread-instructions issued per particle-step by the binary32 fine kernel
-# (d = 1, 4 particles per thread): ncu smsp__inst_issued.sum x 32 over the
-# particle-steps of the launch, double-well workload at 2^16 particles x 9
-# slices x 1000 steps.
-INST_PER_PARTICLE_STEP = 41.42
+# Thread-instructions per particle-step of the binary32 fine kernel (d = 1,
+# 4 particles per thread): ncu smsp__inst_executed.sum x 32 over the
+# particle-steps of the launch, double-well workload at 2^16 and at 2^20
+# particles x 9 slices x 1000 steps (the same count at both sizes).
+INST_PER_PARTICLE_STEP = 41.58
 # DRAM bytes per particle per slice of that kernel, read + write (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of the 9-slice launch at 2^21
 # particles, inputs larger than L2, scaled by particle-slices to the full
 # launch); the algorithmic figure is
 # 16 B (x and y read once and written once, binary32).
-TRAFFIC_BYTES_PER_PARTICLE_SLICE = 13.73
+TRAFFIC_BYTES_PER_PARTICLE_SLICE = 13.75
 SMS = 152
 ISSUE_LANES_PER_SM_CLK = 4 * 32       # 4 sub-partitions x one 32-wide warp instruction per clock
 
