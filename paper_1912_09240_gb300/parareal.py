@@ -122,6 +122,7 @@ class PararealSolver:
             self._su = torch.cuda.Stream(self.device, priority=-1)
             self._ev_fine = [None] * nch     # fine(k, c) of the latest enqueued iteration
             self._ev_upd = [None] * nch      # sweep(k, c) of the latest enqueued iteration
+        self._ev_zero = []                   # zeroth sweep, chunk by chunk (pipelined mode)
         self._pending = False
         self.graph = bool(graph)
         self._swaps = 0                  # iterations since construction (buffer binding parity)
@@ -148,7 +149,7 @@ class PararealSolver:
         """Make the caller's stream wait for every enqueued kernel of the solver."""
         if self.chunk and self._pending:
             s = self._s()
-            for ev in self._ev_upd + self._ev_fine:
+            for ev in self._ev_upd + self._ev_fine + self._ev_zero:
                 if ev is not None:
                     s.wait_event(ev)
             self._pending = False
@@ -195,9 +196,28 @@ class PararealSolver:
         else:
             L.pr_restrict(self.precision, self.x0, self.n, 1, self.grid, self.counts0, self.cdf0, stream=s)
         self.prior0.copy_(self.cdf0.expand(self.K, -1))
-        L.pr_parareal_update(self.coarse, L.PR_ITER_NONE, self.qmode, self.K, self.cdf0, None, None,
-                             self._rho, self._status[0], stream=s)
         self.k = 0
+        if self.chunk:
+            # the zeroth sweep chunk by chunk on the sweep stream: the first
+            # iteration's fine chunk c waits only for the sweep up to its
+            # slices, so the rest of the sweep runs beside the fine work
+            K, C = self.K, self.chunk
+            ready = torch.cuda.Event()
+            ready.record(s)
+            self._su.wait_event(ready)
+            self._ev_zero = []
+            for c in range(len(self._ev_upd)):
+                a, b = c * C, min(K, (c + 1) * C)
+                state = self.cdf0 if a == 0 else self._rho[a]
+                L.pr_parareal_update(self.coarse, L.PR_ITER_NONE, self.qmode, b - a, state, None, None,
+                                     self._rho[a:b + 1], self._status[c], stream=self._su)
+                ev = torch.cuda.Event()
+                ev.record(self._su)
+                self._ev_zero.append(ev)
+            self._pending = True
+        else:
+            L.pr_parareal_update(self.coarse, L.PR_ITER_NONE, self.qmode, self.K, self.cdf0, None, None,
+                                 self._rho, self._status[0], stream=s)
         if self.chunk:
             self._ev_fine = [None] * len(self._ev_fine)
             self._ev_upd = [None] * len(self._ev_upd)
@@ -336,7 +356,8 @@ class PararealSolver:
             a, b = c * C, min(K, (c + 1) * C)
             sf = self._sf[c % 2]
             if not in_graph:   # a graph launch starts after the previous iteration has ended
-                for ev in (self._ev_upd[c], self._ev_fine[c + 1] if c + 1 < nch else None):
+                for ev in (self._ev_upd[c], self._ev_fine[c + 1] if c + 1 < nch else None,
+                           self._ev_zero[c] if first and self._ev_zero else None):
                     if ev is not None:
                         sf.wait_event(ev)
             if carry and a <= self.k - 1 < b:
