@@ -74,6 +74,34 @@ def test_invalid_arguments_rejected_on_host(L):
     assert lib.pr_rng_words(ctypes.byref(r), ctypes.c_void_p(0x1004), 1, fake, None) == L.PR_ERR_INVALID_ARG
 
 
+def test_chemical_and_transfer_arguments_rejected_on_host(L):
+    """Host-side checks of the chemical kinds, the L2 distance and the
+    transfer calls: they return before any CUDA call."""
+    lib = L.lib()
+    r = L.Rng().c()
+    g = L.Grid(16, 0.0, 16.0).c()
+    fake = ctypes.c_void_p(0x1000)
+    rates = (60.0, 1.0, 4.8e-3, 0.666e-5, 0.833, 1.0)
+    for bad in [L.Model(L.PR_MODEL_CHEM, 2, rates=rates),                                   # one fast variable only
+                L.Model(L.PR_MODEL_CHEM, 1, rates=(60.0, -1.0, 4.8e-3, 0.666e-5, 0.833, 1.0)),   # negative rate
+                L.Model(L.PR_MODEL_CHEM, 1, rates=(60.0, 1.0, float("inf"), 0.666e-5, 0.833, 1.0)),
+                L.Model(L.PR_MODEL_CHEM_PRINTED, 1, eps=0.0, rates=rates)]:
+        m = bad.c()
+        assert lib.pr_fine_propagate(ctypes.byref(m), 0, ctypes.byref(r), fake, fake, 0, fake, fake, 10, 0, 1, 1,
+                                     1e-3, None, None, None, None, None, None, None, None) == L.PR_ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    for bad, grid in [(L.Model(L.PR_MODEL_CHEM, 1, rates=(60.0, 1.0, 4.8e-3, 0.666e-5, 0.0, 1.0)), g),   # k4 = 0
+                      (L.Model(L.PR_MODEL_CHEM, 1, rates=rates), L.Grid(16, -1.0, 15.0).c())]:       # x_lo < 0
+        m = bad.c()
+        assert lib.pr_coarse_create(ctypes.byref(m), ctypes.byref(grid), 2.0, ctypes.byref(h), None) == \
+            L.PR_ERR_INVALID_ARG
+    assert lib.pr_l2_density(ctypes.byref(g), 0, fake, fake, fake, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_l2_density(ctypes.byref(g), 1, ctypes.c_void_p(0x1004), fake, fake, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_copy_to_device(None, fake, 8, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_copy_to_host(fake, None, 8, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_copy_to_device(None, None, 0, None) == L.PR_OK    # nothing to copy
+
+
 def test_python_binding_raises(L):
     with pytest.raises(L.PrError) as e:
         L._check("pr_x", L.PR_ERR_NUMERIC)

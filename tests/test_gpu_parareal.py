@@ -171,6 +171,40 @@ def test_pipelined_driver_equals_sequential(L, chunk):
     s.close()
 
 
+@pytest.mark.parametrize("chunk", [0, 3])
+def test_host_buffer_path_equals_device_path(L, chunk):
+    """set_initial_host (X_0, Y_0 copied from page-locked host memory by
+    pr_copy_to_device) and rho_to_host (pr_copy_to_host, then
+    pr_stream_synchronize) give the device path's macroscopic states bit for
+    bit, after the zeroth iteration (in the pipelined schedule, the zeroth
+    sweep chunk by chunk) and after two iterations."""
+    w = workloads.DOUBLE_WELL.scaled(N=3001, K=10, T=0.1, dt=1e-3, bins=128)
+    ref, x0, y0 = _solver(L, w, L.PR_F32)
+    rho_ref = [ref.rho.cpu().numpy().copy()]
+    for _ in range(2):
+        ref.iterate()
+        rho_ref.append(ref.rho.cpu().numpy().copy())
+    ref.close()
+    from paper_1912_09240_gb300.parareal import PararealSolver
+    model = L.Model(w.kind, w.fast_dim, w.lam, w.beta, w.eps, w.tau_x)
+    s = PararealSolver(model, L.Grid(w.bins, w.lo, w.hi), w.N, w.K, w.steps, w.step_dt, precision=L.PR_F32,
+                       rng=L.Rng(w.seed, 0), chunk=chunk)
+    xh = torch.tensor(x0, dtype=torch.float32).pin_memory()
+    yh = torch.tensor(y0, dtype=torch.float32).pin_memory()
+    out = torch.empty(w.K + 1, w.bins + 1, dtype=torch.float64).pin_memory()
+    for run in range(2):
+        s.set_initial_host(xh, yh)
+        s.rho_to_host(out)
+        L.pr_stream_synchronize()
+        np.testing.assert_array_equal(out.numpy(), rho_ref[0])
+        for k in range(2):
+            s.iterate()
+            s.rho_to_host(out)
+            L.pr_stream_synchronize()
+            np.testing.assert_array_equal(out.numpy(), rho_ref[k + 1])
+    s.close()
+
+
 @pytest.mark.parametrize("chunk", [0, 2])
 def test_exactness_theorem_fast16_on_gpu(L, chunk):
     """The 16-dimensional fast space (coupling lambda mean(y)): iterate k equals
