@@ -566,7 +566,9 @@ restrict_kernel(const T* __restrict__ x, int64_t n, GridDev g, float lo_f, float
 // standalone matching
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(1024)
+// two CTAs of 1024 threads per SM (32 registers): the gathers of the
+// matching table need every warp the SM can hold
+__global__ void __launch_bounds__(1024, 2)
 match_f32_kernel(const float* __restrict__ xp, float* __restrict__ xo, int64_t n, GridDev g,
                  float lo_f, float inv_h_f, const double* __restrict__ cp,
                  const double* __restrict__ ct, int64_t per_block)

@@ -26,10 +26,12 @@ namespace pr {
 //            m = thr[j+1] (two pieces: they meet there at fs; one piece: the
 //            line of the piece reaches it at fs >= 1), the particle's target
 //            bin jm - 1 below fs and jm from fs on (jm the index of the edge
-//            m), so that such a particle reads one 16-byte record.  Otherwise
-//            b1 = -1 and m holds the bits of start | end << 16: the pieces
-//            [start, end) of the bin in the arrays below (start == end:
-//            identity; at most 2I+1 <= 8193 pieces).
+//            m), so that such a particle reads one 16-byte record; b2 is
+//            stored negated where an image could leave those bins by
+//            rounding (the general path then checks it).  Otherwise b1 = -2
+//            (identity) or -1 and m holds the bits of start | end << 16: the
+//            pieces [start, end) of the bin in the arrays below (at most
+//            2I+1 <= 8193 pieces).
 //   piece  : float4 [2I+1]  (alpha, beta, thr[j], thr[j+1]) of target bin j:
 //            on prior bin i the map is X = clamp(alpha + beta f, thr[j], thr[j+1])
 //            for the first piece of the bin whose f_end >= f (or its last piece)
@@ -267,20 +269,39 @@ __device__ inline void build_match_table(const GridDev& g, const float* thr, Mat
     __syncthreads();
     for (int i = threadIdx.x; i < I; i += blockDim.x) {
         const int k0 = m.pstart[i], k1 = m.pstart[i + 1];
-        float4 r = make_float4(__uint_as_float((uint32_t)k0 | ((uint32_t)k1 << 16)), 0.0f, -1.0f, 0.0f);
+        // general (-1) or identity (-2) unless one of the anchored forms applies
+        float4 r = make_float4(__uint_as_float((uint32_t)k0 | ((uint32_t)k1 << 16)), 0.0f,
+                               k0 == k1 ? -2.0f : -1.0f, 0.0f);
+        float lo_j = 0.0f, hi_j = 0.0f;   // outer thresholds of the record's target bins
         if (k1 == k0 + 1) {
             // one piece X = alpha + beta f on [thr_j, thr_{j+1}]: anchored at
             // the right edge, reached at fs = (thr_{j+1} - alpha) / beta
             const float4 pc = m.piece[k0];
             if (pc.y > 0.0f && pc.y < 1e30f) {
                 const float fs = (float)(((double)pc.w - (double)pc.x) / (double)pc.y);
-                if (fs >= 1.0f && fs < 1e30f) r = make_float4(pc.w, fs, pc.y, pc.y);
+                if (fs >= 1.0f && fs < 1e30f) {
+                    r = make_float4(pc.w, fs, pc.y, pc.y);
+                    lo_j = pc.z;
+                    hi_j = pc.w;
+                }
             }
         } else if (k1 == k0 + 2) {
             // two pieces meeting at the edge thr_{j+1} = hi of the first = lo of the second
             const float4 p1 = m.piece[k0], p2 = m.piece[k0 + 1];
-            if (p1.w == p2.z && p1.y >= 0.0f && p2.y >= 0.0f && p1.y < 1e30f && p2.y < 1e30f)
+            if (p1.w == p2.z && p1.y > 0.0f && p2.y > 0.0f && p1.y < 1e30f && p2.y < 1e30f) {
                 r = make_float4(p1.w, m.fend[k0], p1.y, p2.y);
+                lo_j = p1.z;
+                hi_j = p2.w;
+            }
+        }
+        if (r.z >= 0.0f) {
+            // Safe when every image the fast path can compute lies in its
+            // target bins: the fast path's f lies in [0, 1] and its image
+            // fmaf(b, f - fs, m) is monotone in f, so the images at f = 0
+            // and f = 1, taken with the same operations, bound them all.
+            const float x0 = fmaf(r.z, 0.0f - r.y, r.x);
+            const float x1 = fmaf(1.0f >= r.y ? r.w : r.z, 1.0f - r.y, r.x);
+            if (!(x0 >= lo_j && x1 <= hi_j)) r.w = -r.w;   // unsafe: the general path checks
         }
         m.rec[i] = r;
     }
@@ -288,14 +309,13 @@ __device__ inline void build_match_table(const GridDev& g, const float* thr, Mat
 }
 
 // Map one binary32 particle through the table.
-// The bin fraction f = (x - e_i)/h takes the left edge as lo + i h in
-// binary32 (one fma, within half an ulp of x's magnitude of the edge).  On
-// a bin with one piece, or two pieces meeting at a target edge, the particle
-// reads a single 16-byte record; its image is checked against its target bin
-// by the fast binning (no table read) and clamped into it by the bin's
-// thresholds only where that check does not confirm it (near an edge).
-__device__ __forceinline__ float match_one_f32(const MatchSmem& m, const float* __restrict__ thr, const BinF32& bf,
-                                               float x)
+// General path: any particle, any bin.  The bin fraction f = (x - e_i)/h
+// takes the left edge as lo + i h in binary32 (one fma, within half an ulp
+// of x's magnitude of the edge).  An anchored record's image is checked
+// against its target bin by the fast binning and clamped into it by the
+// bin's thresholds where that check does not confirm it.
+__device__ __forceinline__ float match_one_f32_general(const MatchSmem& m, const float* __restrict__ thr,
+                                                       const BinF32& bf, float x)
 {
     float fi;
     const int i = bin_fast_f32(bf, thr, x, fi);
@@ -309,7 +329,7 @@ __device__ __forceinline__ float match_one_f32(const MatchSmem& m, const float* 
     float xn;
     if (r.z >= 0.0f) {
         const bool second = f >= r.y;
-        xn = fmaf(second ? r.w : r.z, f - r.y, r.x);
+        xn = fmaf(second ? fabsf(r.w) : r.z, f - r.y, r.x);
         const int jm = __float2int_rn((r.x - bf.lo) * bf.inv_h);
         const int j = min(second ? jm : jm - 1, bf.bins - 1);
         if (bin_try_f32(bf, xn) != j) xn = fminf(fmaxf(xn, thr[j]), thr[j + 1]);
@@ -325,6 +345,30 @@ __device__ __forceinline__ float match_one_f32(const MatchSmem& m, const float* 
     if (below) return x + (xn - bf.thr0);
     if (above) return x + (xn - bf.thrI);
     return xn;
+}
+
+// Map one binary32 particle through the table.  Fast path (most particles:
+// inside the grid, away from their bin's edges by the binning's error
+// margin, on an identity bin or a safe anchored record): the bin and the
+// fraction f = d + 1/2 come from one rounding (d the signed distance to the
+// bin's middle, in bins), one 16-byte record gives the image, and no
+// threshold is read.  Everything else takes the general path.
+__device__ __forceinline__ float match_one_f32(const MatchSmem& m, const float* __restrict__ thr, const BinF32& bf,
+                                               float x)
+{
+    const float g = fmaf(x, bf.inv_h, bf.c);
+    const float t = g + 12582912.0f;
+    const float d = g - (t - 12582912.0f);
+    const int i = __float_as_int(t) - 0x4B400000;
+    if ((unsigned)i < (unsigned)bf.bins && fabsf(d) <= bf.half_m) {
+        const float4 r = m.rec[i];
+        if (r.z >= 0.0f && r.w >= 0.0f) {
+            const float f = d + 0.5f;
+            return fmaf(f >= r.y ? r.w : r.z, f - r.y, r.x);
+        }
+        if (r.z == -2.0f) return x;   // identity on this bin
+    }
+    return match_one_f32_general(m, thr, bf, x);
 }
 
 // Binary64: the map evaluated per particle, in the same operations as the
