@@ -187,8 +187,10 @@ pr_status pr_rng_words(const pr_rng* rng, const uint32_t* ctr, int64_t n, uint32
 
 /*
  * Tuning knob of the binary32 fine propagator with fast_dim = 1: particles
- * carried per thread (1, 2 or 4; other values select 4, the default).
- * Process-wide.  Results do not depend on it.
+ * carried per thread.  1, 2 or 4 force that value; any other value (0, the
+ * default) chooses per launch: 4, or 2 or 1 where a launch over
+ * n x n_slices particles would otherwise have fewer threads than the device
+ * holds resident (2048 per SM).  Process-wide.  Results do not depend on it.
  */
 void pr_set_particles_per_thread(int32_t ppt);
 

@@ -736,13 +736,28 @@ static pr_status launch_f32_multi(int D, const FineArgs& a, FineSmemOffsets so, 
     }
 }
 
-static int g_ppt = 4;   // particles per thread of the binary32 d = 1 kernel
+static int g_ppt = 0;   // particles per thread of the binary32 d = 1 kernel (0: per launch)
+
+// Particles per thread of a binary32 d = 1 launch over n x n_slices
+// particles: 4 unless the launch would then have fewer threads than the
+// device holds resident (2048 per SM), then 2, else 1, so that a small
+// launch still fills the SMs; a value forced by pr_set_particles_per_thread
+// wins.
+static int pick_ppt(int64_t n, int n_slices)
+{
+    if (g_ppt) return g_ppt;
+    const int64_t resident = (int64_t)num_sms() * 2048;
+    const int64_t total = n * (int64_t)n_slices;
+    if (total / 4 >= resident) return 4;
+    if (total / 2 >= resident) return 2;
+    return 1;
+}
 
 }  // namespace pr
 
 using namespace pr;
 
-extern "C" void pr_set_particles_per_thread(int32_t ppt) { g_ppt = (ppt == 1 || ppt == 2) ? ppt : 4; }
+extern "C" void pr_set_particles_per_thread(int32_t ppt) { g_ppt = (ppt == 1 || ppt == 2 || ppt == 4) ? ppt : 0; }
 
 extern "C" void pr_set_tiles_per_cta(int32_t tiles) { g_tiles_max = tiles < 1 ? 1 : (tiles > 64 ? 64 : tiles); }
 
@@ -841,7 +856,7 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
         if (model->kind == PR_MODEL_DW_MULTI && D > 1) {
             rc = launch_f32_multi(D, a, so, flags, L.total, n_slices, st);
         } else if (is_chem(model->kind)) {
-            switch (g_ppt) {
+            switch (pick_ppt(n, n_slices)) {
             case 2: rc = launch_f32_d1<PR_MODEL_CHEM, 2>(a, so, flags, L.total, n_slices, st); break;
             case 4: rc = launch_f32_d1<PR_MODEL_CHEM, 4>(a, so, flags, L.total, n_slices, st); break;
             default: rc = launch_f32_d1<PR_MODEL_CHEM, 1>(a, so, flags, L.total, n_slices, st);
@@ -849,7 +864,7 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
         } else {
             // (the multi-component family with one component is the double well)
             const bool ou = model->kind == PR_MODEL_OU;
-            switch (g_ppt) {
+            switch (pick_ppt(n, n_slices)) {
             case 2:
                 rc = ou ? launch_f32_d1<PR_MODEL_OU, 2>(a, so, flags, L.total, n_slices, st)
                         : launch_f32_d1<PR_MODEL_DOUBLE_WELL, 2>(a, so, flags, L.total, n_slices, st);

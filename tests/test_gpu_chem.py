@@ -71,7 +71,7 @@ def test_fine_f32_matches_oracle(L, orc, kind, ppt):
         L.pr_fine_propagate(gm, L.PR_F32, L.Rng(0), gx, gy, False, ox_, oy_, n, 11, 2, steps, 1e-3)
         torch.cuda.synchronize()
     finally:
-        L.pr_set_particles_per_thread(4)
+        L.pr_set_particles_per_thread(0)
     ox, oy = orc.fine_propagate(om, 0, x0.astype(np.float64), y0.astype(np.float64), 11, steps, 1e-3)
     assert np.all(np.abs(ox_.cpu().numpy() - ox) <= 2e-3 * np.maximum(np.abs(ox), 1.0))
     assert np.all(np.abs(oy_.cpu().numpy() - oy) <= 2e-3 * np.maximum(np.abs(oy), 1.0))

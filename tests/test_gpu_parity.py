@@ -15,6 +15,8 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import workloads
+
 pytestmark = pytest.mark.gpu
 
 
@@ -118,7 +120,7 @@ def test_fine_f32_matches_oracle(L, orc, mi, ppt):
         L.pr_fine_propagate(gm, L.PR_F32, L.Rng(0), gx, gy, False, ox_, oy_, n, slice_begin, n_slices, steps, dt)
         torch.cuda.synchronize()
     finally:
-        L.pr_set_particles_per_thread(4)
+        L.pr_set_particles_per_thread(0)
     ox, oy = orc.fine_propagate(om, 0, x0.astype(np.float64), y0.astype(np.float64), slice_begin, steps, dt)
     gxn, gyn = ox_.cpu().numpy(), oy_.cpu().numpy()
     assert np.all(np.abs(gxn - ox) <= 2e-3 * np.maximum(np.abs(ox), 1.0))
@@ -552,6 +554,55 @@ def test_fused_matching_equals_standalone(L, orc, prec, bins, kind, d):
     assert torch.equal(xf, xs) and torch.equal(yf, ys)
     assert torch.equal(cs, cs_ref) and torch.equal(cds, cds_ref)
     assert torch.equal(ce, ce_ref) and torch.equal(cde, cde_ref)
+
+
+@pytest.mark.parametrize("kind,n,S", [(1, 5003, 2), (1, 100000, 5), (4, 100000, 5), (1, 200003, 4),
+                                      (1, 1 << 20, 2)])
+def test_particles_per_thread_bit_identical(L, orc, kind, n, S):
+    """The binary32 d = 1 propagator gives the same bits whatever number of
+    particles each thread carries: 1, 2 and 4 forced, and the per-launch
+    choice (0), whose value changes across these sizes (on 152 SMs: 1 up to
+    5e5 particles, 2 at 8e5, 4 at 2^21), with the matching fused in and both
+    restrictions."""
+    rng = np.random.default_rng(n + kind)
+    if kind == 4:
+        bins, lo, hi = 600, 0.0, 600.0
+        m = L.Model(4, 1, 0.0, 1.0, 1e-2, 25.0, tuple(workloads.CHEM_RATES))
+        px = rng.lognormal(np.log(98.0), 0.2, (S, n))
+        tgt = rng.lognormal(np.log(101.0), 0.2, (S, 2 * n))
+        y0 = rng.lognormal(np.log(98.0), 0.2, (S, n))
+        dt, steps = 1e-3, 40
+    else:
+        bins, lo, hi = 512, -3.0, 3.0
+        m = L.Model(kind, 1, 0.5, 3.0, 1e-2)
+        px = rng.normal(-0.3, 0.8, (S, n))
+        tgt = rng.normal(0.4, 0.6, (S, 2 * n))
+        y0 = rng.normal(0.0, 1.0, (S, n))
+        dt, steps = 1e-4, 30
+    og = orc.Grid(bins, lo, hi)
+    px = px.astype(np.float32)
+    _, cp = orc.restrict(px.astype(np.float64), og)
+    _, ct = orc.restrict(tgt, og)
+    g = L.Grid(bins, lo, hi)
+    x, y = _t(px), _t(y0.astype(np.float32))
+    cpt, ctt = _t(cp), _t(ct)
+    outs = []
+    try:
+        for ppt in (1, 2, 4, 0):
+            L.pr_set_particles_per_thread(ppt)
+            xf, yf = torch.empty_like(x), torch.empty_like(y)
+            cs, ce = (torch.empty(S, bins, dtype=torch.int32, device=DEV) for _ in range(2))
+            cds, cde = (torch.empty(S, bins + 1, dtype=torch.float64, device=DEV) for _ in range(2))
+            L.pr_fine_propagate(m, L.PR_F32, L.Rng(9), x, y, False, xf, yf, n, 1, S, steps, dt, grid=g,
+                                cdf_prior=cpt, cdf_target=ctt, counts_start=cs, cdf_start=cds, counts_end=ce,
+                                cdf_end=cde)
+            outs.append((xf, yf, cs, cds, ce, cde))
+        torch.cuda.synchronize()
+    finally:
+        L.pr_set_particles_per_thread(0)
+    assert torch.isfinite(outs[0][0]).all()
+    for o in outs[1:]:
+        assert all(torch.equal(a, b) for a, b in zip(outs[0], o))
 
 
 @pytest.mark.parametrize("bins", [1, 2, 3])
