@@ -157,8 +157,12 @@ const char* pr_version(void);
  *   cdf_prior, cdf_target (device, [n_slices][bins+1]) or both NULL: fused
  *                matching (pr_match) applied to the start state first; its
  *                table shares the CTA's shared memory with the histograms
- *                (about 76 bins bytes in binary32, 44 bins in binary64), and a
- *                grid beyond the device's limit returns PR_ERR_UNSUPPORTED.
+ *                (about 76 bins bytes in binary32, 44 bins in binary64).  In
+ *                binary32 on a grid whose table does not fit (more than
+ *                about 3050 bins on GB300) the call runs the same steps in
+ *                turn: pr_match into x_out, the restriction of the matched
+ *                states, y copied to y_out, the propagation in place; every
+ *                grid up to 4096 bins is served in both precisions.
  *   counts_start, cdf_start (device, [n_slices][bins], [n_slices][bins+1]) or
  *                NULL: restriction (pr_restrict) of the start state after the
  *                matching.  cdf_start needs counts_start.
@@ -227,10 +231,11 @@ pr_status pr_counts_to_cdf(const uint32_t* counts, int64_t n, int32_t n_slices, 
  *   x_prior (device) [n_slices][n]; x_out (device) [n_slices][n], may alias x_prior
  *   cdf_prior, cdf_target (device) [n_slices][bins+1]
  * Each CTA holds the map's table in shared memory: about 76 bins bytes in
- * binary32 and 32 bins bytes in binary64.  A grid whose table exceeds the
- * shared memory one CTA can have (227 KB on GB300: about 3000 bins in
- * binary32; binary64 covers every grid up to 4096 bins) returns
- * PR_ERR_UNSUPPORTED before any launch.
+ * binary32 and 32 bins bytes in binary64.  In binary32 on a grid whose table
+ * exceeds the shared memory one CTA can have (227 KB on GB300: about 3050
+ * bins), each particle takes the binary64 map and its image is rounded to
+ * binary32 (bound by the FP64 pipe); binary64 keeps no binary32 table and
+ * covers every grid up to 4096 bins.
  */
 pr_status pr_match(pr_precision precision, const void* x_prior, void* x_out, int64_t n,
                    int32_t n_slices, const pr_grid* grid,

@@ -633,6 +633,28 @@ match_f64_kernel(const double* __restrict__ xp, double* __restrict__ xo, int64_t
     for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) os[p] = match_one_f64(ms, g, xs[p]);
 }
 
+// Binary32 matching on grids whose binary32 table does not fit one CTA's
+// shared memory: the binary64 map of each widened particle (the same
+// operations as match_f64_kernel), its image rounded to binary32.  Bound by
+// the FP64 pipe; it serves only grids of more than about 3050 bins.
+// `in_stride` = 0 maps one input ensemble into every slice.
+__global__ void __launch_bounds__(256)
+match_f32_wide_kernel(const float* __restrict__ xp, float* __restrict__ xo, int64_t n, int64_t in_stride,
+                      GridDev g, const double* __restrict__ cp, const double* __restrict__ ct, int64_t per_block)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int bins = g.bins;
+    MatchSmem ms = carve_match_smem(smem, bins);
+    const int s = blockIdx.y;
+    build_match_index(g, cp + (size_t)s * (bins + 1), ct + (size_t)s * (bins + 1), ms);
+    const int64_t b = (int64_t)blockIdx.x * per_block;
+    const int64_t e = min(n, b + per_block);
+    const float* xs = xp + (int64_t)s * in_stride;
+    float* os = xo + (int64_t)s * n;
+    for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x)
+        os[p] = __double2float_rn(match_one_f64(ms, g, (double)xs[p]));
+}
+
 // raw Philox blocks for caller-given counters
 __global__ void rng_words_kernel(const uint4* __restrict__ ctr, int64_t n, uint32_t k0, uint32_t k1,
                                  uint4* __restrict__ out)
@@ -761,6 +783,21 @@ extern "C" void pr_set_particles_per_thread(int32_t ppt) { g_ppt = (ppt == 1 || 
 
 extern "C" void pr_set_tiles_per_cta(int32_t tiles) { g_tiles_max = tiles < 1 ? 1 : (tiles > 64 ? 64 : tiles); }
 
+// The wide binary32 matching of n_slices slices (see match_f32_wide_kernel).
+static pr_status launch_match_f32_wide(const float* xp, float* xo, int64_t n, int64_t in_stride, int n_slices,
+                                       const GridDev& g, const double* cp, const double* ct, cudaStream_t st)
+{
+    const size_t smem = match_smem_bytes(g.bins);
+    if (smem > (size_t)smem_optin_max()) return PR_ERR_UNSUPPORTED;
+    const int64_t per_block = stream_range(n, n_slices, 4096, 8);
+    const int64_t blocks_per_slice = (n + per_block - 1) / per_block;
+    PR_TRY_CUDA(set_smem(match_f32_wide_kernel, smem));
+    match_f32_wide_kernel<<<dim3((unsigned)blocks_per_slice, (unsigned)n_slices), 256, smem, st>>>(
+        xp, xo, n, in_stride, g, cp, ct, per_block);
+    PR_CHECK_LAUNCH();
+    return PR_OK;
+}
+
 extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision precision, const pr_rng* rng,
                                        const void* x_in, const void* y_in, int32_t broadcast_input,
                                        void* x_out, void* y_out, int64_t n, int32_t slice_begin,
@@ -848,7 +885,32 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
     if (counts_end) PR_TRY_CUDA(cudaMemsetAsync(counts_end, 0, (size_t)n_slices * bins * 4, st));
 
     const FineSmem L = fine_smem_layout(bins, any_grid, do_match, precision == PR_F32);
-    if (L.total > (size_t)smem_optin_max()) return PR_ERR_UNSUPPORTED;   // the fused matching table
+    if (L.total > (size_t)smem_optin_max()) {
+        if (precision != PR_F32 || !do_match) return PR_ERR_UNSUPPORTED;
+        // Binary32 on a grid whose matching table does not fit beside the
+        // histograms: the same steps in turn.  The start states are matched
+        // into x_out by the wide matching, restricted there, and propagated
+        // in place (y brought to y_out first).
+        const size_t ybytes = (size_t)D * n * sizeof(float);
+        if (y_in != y_out) {
+            if (broadcast_input) {
+                for (int s = 0; s < n_slices; ++s)
+                    PR_TRY_CUDA(cudaMemcpyAsync(static_cast<char*>(y_out) + (size_t)s * ybytes, y_in, ybytes,
+                                                cudaMemcpyDeviceToDevice, st));
+            } else {
+                PR_TRY_CUDA(cudaMemcpyAsync(y_out, y_in, ybytes * n_slices, cudaMemcpyDeviceToDevice, st));
+            }
+        }
+        const pr_status m = launch_match_f32_wide(static_cast<const float*>(x_in), static_cast<float*>(x_out), n,
+                                                  broadcast_input ? 0 : n, n_slices, a.g, cdf_prior, cdf_target, st);
+        if (m != PR_OK) return m;
+        if (counts_start) {
+            const pr_status r = pr_restrict(PR_F32, x_out, n, n_slices, grid, counts_start, cdf_start, stream);
+            if (r != PR_OK) return r;
+        }
+        return pr_fine_propagate(model, precision, rng, x_out, y_out, 0, x_out, y_out, n, slice_begin, n_slices,
+                                 steps, dt, grid, nullptr, nullptr, nullptr, nullptr, counts_end, cdf_end, stream);
+    }
     FineSmemOffsets so{(unsigned)L.thr, (unsigned)L.hs, (unsigned)L.he, (unsigned)L.match};
     const int flags = (any_grid ? 1 : 0) | (do_match ? 2 : 0) | (counts_start ? 4 : 0) | (counts_end ? 8 : 0);
     pr_status rc = PR_OK;
@@ -991,9 +1053,13 @@ extern "C" pr_status pr_match(pr_precision precision, const void* x_prior, void*
     const int64_t per_block = stream_range(n, n_slices, 16384, 2);
     const int64_t blocks_per_slice = (n + per_block - 1) / per_block;
     dim3 gr((unsigned)blocks_per_slice, (unsigned)n_slices);
-    // the per-CTA table must fit in shared memory (PR_ERR_UNSUPPORTED beyond)
+    // the per-CTA binary32 table must fit in shared memory; beyond, the wide
+    // matching (binary64 map per particle, rounded to binary32)
     const size_t smem = precision == PR_F32 ? align16((size_t)(bins + 1) * 4) + match_smem_bytes_f32(bins)
                                             : match_smem_bytes(bins);
+    if (precision == PR_F32 && smem > (size_t)smem_optin_max())
+        return launch_match_f32_wide(static_cast<const float*>(x_prior), static_cast<float*>(x_out), n, n, n_slices,
+                                     g, cdf_prior, cdf_target, st);
     if (smem > (size_t)smem_optin_max()) return PR_ERR_UNSUPPORTED;
     if (precision == PR_F32) {
         PR_TRY_CUDA(set_smem(match_f32_kernel, smem));

@@ -485,35 +485,97 @@ def test_update_cluster_sizes_agree(L, bins):
         L.pr_coarse_destroy(h)
 
 
-def test_matching_table_beyond_shared_memory_is_unsupported(L):
-    """A grid whose binary32 matching table does not fit one CTA's shared
-    memory (4096 bins) is refused with PR_ERR_UNSUPPORTED, standalone and
-    fused into the fine propagator; the restriction alone still runs at 4096
-    bins.  (The binary64 matching keeps no table and covers 4096 bins:
-    test_match_f64_bit_exact, test_fused_matching_equals_standalone.)"""
-    bins, n = 4096, 1000
-    grid = L.Grid(bins, -3.0, 3.0)
-    cdf = torch.linspace(0.0, 1.0, bins + 1, dtype=torch.float64, device=DEV).reshape(1, -1)
-    for prec, dt in ((L.PR_F32, torch.float32),):
-        x = torch.zeros(1, n, dtype=dt, device=DEV)
-        y = torch.zeros(1, 1, n, dtype=dt, device=DEV)
-        out = torch.empty_like(x)
-        with pytest.raises(L.PrError) as e:
-            L.pr_match(prec, x, out, n, 1, grid, cdf, cdf)
-        assert e.value.code == L.PR_ERR_UNSUPPORTED
-        m = L.Model(L.PR_MODEL_OU, 1, 1.0, 1.0, 0.1)
-        with pytest.raises(L.PrError) as e:
-            L.pr_fine_propagate(m, prec, L.Rng(0), x, y, False, out, y.clone(), n, 0, 1, 4, 1e-3, grid=grid,
-                                cdf_prior=cdf, cdf_target=cdf)
-        assert e.value.code == L.PR_ERR_UNSUPPORTED
-        counts = torch.empty(1, bins, dtype=torch.int32, device=DEV)
-        L.pr_fine_propagate(m, prec, L.Rng(0), x, y, False, out, y.clone(), n, 0, 1, 4, 1e-3, grid=grid,
-                            counts_end=counts)
-        torch.cuda.synchronize()
-        assert int(counts.sum().item()) == n
+@pytest.mark.parametrize("bins", [3100, 4096])
+def test_match_f32_beyond_table_limit(L, orc, bins):
+    """Binary32 matching on grids whose binary32 table does not fit one
+    CTA's shared memory: each particle takes the binary64 map (bit-exact
+    with the oracle's, test_match_f64_bit_exact), so the result is the
+    oracle's image rounded to binary32, bit for bit, on ragged slices with
+    edge points and escapees; in place too, and identity on a slice whose
+    prior and target agree."""
+    og = orc.Grid(bins, -3.0, 3.0)
+    rng = np.random.default_rng(bins)
+    n, S = 30_001, 3
+    xs, cps, cts = [], [], []
+    for s_ in range(S):
+        x, _, ct = _cdf_pair(orc, og, rng, n)
+        x[:8] = [-4.0, 4.0, -3.0, 3.0, og.edges()[5], -1e9, 1e9, 0.0]
+        x32 = x.astype(np.float32)
+        _, cp = orc.restrict(x32.astype(np.float64)[None], og)
+        xs.append(x32)
+        cps.append(cp[0])
+        cts.append(ct)
+    x32, cp, ct = np.stack(xs), np.stack(cps), np.stack(cts)
+    ct[1] = cp[1]
+    want = orc.match(x32.astype(np.float64), og, cp, ct).astype(np.float32)
+    np.testing.assert_array_equal(want[1], x32[1])
+    g = L.Grid(bins, -3.0, 3.0)
+    out = torch.empty(S, n, dtype=torch.float32, device=DEV)
+    L.pr_match(L.PR_F32, _t(x32), out, n, S, g, _t(cp), _t(ct))
+    inplace = _t(x32)
+    L.pr_match(L.PR_F32, inplace, inplace, n, S, g, _t(cp), _t(ct))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+    np.testing.assert_array_equal(inplace.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("broadcast", [False, True])
+@pytest.mark.parametrize("kind,d", [(1, 1), (2, 3)])
+def test_fused_matching_beyond_table_limit(L, orc, broadcast, kind, d):
+    """pr_fine_propagate in binary32 with matching on a 4096-bin grid (its
+    table does not fit beside the histograms): the call equals pr_match,
+    pr_restrict and pr_fine_propagate without matching in turn, bit for bit,
+    with a broadcast start ensemble and out of place, or in place; the
+    propagated states agree with the oracle's propagation of the matched
+    states within the binary32 tolerance."""
+    bins, n, S, steps, dt = 4096, 4003, 2, 20, 1e-3
+    rng = np.random.default_rng(4096 + d + int(broadcast))
+    og = orc.Grid(bins, -3.0, 3.0)
+    nin = 1 if broadcast else S
+    px = rng.normal(-0.3, 0.8, (nin, n)).astype(np.float32)
+    _, cp1 = orc.restrict(px.astype(np.float64), og)
+    cp = np.repeat(cp1, S, axis=0) if broadcast else cp1
+    _, ct = orc.restrict(rng.normal(0.4, 0.6, (S, 4 * n)), og)
+    x = torch.tensor(px, device=DEV)
+    y = torch.tensor(rng.normal(0.0, 1.0, (nin, d, n)), dtype=torch.float32, device=DEV)
+    g = L.Grid(bins, -3.0, 3.0)
+    m = L.Model(kind, d, 0.5, 3.0, 0.05)
+    cpt, ctt = _t(cp), _t(ct)
+    cs, ce = (torch.empty(S, bins, dtype=torch.int32, device=DEV) for _ in range(2))
+    cds, cde = (torch.empty(S, bins + 1, dtype=torch.float64, device=DEV) for _ in range(2))
+    if broadcast:
+        xf = torch.empty(S, n, dtype=torch.float32, device=DEV)
+        yf = torch.empty(S, d, n, dtype=torch.float32, device=DEV)
+        L.pr_fine_propagate(m, 0, L.Rng(7, 2), x, y, True, xf, yf, n, 1, S, steps, dt, grid=g, cdf_prior=cpt,
+                            cdf_target=ctt, counts_start=cs, cdf_start=cds, counts_end=ce, cdf_end=cde)
+    else:
+        xf, yf = x.clone(), y.clone()
+        L.pr_fine_propagate(m, 0, L.Rng(7, 2), xf, yf, False, xf, yf, n, 1, S, steps, dt, grid=g, cdf_prior=cpt,
+                            cdf_target=ctt, counts_start=cs, cdf_start=cds, counts_end=ce, cdf_end=cde)
+    xb = x.expand(S, n).contiguous() if broadcast else x
+    yb = y.expand(S, d, n).contiguous() if broadcast else y
+    xm = torch.empty_like(xb)
+    L.pr_match(0, xb, xm, n, S, g, cpt, ctt)
+    cs_ref, ce_ref = (torch.empty(S, bins, dtype=torch.int32, device=DEV) for _ in range(2))
+    cds_ref, cde_ref = (torch.empty(S, bins + 1, dtype=torch.float64, device=DEV) for _ in range(2))
+    L.pr_restrict(0, xm, n, S, g, cs_ref, cds_ref)
+    xs, ys = torch.empty_like(xb), torch.empty_like(yb)
+    L.pr_fine_propagate(m, 0, L.Rng(7, 2), xm, yb, False, xs, ys, n, 1, S, steps, dt)
+    L.pr_restrict(0, xs, n, S, g, ce_ref, cde_ref)
+    torch.cuda.synchronize()
+    assert torch.equal(xf, xs) and torch.equal(yf, ys)
+    assert torch.equal(cs, cs_ref) and torch.equal(cds, cds_ref)
+    assert torch.equal(ce, ce_ref) and torch.equal(cde, cde_ref)
+    # the propagation against the oracle's, from the same matched states
+    om = orc.Model(kind, d, 0.5, 3.0, 0.05)
+    ox, _ = orc.fine_propagate(om, 7, xm.cpu().numpy().astype(np.float64), yb.cpu().numpy().astype(np.float64),
+                               1, steps, dt, problem=2)
+    got = xf.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ox) <= 2e-3 * np.maximum(np.abs(ox), 1.0))
 
 
 @pytest.mark.parametrize("prec,bins,kind,d", [(0, 64, 1, 1), (0, 512, 1, 1), (0, 2900, 0, 1), (0, 512, 2, 3),
+                                              (0, 4096, 1, 1), (0, 3500, 2, 3),
                                               (1, 64, 0, 1), (1, 2400, 1, 1), (1, 256, 2, 3), (1, 4096, 1, 1)])
 def test_fused_matching_equals_standalone(L, orc, prec, bins, kind, d):
     """pr_fine_propagate with the matching fused into its prologue equals
