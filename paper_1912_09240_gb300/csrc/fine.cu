@@ -655,6 +655,16 @@ match_f32_wide_kernel(const float* __restrict__ xp, float* __restrict__ xo, int6
         os[p] = __double2float_rn(match_one_f64(ms, g, (double)xs[p]));
 }
 
+// dst[s][j] = src[j] for every slice s (one ensemble's values copied into
+// every slice of a slice-major array of `per_slice` floats per slice).
+__global__ void broadcast_slices_kernel(const float* __restrict__ src, float* __restrict__ dst, int64_t per_slice,
+                                        int n_slices)
+{
+    const int64_t total = per_slice * n_slices;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i % per_slice];
+}
+
 // raw Philox blocks for caller-given counters
 __global__ void rng_words_kernel(const uint4* __restrict__ ctr, int64_t n, uint32_t k0, uint32_t k1,
                                  uint4* __restrict__ out)
@@ -894,9 +904,11 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
         const size_t ybytes = (size_t)D * n * sizeof(float);
         if (y_in != y_out) {
             if (broadcast_input) {
-                for (int s = 0; s < n_slices; ++s)
-                    PR_TRY_CUDA(cudaMemcpyAsync(static_cast<char*>(y_out) + (size_t)s * ybytes, y_in, ybytes,
-                                                cudaMemcpyDeviceToDevice, st));
+                const int64_t per = (int64_t)D * n;
+                const int blocks = (int)std::min<int64_t>((per * n_slices + 255) / 256, 8 * (int64_t)num_sms());
+                broadcast_slices_kernel<<<blocks, 256, 0, st>>>(static_cast<const float*>(y_in),
+                                                                static_cast<float*>(y_out), per, n_slices);
+                PR_CHECK_LAUNCH();
             } else {
                 PR_TRY_CUDA(cudaMemcpyAsync(y_out, y_in, ybytes * n_slices, cudaMemcpyDeviceToDevice, st));
             }
