@@ -152,7 +152,8 @@ const char* pr_version(void);
  *                with broadcast_input != 0 a single ensemble [n], [d][n] is
  *                the start of every slice (the zeroth iteration).
  *   x_out, y_out (device) end states, same layout as the non-broadcast input;
- *                may alias x_in / y_in exactly (in-place), not partially.
+ *                may alias x_in / y_in exactly (in-place), not partially, and
+ *                not at all with broadcast_input (PR_ERR_INVALID_ARG).
  *   grid         needed when any of the fused outputs below is requested.
  *   cdf_prior, cdf_target (device, [n_slices][bins+1]) or both NULL: fused
  *                matching (pr_match) applied to the start state first; its

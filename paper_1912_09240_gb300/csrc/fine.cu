@@ -838,8 +838,10 @@ extern "C" pr_status pr_fine_propagate(const pr_model* model, pr_precision preci
     if (any_grid && !grid_ok(grid)) return PR_ERR_INVALID_ARG;
     const int D = model->fast_dim;
     const size_t esz = precision == PR_F32 ? 4 : 8;
-    // in-place is allowed only as exact aliasing of whole arrays
+    // in-place is allowed only as exact aliasing of whole arrays, and not
+    // from a broadcast input (every slice reads the one input ensemble)
     if (x_in == x_out && (broadcast_input || y_in != y_out)) return PR_ERR_INVALID_ARG;
+    if (broadcast_input && y_in == y_out) return PR_ERR_INVALID_ARG;
     (void)esz;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 

@@ -63,6 +63,12 @@ def test_invalid_arguments_rejected_on_host(L):
                                  1e-3, None, None, None, fake, None, None, None, None) == L.PR_ERR_INVALID_ARG
     assert lib.pr_fine_propagate(ctypes.byref(m), 0, ctypes.byref(r), fake, fake, 0, fake, fake, 10, 0, 1, 1,
                                  1e-3, ctypes.byref(g), None, None, None, fake, None, None, None) == L.PR_ERR_INVALID_ARG
+    # outputs aliasing a broadcast input
+    other = ctypes.c_void_p(0x2000)
+    assert lib.pr_fine_propagate(ctypes.byref(m), 0, ctypes.byref(r), fake, other, 1, fake, fake, 10, 0, 1, 1,
+                                 1e-3, None, None, None, None, None, None, None, None) == L.PR_ERR_INVALID_ARG
+    assert lib.pr_fine_propagate(ctypes.byref(m), 0, ctypes.byref(r), other, fake, 1, fake, fake, 10, 0, 1, 1,
+                                 1e-3, None, None, None, None, None, None, None, None) == L.PR_ERR_INVALID_ARG
     bad = L.Grid(0, -1.0, 1.0).c()
     assert lib.pr_restrict(0, fake, 10, 1, ctypes.byref(bad), fake, None, None) == L.PR_ERR_INVALID_ARG
     inv = L.Grid(4, 1.0, -1.0).c()
