@@ -502,6 +502,12 @@ __device__ __forceinline__ void for_each_f32(const float* __restrict__ xs, int64
     const int64_t nv = (e - hb) >> 2;
     const float4* __restrict__ v = reinterpret_cast<const float4*>(xs + hb);
     int64_t q = t;
+    for (; q + 3 * T < nv; q += 4 * T) {   // four loads in flight per thread
+        const float4 u0 = __ldcs(v + q), u1 = __ldcs(v + q + T), u2 = __ldcs(v + q + 2 * T),
+                     u3 = __ldcs(v + q + 3 * T);
+        op8(u0, u1);
+        op8(u2, u3);
+    }
     for (; q + T < nv; q += 2 * T) op8(__ldcs(v + q), __ldcs(v + q + T));
     if (q < nv) op4(__ldcs(v + q));
     for (int64_t p = hb + 4 * nv + t; p < e; p += T) op1(xs[p]);
