@@ -805,7 +805,9 @@ static pr_status launch_match_f32_wide(const float* xp, float* xo, int64_t n, in
 {
     const size_t smem = match_smem_bytes(g.bins);
     if (smem > (size_t)smem_optin_max()) return PR_ERR_UNSUPPORTED;
-    const int64_t per_block = stream_range(n, n_slices, 4096, 8);
+    // one wave of as many CTAs per SM as their shared memory allows (at most 8)
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(228 * 1024) / (smem + 1024)));
+    const int64_t per_block = stream_range(n, n_slices, 4096, per_sm);
     const int64_t blocks_per_slice = (n + per_block - 1) / per_block;
     PR_TRY_CUDA(set_smem(match_f32_wide_kernel, smem));
     match_f32_wide_kernel<<<dim3((unsigned)blocks_per_slice, (unsigned)n_slices), 256, smem, st>>>(
